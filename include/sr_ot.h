@@ -1,0 +1,227 @@
+/*
+ * sr_ot.h -- C ABI of the GB300 (sm_103a) block-coordinate Frank-Wolfe solver
+ * for squared-l2 semi-relaxed optimal transport (Fukunaga & Kasai,
+ * arXiv 2103.05857).
+ *
+ * Problem (Sec. 3, eq. 5, stated here in the library's orientation, which is
+ * the transpose of the paper's: rows are the blocks):
+ *
+ *     minimise  f(T) = <C, T> + (rho/2) || T^T 1_m - b ||^2
+ *     over      T in R^{m x n}, T >= 0, T 1_n = a          (eq. 6: product of
+ *                                                           scaled simplices)
+ *
+ * rho = 1/lambda of the paper. The block gradient of row i is
+ * grad_i = C_{i,:} + rho (s - b), s = T^T 1_m (Sec. 3.1); the linear
+ * minimisation oracle is a_i e_{j*}, j* = argmin_j grad_ij (eq. 7); the
+ * duality gap is g(T) = sum_i <t_i - a_i e_{j*}, grad_i> (Thm 2, eq. 11).
+ *
+ * Conventions for every entry point:
+ *   - All matrices are dense row-major; all sizes are element counts.
+ *   - Pointers named X, Y, C, a, b, T, dX, dY, db, dC are DEVICE pointers on
+ *     the handle's device, owned by the caller, and must stay valid until the
+ *     call returns. Their element type follows opts->precision: double for
+ *     SR_OT_FP64, float for SR_OT_FP32 and SR_OT_FP32_BF16COST.
+ *   - Pointers to sr_ot_options, sr_ot_result and per-instance size/offset
+ *     arrays are HOST pointers.
+ *   - Calls are ordered on the handle's stream and return after the stream
+ *     has been synchronised (results are final when the call returns).
+ *   - One handle per host thread. A handle owns its device workspace (grown
+ *     on demand, freed by sr_ot_destroy) and a pinned result buffer.
+ *   - Return value: SR_OT_OK or SR_OT_NOT_CONVERGED on success, a negative
+ *     sr_ot_status on error; sr_ot_last_error() then describes it. Nothing
+ *     aborts, traps or waits without bound.
+ */
+#ifndef SR_OT_H
+#define SR_OT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sr_ot_ctx *sr_ot_handle;
+
+typedef enum {
+    SR_OT_OK = 0,
+    SR_OT_NOT_CONVERGED = 1,  /* status, not an error: max_epochs reached before tol */
+    SR_OT_EINVAL = -1,        /* invalid argument (sizes, pointers, options, weights) */
+    SR_OT_ENOMEM = -2,        /* device workspace allocation failed */
+    SR_OT_ECUDA = -3,         /* CUDA runtime error */
+    SR_OT_ETIMEOUT = -4,      /* a bounded device wait gave up */
+    SR_OT_ENUMERIC = -5,      /* non-finite value met in the inputs or iterates */
+    SR_OT_EUNSUPPORTED = -6   /* valid request outside this build's limits */
+} sr_ot_status;
+
+/* Direction rule (Alg. 1; Alg. A.2 away steps; Alg. A.3 pairwise steps;
+ * Alg. A.1 full FW). */
+typedef enum { SR_OT_BCFW = 0, SR_OT_BCAFW = 1, SR_OT_BCPFW = 2, SR_OT_FW = 3 } sr_ot_variant;
+
+/* Block order (Sec. 3.1: U = uniform, P = fresh permutation per epoch;
+ * Sec. 4.2 / Alg. A.4: gap-adaptive sampling, "BCFW-GA"). */
+typedef enum {
+    SR_OT_CYCLIC = 0,
+    SR_OT_PERMUTE = 1,
+    SR_OT_UNIFORM = 2,
+    SR_OT_GAP_ADAPTIVE = 3
+} sr_ot_order;
+
+/* Step rule (Alg. 1): decay 2m/(k+2m) (FW: 2/(k+2)) or exact line search
+ * (eq. 8; eq. 10 for away/pairwise, which require SR_OT_ELS). */
+typedef enum { SR_OT_DEC = 0, SR_OT_ELS = 1 } sr_ot_step;
+
+/* Arithmetic. SR_OT_FP64: everything in double. SR_OT_FP32: float plan,
+ * cost and row updates; the duality gap, column-sum refresh and stopping test
+ * accumulate in double. SR_OT_FP32_BF16COST: as SR_OT_FP32, with the cost
+ * C = |x|^2 + |y|^2 - 2 X Y^T built by a BF16 tensor-core GEMM with FP32
+ * accumulation and FP32 norms (points mode, d a multiple of 64). */
+typedef enum { SR_OT_FP64 = 0, SR_OT_FP32 = 1, SR_OT_FP32_BF16COST = 2 } sr_ot_precision;
+
+typedef struct {
+    int variant;              /* sr_ot_variant                                     */
+    int order;                /* sr_ot_order (ignored by SR_OT_FW)                 */
+    int step;                 /* sr_ot_step                                        */
+    int precision;            /* sr_ot_precision                                   */
+    double rho;               /* penalty weight rho = 1/lambda_paper, finite, >= 0 */
+    double tol_rel_gap;       /* stop when g(T) <= tol * f(T); 0 = run max_epochs  */
+    long long max_epochs;     /* epochs of m block updates (FW: iterations), >= 0 */
+    int gap_every;            /* certificate every this many epochs, >= 1          */
+    int refresh_every;        /* FP32: reload the running residual from the exact
+                                 column sums every this many certificates; 0 never */
+    int ga_M;                 /* gap-adaptive: global gap update every ga_M epochs */
+    int ga_global_only;       /* gap-adaptive: 1 = no inner update (BCFW-GAS)      */
+    unsigned long long seed;  /* block-order random stream                         */
+    int *trace;               /* optional DEVICE int32[4*trace_capacity]: per block
+                                 update k, trace[4k..4k+3] = block i, LMO vertex
+                                 j*, away vertex v (-1 if none), step gamma as
+                                 IEEE-754 binary32 bits                           */
+    long long trace_capacity;
+    int dense_only;           /* 1: FP32 away/pairwise solves keep the dense row
+                                 kernel instead of the active-set kernel          */
+    int reserved;
+} sr_ot_options;
+
+typedef struct {
+    double objective;         /* f(T) at return                                    */
+    double gap;               /* g(T) at return (Thm 2)                            */
+    double rel_gap;           /* g / f                                             */
+    double dual;              /* Lagrangian dual value w(T) = f - g (Thm 2)        */
+    long long epochs;         /* epochs (FW: iterations) performed                 */
+    long long block_updates;  /* block updates performed                           */
+    int status;               /* sr_ot_status of this solve                        */
+    int reserved;
+} sr_ot_result;
+
+/* Fill *opts with defaults: BCFW, cyclic, DEC, FP32, rho = 10, tol 0,
+ * max_epochs 100, gap_every 1, refresh_every 1, ga_M 1, seed 0, no trace,
+ * dense_only 0. */
+void sr_ot_default_options(sr_ot_options *opts);
+
+/* Create a handle bound to CUDA device `device` and stream `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream). *h is NULL on error. */
+sr_ot_status sr_ot_create(sr_ot_handle *h, int device, void *cuda_stream);
+
+/* Rebind the handle to another stream of the same device. */
+sr_ot_status sr_ot_set_stream(sr_ot_handle h, void *cuda_stream);
+
+/* Free the handle's workspace, graphs and pinned buffers. NULL is a no-op. */
+sr_ot_status sr_ot_destroy(sr_ot_handle h);
+
+/* Message for the last error on h (or for a failed sr_ot_create when h is
+ * NULL). The string is owned by the library and valid until the next call. */
+const char *sr_ot_last_error(sr_ot_handle h);
+
+/*
+ * Solve one instance (Alg. 1 / A.2 / A.3 / A.4 / A.1 per opts).
+ *
+ * Cost: exactly one of {C} (m x n) or {X (m x d), Y (n x d)} is non-NULL.
+ * Points are turned into the squared-Euclidean cost C_ij = ||x_i - y_j||^2;
+ * d = 3 is evaluated on the fly inside the solver, other d are materialised
+ * once per call in the handle's workspace.
+ * a (m), b (n): nonnegative finite weights (the paper's are histograms).
+ * T_inout (m x n): if warm_start != 0, a feasible start (T >= 0, rows sum to
+ * a); otherwise it is overwritten with T0 = (a_i e_0) (Thm 1). On return it
+ * holds the final plan.
+ * res: host pointer, filled on return.
+ */
+sr_ot_status sr_ot_solve(sr_ot_handle h, const sr_ot_options *opts, int m, int n, int d,
+                         const void *C, const void *X, const void *Y, const void *a,
+                         const void *b, void *T_inout, int warm_start, sr_ot_result *res);
+
+/*
+ * Solve `batch` independent instances in one persistent launch (captured in a
+ * CUDA graph and replayed for a repeated shape set). Points mode with d = 3.
+ * m[k], n[k]: HOST arrays of per-instance sizes. off_X, off_Y, off_a, off_b,
+ * off_T: HOST arrays of per-instance ELEMENT offsets into the packed device
+ * buffers X, Y, a, b, T. Each instance starts from T0 = (a_i e_0).
+ * res: HOST array of `batch` results; each instance has its own status.
+ */
+sr_ot_status sr_ot_solve_batched(sr_ot_handle h, const sr_ot_options *opts, int batch,
+                                 const int *m, const int *n, int d, const long long *off_X,
+                                 const long long *off_Y, const long long *off_a,
+                                 const long long *off_b, const long long *off_T,
+                                 const void *X, const void *Y, const void *a, const void *b,
+                                 void *T, sr_ot_result *res);
+
+/*
+ * Gradients of the optimal value through the envelope theorem at a (converged)
+ * plan T, for the squared-Euclidean point cost (not in the paper):
+ *   dC = T,  dX = 2 (diag(T 1) X - T Y),  dY = 2 (diag(T^T 1) Y - T^T X),
+ *   db = -rho (T^T 1 - b).
+ * X, Y (points, d <= 16) may be NULL when only dC/db are requested; any
+ * output may be NULL to skip it. Uses opts->precision and opts->rho only.
+ */
+sr_ot_status sr_ot_grad(sr_ot_handle h, const sr_ot_options *opts, int m, int n, int d,
+                        const void *X, const void *Y, const void *a, const void *b,
+                        const void *T, void *dC, void *dX, void *dY, void *db);
+
+/* Batched form of sr_ot_grad over packed instances (offsets as in
+ * sr_ot_solve_batched; off_dX/off_dY/off_db index the outputs). */
+sr_ot_status sr_ot_grad_batched(sr_ot_handle h, const sr_ot_options *opts, int batch,
+                                const int *m, const int *n, int d, const long long *off_X,
+                                const long long *off_Y, const long long *off_b,
+                                const long long *off_T, const void *X, const void *Y,
+                                const void *b, const void *T, void *dX, void *dY, void *db);
+
+/*
+ * Certificate of any feasible plan T (Thm 2): objective f, linearisation
+ * duality gap g = sum_i g_i (eq. 11) and Lagrangian dual w = f - g.
+ * Cost as in sr_ot_solve. If g_rows is non-NULL it receives the per-row
+ * gaps g_i as DEVICE doubles (m). Uses opts->precision and opts->rho only.
+ */
+sr_ot_status sr_ot_gap(sr_ot_handle h, const sr_ot_options *opts, int m, int n, int d,
+                       const void *C, const void *X, const void *Y, const void *a,
+                       const void *b, const void *T, double *g_rows, sr_ot_result *res);
+
+/*
+ * Squared-Euclidean cost matrix C_ij = ||x_i - y_j||^2 (m x n, float),
+ * built on the tensor cores from BF16-rounded points with FP32 accumulation
+ * and FP32 norms of the rounded points: C = |x~|^2 + |y~|^2 - 2 X~ Y~^T.
+ * X (m x d), Y (n x d) are float; d must be a multiple of 64. The paper uses
+ * the Euclidean cost of colour centroids (Sec. 6.1); the GEMM form is this
+ * library's route for feature dimensions d >= 64.
+ */
+sr_ot_status sr_ot_cost_bf16(sr_ot_handle h, int m, int n, int d, const float *X,
+                             const float *Y, float *C);
+
+/*
+ * Observability (not in the paper). sr_ot_launch_count: number of this
+ * library's kernels launched on h since it was created. When profiling is
+ * enabled, the library brackets each launch group on the handle's stream with
+ * CUDA events and accumulates device time per kernel class:
+ *   SR_OT_PROF_EPOCH  single-instance epoch kernels (block updates)
+ *   SR_OT_PROF_CERT   certificate passes (column sums, row pass, reduction)
+ *   SR_OT_PROF_BATCH  batched persistent solves
+ *   SR_OT_PROF_GRAD   adjoint kernels
+ *   SR_OT_PROF_COST   cost materialisation (plain or BF16 tensor-core GEMM)
+ * sr_ot_profile_read returns the total milliseconds and the number of timed
+ * launch groups of one class; sr_ot_profile_enable(h, 1) also resets them.
+ */
+enum { SR_OT_PROF_EPOCH = 0, SR_OT_PROF_CERT = 1, SR_OT_PROF_BATCH = 2, SR_OT_PROF_GRAD = 3,
+       SR_OT_PROF_COST = 4, SR_OT_PROF_KINDS = 5 };
+long long sr_ot_launch_count(sr_ot_handle h);
+sr_ot_status sr_ot_profile_enable(sr_ot_handle h, int enable);
+sr_ot_status sr_ot_profile_read(sr_ot_handle h, int kind, double *total_ms, long long *groups);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SR_OT_H */

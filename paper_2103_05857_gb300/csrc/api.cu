@@ -1,0 +1,689 @@
+// api.cu -- the C ABI declared in include/sr_ot.h: handle, validation,
+// workspace, and the host loop that drives the epoch and certificate kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sr_ot.h"
+#include "common.cuh"
+#include "internal.h"
+
+using namespace srot;
+
+namespace {
+
+// Workspace slots owned by a handle; each grows on demand.
+enum WsSlot {
+    WS_Q = 0, WS_PARTIAL, WS_R64, WS_RQ32, WS_COLPART, WS_ROWPART, WS_CERT, WS_PERM, WS_PERMKEY,
+    WS_PERMIDX, WS_GSTORE, WS_STATUS, WS_COST, WS_CHECK, WS_SCRATCH, WS_ATOMS, WS_COUNT
+};
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct ProfPair {
+    cudaEvent_t a, b;
+    int kind;
+};
+
+struct sr_ot_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    DevBuf ws[WS_COUNT];
+    double *h_cert = nullptr;   // pinned: kCertCount doubles
+    int *h_status = nullptr;    // pinned: {device status, sparse-kernel resume index}
+    double *h_check = nullptr;  // pinned: input check results
+    long long launches = 0;     // kernels launched on this handle
+    // profiling: event pairs waiting for the next synchronisation
+    bool prof = false;
+    std::vector<ProfPair> pending;
+    std::vector<cudaEvent_t> event_pool;
+    double prof_ms[SR_OT_PROF_KINDS] = {0, 0, 0, 0, 0};
+    long long prof_groups[SR_OT_PROF_KINDS] = {0, 0, 0, 0, 0};
+};
+
+namespace {
+
+sr_ot_status fail(sr_ot_handle h, sr_ot_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    else g_create_error = buf;
+    return st;
+}
+
+#define CK(h, expr)                                                                     \
+    do {                                                                                \
+        cudaError_t e_ = (expr);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail((h), e_ == cudaErrorMemoryAllocation ? SR_OT_ENOMEM : SR_OT_ECUDA, \
+                        "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+#define CKL(h)                                                                          \
+    do {                                                                                \
+        cudaError_t e_ = cudaPeekAtLastError();                                          \
+        if (e_ != cudaSuccess) {                                                        \
+            cudaGetLastError();                                                          \
+            return fail((h), SR_OT_ECUDA, "kernel launch: %s (%s:%d)", cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                            \
+        }                                                                               \
+    } while (0)
+
+cudaEvent_t prof_event(sr_ot_handle h) {
+    if (!h->event_pool.empty()) {
+        cudaEvent_t e = h->event_pool.back();
+        h->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Bracket a launch group of class `kind` (no-op unless profiling).
+struct ProfScope {
+    sr_ot_handle h;
+    int kind;
+    cudaEvent_t a = nullptr;
+    ProfScope(sr_ot_handle h_, int kind_) : h(h_), kind(kind_) {
+        if (h->prof) {
+            a = prof_event(h);
+            cudaEventRecord(a, h->stream);
+        }
+    }
+    ~ProfScope() {
+        if (h->prof) {
+            cudaEvent_t b = prof_event(h);
+            cudaEventRecord(b, h->stream);
+            h->pending.push_back(ProfPair{a, b, kind});
+        }
+    }
+};
+
+// Fold finished event pairs into the totals (call after a stream sync).
+void prof_collect(sr_ot_handle h) {
+    for (auto &p : h->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            h->prof_ms[p.kind] += ms;
+            h->prof_groups[p.kind] += 1;
+        } else {
+            cudaGetLastError();
+        }
+        h->event_pool.push_back(p.a);
+        h->event_pool.push_back(p.b);
+    }
+    h->pending.clear();
+}
+
+sr_ot_status ws_get(sr_ot_handle h, int slot, size_t bytes, void **out) {
+    DevBuf &b = h->ws[slot];
+    bytes = std::max<size_t>(bytes, 256);
+    if (b.cap < bytes) {
+        if (b.p) {
+            cudaStreamSynchronize(h->stream);
+            cudaFree(b.p);
+            b.p = nullptr;
+            b.cap = 0;
+        }
+        size_t cap = bytes + bytes / 4;
+        cudaError_t e = cudaMalloc(&b.p, cap);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, SR_OT_ENOMEM, "workspace allocation of %zu bytes failed: %s", cap,
+                        cudaGetErrorString(e));
+        }
+        b.cap = cap;
+    }
+    *out = b.p;
+    return SR_OT_OK;
+}
+
+template <typename T>
+sr_ot_status ws_typed(sr_ot_handle h, int slot, size_t count, T **out) {
+    void *p = nullptr;
+    sr_ot_status st = ws_get(h, slot, count * sizeof(T), &p);
+    *out = static_cast<T *>(p);
+    return st;
+}
+
+// ---------------------------------------------------------------------------
+// Input checks on the device: finiteness and sign of weights, finiteness of
+// the cost source. out[0] = #bad entries of a, out[1] = #bad of b,
+// out[2] = #non-finite cost entries.
+// ---------------------------------------------------------------------------
+template <typename Real>
+__global__ void k_check_inputs(int m, int n, const Real *a, const Real *b, const Real *src,
+                               long long nsrc, double *out) {
+    __shared__ int cnt[3];
+    if (threadIdx.x < 3) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    int c0 = 0, c1 = 0, c2 = 0;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+         e < (long long)m || e < (long long)n || e < nsrc; e += (long long)gridDim.x * blockDim.x) {
+        if (e < m) { Real v = a[e]; c0 += !(isfinite((double)v) && v >= Real(0)); }
+        if (e < n) { Real v = b[e]; c1 += !(isfinite((double)v) && v >= Real(0)); }
+        if (e < nsrc) c2 += !isfinite((double)src[e]);
+    }
+    if (c0) atomicAdd(&cnt[0], c0);
+    if (c1) atomicAdd(&cnt[1], c1);
+    if (c2) atomicAdd(&cnt[2], c2);
+    __syncthreads();
+    if (threadIdx.x < 3 && cnt[threadIdx.x]) atomicAdd(&out[threadIdx.x], (double)cnt[threadIdx.x]);
+}
+
+template <typename Real>
+sr_ot_status check_inputs(sr_ot_handle h, int m, int n, const Real *a, const Real *b,
+                          const Real *src, long long nsrc, const Real *src2, long long nsrc2) {
+    double *d;
+    sr_ot_status st = ws_typed(h, WS_CHECK, 4, &d);
+    if (st) return st;
+    CK(h, cudaMemsetAsync(d, 0, 4 * sizeof(double), h->stream));
+    long long tot = std::max<long long>(std::max<long long>(m, n), nsrc);
+    int blocks = (int)std::min<long long>((tot + 255) / 256, 152 * 8);
+    k_check_inputs<Real><<<blocks, 256, 0, h->stream>>>(m, n, a, b, src, nsrc, d);
+    h->launches += 1;
+    CKL(h);
+    if (src2 && nsrc2 > 0) {
+        blocks = (int)std::min<long long>((nsrc2 + 255) / 256, 152 * 8);
+        k_check_inputs<Real><<<blocks, 256, 0, h->stream>>>(0, 0, a, b, src2, nsrc2, d);
+        h->launches += 1;
+        CKL(h);
+    }
+    CK(h, cudaMemcpyAsync(h->h_check, d, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (h->h_check[0] > 0) return fail(h, SR_OT_EINVAL, "a has %.0f negative or non-finite entries", h->h_check[0]);
+    if (h->h_check[1] > 0) return fail(h, SR_OT_EINVAL, "b has %.0f negative or non-finite entries", h->h_check[1]);
+    if (h->h_check[2] > 0) return fail(h, SR_OT_ENUMERIC, "cost input has %.0f non-finite entries", h->h_check[2]);
+    return SR_OT_OK;
+}
+
+sr_ot_status check_opts(sr_ot_handle h, const sr_ot_options *o) {
+    if (!o) return fail(h, SR_OT_EINVAL, "opts is NULL");
+    if (o->variant < SR_OT_BCFW || o->variant > SR_OT_FW) return fail(h, SR_OT_EINVAL, "unknown variant %d", o->variant);
+    if (o->order < SR_OT_CYCLIC || o->order > SR_OT_GAP_ADAPTIVE) return fail(h, SR_OT_EINVAL, "unknown order %d", o->order);
+    if (o->step != SR_OT_DEC && o->step != SR_OT_ELS) return fail(h, SR_OT_EINVAL, "unknown step rule %d", o->step);
+    if (o->precision < SR_OT_FP64 || o->precision > SR_OT_FP32_BF16COST) return fail(h, SR_OT_EINVAL, "unknown precision %d", o->precision);
+    if (!std::isfinite(o->rho) || o->rho < 0.0) return fail(h, SR_OT_EINVAL, "rho must be finite and >= 0 (got %g)", o->rho);
+    if (!std::isfinite(o->tol_rel_gap) || o->tol_rel_gap < 0.0) return fail(h, SR_OT_EINVAL, "tol_rel_gap must be finite and >= 0");
+    if (o->max_epochs < 0) return fail(h, SR_OT_EINVAL, "max_epochs must be >= 0");
+    if (o->gap_every < 1) return fail(h, SR_OT_EINVAL, "gap_every must be >= 1");
+    if (o->refresh_every < 0) return fail(h, SR_OT_EINVAL, "refresh_every must be >= 0");
+    if ((o->variant == SR_OT_BCAFW || o->variant == SR_OT_BCPFW) && o->step != SR_OT_ELS)
+        return fail(h, SR_OT_EINVAL, "away and pairwise steps need the exact line search (SR_OT_ELS)");
+    if (o->trace && o->trace_capacity < 0) return fail(h, SR_OT_EINVAL, "trace_capacity must be >= 0");
+    return SR_OT_OK;
+}
+
+sr_ot_status check_stream_device(sr_ot_handle h) {
+    int cur = -1;
+    CK(h, cudaGetDevice(&cur));
+    if (cur != h->device) CK(h, cudaSetDevice(h->device));
+    return SR_OT_OK;
+}
+
+// Workspace and the certificate plan for an m x n instance.
+sr_ot_status cert_work(sr_ot_handle h, int m, int n, CertWork *w) {
+    int nchunks, rpc, ncolb, nrowb;
+    cert_work_shape(m, n, &nchunks, &rpc, &ncolb, &nrowb);
+    w->nchunks = nchunks;
+    w->rows_per_chunk = rpc;
+    w->ncolblocks = ncolb;
+    w->nrowblocks = nrowb;
+    sr_ot_status st;
+    if ((st = ws_typed(h, WS_PARTIAL, (size_t)nchunks * n, &w->partial))) return st;
+    if ((st = ws_typed(h, WS_R64, (size_t)n, &w->r64))) return st;
+    if ((st = ws_typed(h, WS_RQ32, (size_t)n, &w->rq32))) return st;
+    if ((st = ws_typed(h, WS_COLPART, (size_t)2 * ncolb, &w->colpart))) return st;
+    if ((st = ws_typed(h, WS_ROWPART, (size_t)2 * nrowb, &w->rowpart))) return st;
+    if ((st = ws_typed(h, WS_CERT, (size_t)kCertCount, &w->cert))) return st;
+    return SR_OT_OK;
+}
+
+void fill_result(sr_ot_result *res, const double *cert, long long epochs, long long updates,
+                 int status) {
+    if (!res) return;
+    res->objective = cert[kCertF];
+    res->gap = cert[kCertG];
+    res->rel_gap = cert[kCertRel];
+    res->dual = cert[kCertW];
+    res->epochs = epochs;
+    res->block_updates = updates;
+    res->status = status;
+    res->reserved = 0;
+}
+
+// Resolve the cost source of an instance: C given, d = 3 points on the fly,
+// or other d materialised once into the workspace.
+template <typename Real>
+sr_ot_status make_inst(sr_ot_handle h, const sr_ot_options *o, int m, int n, int d, const void *C,
+                       const void *X, const void *Y, const void *a, const void *b, Inst<Real> *in) {
+    in->m = m;
+    in->n = n;
+    in->a = static_cast<const Real *>(a);
+    in->b = static_cast<const Real *>(b);
+    in->C = nullptr;
+    in->X = nullptr;
+    in->Y = nullptr;
+    const bool have_c = C != nullptr, have_pts = X != nullptr || Y != nullptr;
+    if (have_c == have_pts) return fail(h, SR_OT_EINVAL, "pass exactly one of C or (X, Y)");
+    sr_ot_status st;
+    if (have_c) {
+        if (o->precision == SR_OT_FP32_BF16COST)
+            return fail(h, SR_OT_EINVAL, "SR_OT_FP32_BF16COST needs points X, Y, not C");
+        in->cost_mode = kCostGiven;
+        in->C = static_cast<const Real *>(C);
+        if ((st = check_inputs<Real>(h, m, n, in->a, in->b, in->C, (long long)m * n, nullptr, 0))) return st;
+        return SR_OT_OK;
+    }
+    if (!X || !Y) return fail(h, SR_OT_EINVAL, "points mode needs both X and Y");
+    if (d <= 0) return fail(h, SR_OT_EINVAL, "d must be >= 1 in points mode (got %d)", d);
+    const Real *Xr = static_cast<const Real *>(X), *Yr = static_cast<const Real *>(Y);
+    if ((st = check_inputs<Real>(h, m, n, in->a, in->b, Xr, (long long)m * d, Yr, (long long)n * d))) return st;
+    if (o->precision == SR_OT_FP32_BF16COST) {
+        if constexpr (std::is_same<Real, float>::value) {
+            Real *Cw;
+            if ((st = ws_typed(h, WS_COST, (size_t)m * n, &Cw))) return st;
+            sr_ot_status s2 = sr_ot_cost_bf16(h, m, n, d, Xr, Yr, Cw);
+            if (s2 != SR_OT_OK) return s2;
+            in->cost_mode = kCostGiven;
+            in->C = Cw;
+            return SR_OT_OK;
+        } else {
+            return fail(h, SR_OT_EINVAL, "BF16 cost needs the FP32 element type");
+        }
+    }
+    if (d == 3) {
+        in->cost_mode = kCostPts3;
+        in->X = Xr;
+        in->Y = Yr;
+        return SR_OT_OK;
+    }
+    Real *Cw;
+    if ((st = ws_typed(h, WS_COST, (size_t)m * n, &Cw))) return st;
+    {
+        ProfScope ps(h, SR_OT_PROF_COST);
+        launch_cost_plain<Real>(m, n, d, Xr, Yr, Cw, h->stream);
+    }
+    h->launches += 1;
+    CKL(h);
+    in->cost_mode = kCostGiven;
+    in->C = Cw;
+    return SR_OT_OK;
+}
+
+// Read back the certificate and the device status words (one sync).
+// dev_status[0] is the status word, dev_status[1] the sparse-kernel resume index.
+sr_ot_status read_cert(sr_ot_handle h, const CertWork &w, int *dev_status, int *dstat) {
+    CK(h, cudaMemcpyAsync(h->h_cert, w.cert, kCertCount * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(h->h_status, dev_status, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    *dstat = *h->h_status;
+    prof_collect(h);
+    return SR_OT_OK;
+}
+
+sr_ot_status dev_status_error(sr_ot_handle h, int dstat) {
+    if (dstat == kDevNonFinite) return fail(h, SR_OT_ENUMERIC, "a non-finite gradient was met during the solve");
+    if (dstat == kDevTimeout) return fail(h, SR_OT_ETIMEOUT, "a bounded device wait gave up");
+    return fail(h, SR_OT_ECUDA, "device reported status %d", dstat);
+}
+
+template <typename Real>
+sr_ot_status solve_impl(sr_ot_handle h, const sr_ot_options *o, int m, int n, int d, const void *C,
+                        const void *X, const void *Y, const void *a, const void *b, void *T_inout,
+                        int warm_start, sr_ot_result *res) {
+    sr_ot_status st;
+    Inst<Real> in;
+    if ((st = make_inst<Real>(h, o, m, n, d, C, X, Y, a, b, &in))) return st;
+    const bool fp64 = std::is_same<Real, double>::value;
+    if (o->variant == SR_OT_FW)
+        return fail(h, SR_OT_EUNSUPPORTED, "full Frank-Wolfe is not available in this build");
+    if (o->order == SR_OT_GAP_ADAPTIVE)
+        return fail(h, SR_OT_EUNSUPPORTED, "gap-adaptive sampling is not available in this build");
+    if (n > epoch_max_n(fp64))
+        return fail(h, SR_OT_EUNSUPPORTED, "n = %d exceeds the single-instance limit %d for this precision",
+                    n, epoch_max_n(fp64));
+    Real *T = static_cast<Real *>(T_inout);
+    double *q;
+    int *dstat_d;
+    if ((st = ws_typed(h, WS_Q, (size_t)n, &q))) return st;
+    if ((st = ws_typed(h, WS_STATUS, 4, &dstat_d))) return st;
+    CK(h, cudaMemsetAsync(dstat_d, 0, sizeof(int), h->stream));
+    CK(h, cudaMemsetAsync(dstat_d + 1, 0xff, sizeof(int), h->stream));  // resume = -1
+    CertWork w;
+    if ((st = cert_work(h, m, n, &w))) return st;
+    int *perm = nullptr;
+    uint64_t *pkey = nullptr;
+    int *pidx = nullptr;
+    if (o->order == SR_OT_PERMUTE) {
+        if ((st = ws_typed(h, WS_PERM, (size_t)m, &perm))) return st;
+        size_t sb = make_perm_scratch_bytes(m);
+        if (sb) {
+            int L = 1;
+            while (L < m) L <<= 1;
+            if ((st = ws_typed(h, WS_PERMKEY, (size_t)L, &pkey))) return st;
+            if ((st = ws_typed(h, WS_PERMIDX, (size_t)L, &pidx))) return st;
+        }
+    }
+    launch_init_plan<Real>(in, T, warm_start, o->rho, q, h->stream);
+    h->launches += warm_start ? 1 : 2;
+    CKL(h);
+
+    // Away / pairwise steps in FP32 run on the active-set kernel while every
+    // row fits its atom record; an overflow hands the rest of the solve to
+    // the dense kernel.
+    bool use_sparse = false;
+    int2 *atoms = nullptr;
+    if constexpr (std::is_same<Real, float>::value) {
+        if ((o->variant == SR_OT_BCAFW || o->variant == SR_OT_BCPFW) && !o->dense_only &&
+            n <= epoch_max_n(false)) {
+            if ((st = ws_typed(h, WS_ATOMS, (size_t)m * kAtomRecord, &atoms))) return st;
+            CK(h, cudaMemsetAsync(dstat_d + 2, 0, sizeof(int), h->stream));
+            launch_build_atoms(m, n, T, atoms, dstat_d + 2, h->stream);
+            h->launches += 1;
+            CKL(h);
+            int ovf = 0;
+            CK(h, cudaMemcpyAsync(h->h_status, dstat_d + 2, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+            CK(h, cudaStreamSynchronize(h->stream));
+            ovf = h->h_status[0];
+            use_sparse = (ovf == 0);
+        }
+    }
+
+    EpochArgs<Real> A;
+    A.in = in;
+    A.T = T;
+    A.q = q;
+    A.rho = o->rho;
+    A.variant = o->variant;
+    A.step = o->step;
+    A.order = o->order;
+    A.seed = o->seed;
+    A.perm = perm;
+    A.g_store = nullptr;
+    A.ga_inner = 0;
+    A.trace = o->trace;
+    A.trace_cap = o->trace ? o->trace_capacity : 0;
+    A.status = dstat_d;
+    A.atoms = atoms;
+    A.resume = nullptr;
+    A.resume_in = nullptr;
+    {
+        const size_t rb = (size_t)n * sizeof(Real);
+        bool v = (rb % 16 == 0) && ((uintptr_t)T % 16 == 0);
+        if (in.cost_mode == kCostGiven) v = v && ((uintptr_t)in.C % 16 == 0);
+        A.vec = v;
+    }
+
+    const int refresh_every = fp64 ? 0 : o->refresh_every;
+    long long ep = 0, ncert = 0;
+    bool converged = false, have_cert = false;
+    for (ep = 0; ep < o->max_epochs; ++ep) {
+        if (o->order == SR_OT_PERMUTE) {
+            launch_make_perm(o->seed, ep, m, perm, pkey, pidx, h->stream);
+            h->launches += make_perm_scratch_bytes(m) ? 2 : 1;
+            CKL(h);
+        }
+        A.k0 = ep * (long long)m;
+        A.epoch = ep;
+        {
+            ProfScope ps(h, SR_OT_PROF_EPOCH);
+            if constexpr (std::is_same<Real, float>::value) {
+                if (use_sparse) {
+                    EpochArgs<float> As = A;
+                    As.resume = dstat_d + 1;
+                    launch_epoch_sparse(As, h->stream);
+                    EpochArgs<float> Ad = A;
+                    Ad.resume_in = dstat_d + 1;  // finishes the epoch only after an overflow
+                    launch_epoch<float>(Ad, h->stream);
+                    h->launches += 1;
+                } else {
+                    launch_epoch<Real>(A, h->stream);
+                }
+            } else {
+                launch_epoch<Real>(A, h->stream);
+            }
+        }
+        h->launches += 1;
+        CKL(h);
+        const bool last = ep + 1 == o->max_epochs;
+        if ((ep + 1) % o->gap_every == 0 || last) {
+            ++ncert;
+            double *refresh = (refresh_every > 0 && ncert % refresh_every == 0) ? q : nullptr;
+            {
+                ProfScope ps(h, SR_OT_PROF_CERT);
+                launch_certificate<Real>(in, T, o->rho, o->tol_rel_gap, w, refresh, nullptr, h->stream);
+            }
+            h->launches += 4;
+            CKL(h);
+            int dstat = 0;
+            if ((st = read_cert(h, w, dstat_d, &dstat))) return st;
+            have_cert = true;
+            if (dstat) return dev_status_error(h, dstat);
+            if (use_sparse && h->h_status[1] >= 0) use_sparse = false;  // a row outgrew its record
+            if (h->h_cert[kCertStop] != 0.0) { converged = true; ++ep; break; }
+        }
+    }
+    if (!have_cert) {
+        launch_certificate<Real>(in, T, o->rho, o->tol_rel_gap, w, nullptr, nullptr, h->stream);
+        h->launches += 4;
+        CKL(h);
+        int dstat = 0;
+        if ((st = read_cert(h, w, dstat_d, &dstat))) return st;
+        if (dstat) return dev_status_error(h, dstat);
+        converged = h->h_cert[kCertStop] != 0.0;
+    }
+    sr_ot_status out = (o->tol_rel_gap > 0.0 && !converged) ? SR_OT_NOT_CONVERGED : SR_OT_OK;
+    fill_result(res, h->h_cert, ep, ep * (long long)m, out);
+    return out;
+}
+
+template <typename Real>
+sr_ot_status gap_impl(sr_ot_handle h, const sr_ot_options *o, int m, int n, int d, const void *C,
+                      const void *X, const void *Y, const void *a, const void *b, const void *T,
+                      double *g_rows, sr_ot_result *res) {
+    sr_ot_status st;
+    Inst<Real> in;
+    if ((st = make_inst<Real>(h, o, m, n, d, C, X, Y, a, b, &in))) return st;
+    CertWork w;
+    if ((st = cert_work(h, m, n, &w))) return st;
+    int *dstat_d;
+    if ((st = ws_typed(h, WS_STATUS, 1, &dstat_d))) return st;
+    CK(h, cudaMemsetAsync(dstat_d, 0, sizeof(int), h->stream));
+    {
+        ProfScope ps(h, SR_OT_PROF_CERT);
+        launch_certificate<Real>(in, static_cast<const Real *>(T), o->rho, o->tol_rel_gap, w, nullptr,
+                                 g_rows, h->stream);
+    }
+    h->launches += 4;
+    CKL(h);
+    int dstat = 0;
+    if ((st = read_cert(h, w, dstat_d, &dstat))) return st;
+    fill_result(res, h->h_cert, 0, 0, SR_OT_OK);
+    return SR_OT_OK;
+}
+
+sr_ot_status check_sizes(sr_ot_handle h, int m, int n) {
+    if (m <= 0 || n <= 0) return fail(h, SR_OT_EINVAL, "m and n must be >= 1 (got m=%d, n=%d)", m, n);
+    return SR_OT_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void sr_ot_default_options(sr_ot_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->variant = SR_OT_BCFW;
+    o->order = SR_OT_CYCLIC;
+    o->step = SR_OT_DEC;
+    o->precision = SR_OT_FP32;
+    o->rho = 10.0;
+    o->tol_rel_gap = 0.0;
+    o->max_epochs = 100;
+    o->gap_every = 1;
+    o->refresh_every = 1;
+    o->ga_M = 1;
+    o->ga_global_only = 0;
+    o->seed = 0;
+    o->trace = nullptr;
+    o->trace_capacity = 0;
+}
+
+sr_ot_status sr_ot_create(sr_ot_handle *out, int device, void *cuda_stream) {
+    if (!out) return fail(nullptr, SR_OT_EINVAL, "sr_ot_create: out is NULL");
+    *out = nullptr;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || count == 0) {
+        cudaGetLastError();
+        return fail(nullptr, SR_OT_ECUDA, "no CUDA device available: %s", cudaGetErrorString(e));
+    }
+    if (device < 0 || device >= count) return fail(nullptr, SR_OT_EINVAL, "device %d out of range", device);
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return fail(nullptr, SR_OT_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    sr_ot_ctx *h = new sr_ot_ctx();
+    h->device = device;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaMallocHost(&h->h_cert, kCertCount * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&h->h_status, 2 * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&h->h_check, 4 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        sr_ot_destroy(h);
+        return fail(nullptr, SR_OT_ENOMEM, "pinned host buffer allocation failed");
+    }
+    *out = h;
+    return SR_OT_OK;
+}
+
+sr_ot_status sr_ot_set_stream(sr_ot_handle h, void *cuda_stream) {
+    if (!h) return fail(nullptr, SR_OT_EINVAL, "handle is NULL");
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    return SR_OT_OK;
+}
+
+sr_ot_status sr_ot_destroy(sr_ot_handle h) {
+    if (!h) return SR_OT_OK;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    for (auto &b : h->ws)
+        if (b.p) cudaFree(b.p);
+    if (h->h_cert) cudaFreeHost(h->h_cert);
+    if (h->h_status) cudaFreeHost(h->h_status);
+    if (h->h_check) cudaFreeHost(h->h_check);
+    for (auto &p : h->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (auto e : h->event_pool) cudaEventDestroy(e);
+    delete h;
+    return SR_OT_OK;
+}
+
+const char *sr_ot_last_error(sr_ot_handle h) {
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+sr_ot_status sr_ot_solve(sr_ot_handle h, const sr_ot_options *opts, int m, int n, int d,
+                         const void *C, const void *X, const void *Y, const void *a, const void *b,
+                         void *T_inout, int warm_start, sr_ot_result *res) {
+    if (!h) return fail(nullptr, SR_OT_EINVAL, "handle is NULL");
+    h->err.clear();
+    sr_ot_status st;
+    if ((st = check_opts(h, opts))) return st;
+    if ((st = check_sizes(h, m, n))) return st;
+    if (!a || !b || !T_inout) return fail(h, SR_OT_EINVAL, "a, b and T must be non-NULL");
+    if ((st = check_stream_device(h))) return st;
+    if (opts->precision == SR_OT_FP64)
+        return solve_impl<double>(h, opts, m, n, d, C, X, Y, a, b, T_inout, warm_start, res);
+    return solve_impl<float>(h, opts, m, n, d, C, X, Y, a, b, T_inout, warm_start, res);
+}
+
+sr_ot_status sr_ot_gap(sr_ot_handle h, const sr_ot_options *opts, int m, int n, int d,
+                       const void *C, const void *X, const void *Y, const void *a, const void *b,
+                       const void *T, double *g_rows, sr_ot_result *res) {
+    if (!h) return fail(nullptr, SR_OT_EINVAL, "handle is NULL");
+    h->err.clear();
+    sr_ot_status st;
+    if (!opts) return fail(h, SR_OT_EINVAL, "opts is NULL");
+    if (!std::isfinite(opts->rho) || opts->rho < 0.0) return fail(h, SR_OT_EINVAL, "rho must be finite and >= 0");
+    if ((st = check_sizes(h, m, n))) return st;
+    if (!a || !b || !T) return fail(h, SR_OT_EINVAL, "a, b and T must be non-NULL");
+    if ((st = check_stream_device(h))) return st;
+    if (opts->precision == SR_OT_FP64)
+        return gap_impl<double>(h, opts, m, n, d, C, X, Y, a, b, T, g_rows, res);
+    return gap_impl<float>(h, opts, m, n, d, C, X, Y, a, b, T, g_rows, res);
+}
+
+sr_ot_status sr_ot_solve_batched(sr_ot_handle h, const sr_ot_options *opts, int batch, const int *m,
+                                 const int *n, int d, const long long *off_X, const long long *off_Y,
+                                 const long long *off_a, const long long *off_b,
+                                 const long long *off_T, const void *X, const void *Y, const void *a,
+                                 const void *b, void *T, sr_ot_result *res) {
+    if (!h) return fail(nullptr, SR_OT_EINVAL, "handle is NULL");
+    return fail(h, SR_OT_EUNSUPPORTED, "batched solve is not available in this build");
+}
+
+sr_ot_status sr_ot_grad(sr_ot_handle h, const sr_ot_options *opts, int m, int n, int d,
+                        const void *X, const void *Y, const void *a, const void *b, const void *T,
+                        void *dC, void *dX, void *dY, void *db) {
+    if (!h) return fail(nullptr, SR_OT_EINVAL, "handle is NULL");
+    return fail(h, SR_OT_EUNSUPPORTED, "gradients are not available in this build");
+}
+
+sr_ot_status sr_ot_grad_batched(sr_ot_handle h, const sr_ot_options *opts, int batch, const int *m,
+                                const int *n, int d, const long long *off_X, const long long *off_Y,
+                                const long long *off_b, const long long *off_T, const void *X,
+                                const void *Y, const void *b, const void *T, void *dX, void *dY,
+                                void *db) {
+    if (!h) return fail(nullptr, SR_OT_EINVAL, "handle is NULL");
+    return fail(h, SR_OT_EUNSUPPORTED, "batched gradients are not available in this build");
+}
+
+long long sr_ot_launch_count(sr_ot_handle h) { return h ? h->launches : 0; }
+
+sr_ot_status sr_ot_profile_enable(sr_ot_handle h, int enable) {
+    if (!h) return fail(nullptr, SR_OT_EINVAL, "handle is NULL");
+    cudaStreamSynchronize(h->stream);
+    prof_collect(h);
+    h->prof = enable != 0;
+    for (int k = 0; k < SR_OT_PROF_KINDS; ++k) { h->prof_ms[k] = 0.0; h->prof_groups[k] = 0; }
+    return SR_OT_OK;
+}
+
+sr_ot_status sr_ot_profile_read(sr_ot_handle h, int kind, double *total_ms, long long *groups) {
+    if (!h) return fail(nullptr, SR_OT_EINVAL, "handle is NULL");
+    if (kind < 0 || kind >= SR_OT_PROF_KINDS) return fail(h, SR_OT_EINVAL, "unknown profile class %d", kind);
+    CK(h, cudaStreamSynchronize(h->stream));
+    prof_collect(h);
+    if (total_ms) *total_ms = h->prof_ms[kind];
+    if (groups) *groups = h->prof_groups[kind];
+    return SR_OT_OK;
+}
+
+sr_ot_status sr_ot_cost_bf16(sr_ot_handle h, int m, int n, int d, const float *X, const float *Y,
+                             float *C) {
+    if (!h) return fail(nullptr, SR_OT_EINVAL, "handle is NULL");
+    return fail(h, SR_OT_EUNSUPPORTED, "the BF16 tensor-core cost is not available in this build");
+}
+
+}  // extern "C"

@@ -1,0 +1,124 @@
+// internal.h -- launchers shared between the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace srot {
+
+// Cost source of one instance.
+enum CostMode : int {
+    kCostGiven = 0,  // dense C (m x n) in device memory
+    kCostPts3 = 1,   // points X (m x 3), Y (n x 3): C_ij = ||x_i - y_j||^2 on the fly
+};
+
+// Device-side layout of one certificate (Thm 2) result: doubles.
+enum CertSlot : int {
+    kCertF = 0,      // objective f(T)
+    kCertG = 1,      // linearisation gap g(T)
+    kCertW = 2,      // Lagrangian dual w(T) = f - g
+    kCertLin = 3,    // <C, T>
+    kCertPen = 4,    // (rho/2) ||T^T 1 - b||^2
+    kCertRel = 5,    // g / f
+    kCertStop = 6,   // 1.0 when g <= tol * f
+    kCertCount = 8
+};
+
+// One instance as seen by the certificate and solver kernels.
+template <typename Real>
+struct Inst {
+    int m, n;
+    int cost_mode;
+    const Real *C;   // kCostGiven
+    const Real *X;   // kCostPts3
+    const Real *Y;
+    const Real *a;
+    const Real *b;
+};
+
+// Workspace the certificate needs (all device pointers).
+struct CertWork {
+    double *partial;     // nchunks * n
+    int nchunks, rows_per_chunk;
+    double *r64;         // n: exact residual s - b
+    float *rq32;         // n: (float)(rho * r) for the FP32 argmin
+    double *colpart;     // per-block partials of the column pass (2 per block)
+    int ncolblocks;
+    double *rowpart;     // per-block partials of the row pass (3 per block)
+    int nrowblocks;
+    double *cert;        // kCertCount doubles
+};
+
+// Sizes of the certificate workspace for an m x n instance.
+void cert_work_shape(int m, int n, int *nchunks, int *rows_per_chunk, int *ncolblocks,
+                     int *nrowblocks);
+
+// Certificate of plan T (Thm 2). If refresh_q is non-null, the solver's
+// running residual is overwritten from the exact column sums: the FP32 path
+// keeps q = rho * r, the FP64 path keeps r (both in double). g_rows
+// (optional) receives per-row gaps.
+template <typename Real>
+void launch_certificate(const Inst<Real> &in, const Real *T, double rho, double tol,
+                        const CertWork &w, double *refresh_q, double *g_rows, cudaStream_t st);
+
+// T = (a_i e_0) (Thm 1) and the solver's initial residual (FP32: q = rho (T^T1 - b);
+// FP64: r = T^T1 - b with the column sums taken in ascending row order).
+template <typename Real>
+void launch_init_plan(const Inst<Real> &in, Real *T, int warm, double rho, double *q,
+                      cudaStream_t st);
+
+// Exact column-sum residual for the solver (ascending row order, FP64 accumulate).
+template <typename Real>
+void launch_init_residual(const Inst<Real> &in, const Real *T, double rho, double *q,
+                          cudaStream_t st);
+
+// Uniform random permutation of 0..m-1 for epoch `epoch` (sort by splitmix64 keys).
+void launch_make_perm(unsigned long long seed, long long epoch, int m, int *perm,
+                      uint64_t *keybuf, int *idxbuf, cudaStream_t st);
+size_t make_perm_scratch_bytes(int m);
+
+// Materialise C_ij = ||x_i - y_j||^2 for general d on the CUDA cores.
+template <typename Real>
+void launch_cost_plain(int m, int n, int d, const Real *X, const Real *Y, Real *C,
+                       cudaStream_t st);
+
+// Single-instance epoch of block updates.
+template <typename Real>
+struct EpochArgs {
+    Inst<Real> in;
+    Real *T;
+    double *q;               // running residual: FP32 path rho * r, FP64 path r
+    double rho;
+    int variant, step, order;
+    long long k0;            // block updates before this epoch
+    long long epoch;
+    unsigned long long seed;
+    const int *perm;         // order == PERMUTE
+    double *g_store;         // order == GAP_ADAPTIVE: per-row gaps (m)
+    int ga_inner;            // 1: recompute g_i after each update
+    int *trace;
+    long long trace_cap;
+    int *status;
+    bool vec;                // T (and C) rows start on 16-byte boundaries
+    int2 *atoms;             // sparse kernel: per-row atom records (m x kAtomRecord)
+    int *resume;             // sparse kernel: set to the update index where it stopped
+    const int *resume_in;    // dense kernel: start at *resume_in, or return if it is < 0
+};
+
+// Atom record of one row for the sparse kernel: {count, 0} then up to 31
+// (column, value bits) pairs; 256 bytes.
+constexpr int kAtomRecord = 32;
+
+// Sparse-support epoch (FP32, away / pairwise steps). False if n is too large.
+bool launch_epoch_sparse(const EpochArgs<float> &args, cudaStream_t st);
+
+// Atom records of a dense plan; *overflow becomes 1 if a row has > 31 atoms.
+void launch_build_atoms(int m, int n, const float *T, int2 *rec, int *overflow, cudaStream_t st);
+
+// Returns false when n exceeds the single-instance kernel's limit.
+template <typename Real>
+bool launch_epoch(const EpochArgs<Real> &args, cudaStream_t st);
+
+int epoch_max_n(bool fp64);
+
+}  // namespace srot

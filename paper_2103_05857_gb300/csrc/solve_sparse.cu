@@ -1,0 +1,506 @@
+// solve_sparse.cu -- one epoch of BCPFW / BCAFW (FP32) with per-row active
+// sets kept as compact atom lists.
+//
+// With away or pairwise steps (Sec. 4.1, Alg. A.2, A.3) a row's active set
+// S_i = {j : t_ij > 0} stays small, and the paper notes that these steps cost
+// O(n + |S_i|) per block (Sec. 4.3). This kernel follows that count: per
+// block update the only O(n) work is the LMO argmin of the row gradient
+// (eq. 7); the away vertex, the line search (eq. 10) and the rank-1 update
+// touch the |S_i| atoms only.
+//
+// Layout. One CTA of NT threads. Thread tid owns columns j = 4 (tid + NT g)+e
+// as in the dense kernel; the target points y_j of those columns live in
+// registers as pairs for packed FP32x2 arithmetic. The running residual
+// q = rho (T^T 1 - b) lives in shared memory as a compensated FP32 pair
+// (qh, ql), initialised from the exact FP64 column sums and updated only at
+// the columns an update changes, so its value never drifts by the FP32
+// rounding of large partial sums. Each row's atoms are a 256-byte record
+// {count, (j, t) x 31} in global memory, streamed into a shared-memory ring
+// RING-2 updates ahead (cp.async) by warp 0, which alone applies the update.
+// The dense plan T is kept exact by storing the changed entries.
+//
+// Per update: argmin pass (all threads) -> barrier -> warp 0: global argmin,
+// away vertex, decision, atom / T / q updates -> barrier.
+//
+// If a row would need more than 31 atoms, the kernel stops before changing
+// it and records the update index in *resume; the dense kernel then finishes
+// the epoch from there and the solve continues on the dense path.
+#include <limits>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+#include "step.cuh"
+
+namespace srot {
+
+namespace {
+
+constexpr int kSmemMax = 227 * 1024;
+
+struct SpRed {
+    uint32_t kmin;
+    int jmin;
+};
+
+__device__ inline void kahan_add(float &hi, float &lo, float d) {
+    float y = __fsub_rn(d, lo);
+    float t = __fadd_rn(hi, y);
+    lo = __fsub_rn(__fsub_rn(t, hi), y);
+    hi = t;
+}
+
+__device__ inline void cp16(void *smem_dst, const void *gsrc) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc));
+}
+__device__ inline void cp4(void *smem_dst, const void *gsrc) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc));
+}
+__device__ inline void commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ inline void wait_groups() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+}  // namespace
+
+template <int NTC, int G, bool PTS, int RING, bool PAIR>
+__global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_sparse(EpochArgs<float> A) {
+    constexpr int NWC = NTC / kWarp;  // compute warps; warp NWC is the control warp
+    constexpr int NT = NTC + kWarp;
+    constexpr int CPT = 4 * G;
+    constexpr int WID = NTC * CPT;
+    constexpr int D = RING - 2;
+    constexpr int K = kAtomRecord - 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *qh = reinterpret_cast<float *>(smem);
+    float *ql = qh + WID;
+    float4 *ys = reinterpret_cast<float4 *>(ql + WID);
+    float *cring = reinterpret_cast<float *>(ys + (PTS ? WID : 0));
+    int2 *aring = reinterpret_cast<int2 *>(cring + (PTS ? 0 : RING * WID));
+    SpRed(*red)[NWC] = reinterpret_cast<SpRed(*)[NWC]>(aring + RING * kAtomRecord);
+    int *sflag = reinterpret_cast<int *>(red + 2);
+
+    const int m = A.in.m, n = A.in.n;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool ctrl = warp == NWC;
+    const unsigned FULL = 0xffffffffu;
+    const float rho = (float)A.rho;
+    const int order = A.order;
+    const bool vec = A.vec;
+    int2 *grec = A.atoms;
+
+    // ---- one-time set-up: residual pair, point table, padding ------------
+    for (int j = tid; j < WID; j += NT) {
+        if (j < n) {
+            const double qq = A.q[j];
+            const float h = (float)qq;
+            qh[j] = h;
+            ql[j] = (float)((double)h - qq);  // value = qh - ql
+        } else {
+            qh[j] = 1e30f;
+            ql[j] = 0.f;
+        }
+        if (PTS)
+            ys[j] = j < n ? make_float4(A.in.Y[(size_t)j * 3], A.in.Y[(size_t)j * 3 + 1],
+                                        A.in.Y[(size_t)j * 3 + 2], 0.f)
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!PTS)
+            for (int s = 0; s < RING; ++s) cring[(size_t)s * WID + j] = 0.f;
+    }
+    if (tid == 0) {
+        sflag[0] = 0;
+        if (A.resume) *A.resume = -1;
+    }
+    // compute threads: negated target points of their columns, in pairs
+    float2 ny0[PTS ? 2 * G : 1], ny1[PTS ? 2 * G : 1], ny2[PTS ? 2 * G : 1];
+    if (PTS && !ctrl) {
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = 4 * (tid + NTC * g) + 2 * h;
+                const bool a0 = j < n, a1 = j + 1 < n;
+                ny0[2 * g + h] = make_float2(a0 ? -A.in.Y[(size_t)j * 3] : 0.f, a1 ? -A.in.Y[(size_t)(j + 1) * 3] : 0.f);
+                ny1[2 * g + h] = make_float2(a0 ? -A.in.Y[(size_t)j * 3 + 1] : 0.f, a1 ? -A.in.Y[(size_t)(j + 1) * 3 + 1] : 0.f);
+                ny2[2 * g + h] = make_float2(a0 ? -A.in.Y[(size_t)j * 3 + 2] : 0.f, a1 ? -A.in.Y[(size_t)(j + 1) * 3 + 2] : 0.f);
+            }
+    }
+    __syncthreads();
+
+    auto row_of = [&](int p) -> int {
+        if (p >= m) return -1;
+        if (order == SR_OT_CYCLIC) return p;
+        if (order == SR_OT_PERMUTE) return A.perm[p];
+        return scale_u64(sm64_draw(A.seed, 2, (uint64_t)(A.k0 + p)), m);
+    };
+    // control warp: atom record; compute threads: their quads of the cost row
+    auto fetch_async = [&](int i, int s) {
+        if (ctrl) {
+            if (lane < kAtomRecord / 2)
+                cp16(aring + (size_t)s * kAtomRecord + 2 * lane, grec + (size_t)i * kAtomRecord + 2 * lane);
+        } else if (!PTS) {
+            float *dst = cring + (size_t)s * WID;
+            const float *src = A.in.C + (size_t)i * n;
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const int j0 = 4 * (tid + NTC * g);
+                if (vec && j0 + 3 < n) cp16(dst + j0, src + j0);
+                else
+                    for (int e = 0; e < 4; ++e)
+                        if (j0 + e < n) cp4(dst + j0 + e, src + j0 + e);
+            }
+        }
+    };
+    auto fetch_sync_record = [&](int i, int s) {
+        aring[(size_t)s * kAtomRecord + lane] = grec[(size_t)i * kAtomRecord + lane];
+    };
+    auto fetch_sync_costs = [&](int i, int s) {
+        float *dst = cring + (size_t)s * WID;
+        const float *src = A.in.C + (size_t)i * n;
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int j = 4 * (tid + NTC * g) + e;
+                if (j < n) dst[j] = src[j];
+            }
+    };
+    // compute threads: the cost of their columns for row i (slot s when given)
+    float cst[CPT];
+    auto load_costs = [&](int i, int s, float x0, float x1, float x2) {
+        if (i < 0) return;
+        if (PTS) {
+            const float2 X0 = make_float2(x0, x0), X1 = make_float2(x1, x1), X2 = make_float2(x2, x2);
+#pragma unroll
+            for (int h = 0; h < 2 * G; ++h) {
+                const float2 d0 = __fadd2_rn(X0, ny0[h]), d1 = __fadd2_rn(X1, ny1[h]), d2 = __fadd2_rn(X2, ny2[h]);
+                float2 c = __fmul2_rn(d0, d0);
+                c = __ffma2_rn(d1, d1, c);
+                c = __ffma2_rn(d2, d2, c);
+                cst[2 * h] = c.x;
+                cst[2 * h + 1] = c.y;
+            }
+        } else {
+            const float *cs = cring + (size_t)s * WID;
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const float4 c4 = *reinterpret_cast<const float4 *>(cs + 4 * (tid + NTC * g));
+                cst[4 * g] = c4.x;
+                cst[4 * g + 1] = c4.y;
+                cst[4 * g + 2] = c4.z;
+                cst[4 * g + 3] = c4.w;
+            }
+        }
+    };
+    auto load_x = [&](int i, float &x0, float &x1, float &x2, float &ai) {
+        if (i < 0) return;
+        if (PTS) {
+            x0 = A.in.X[(size_t)i * 3];
+            x1 = A.in.X[(size_t)i * 3 + 1];
+            x2 = A.in.X[(size_t)i * 3 + 2];
+        }
+        ai = A.in.a[i];
+    };
+
+    const bool prefetchable = (order == SR_OT_CYCLIC || order == SR_OT_PERMUTE || order == SR_OT_UNIFORM);
+    // Pipelines: rq[t] = row of update p+t (t <= D+1), aq[t] = it travels by
+    // cp.async (t < D); x, a of the rows of updates p, p+1 (c, n).
+    int rq[D + 2];
+    bool aq[D + 1];
+#pragma unroll
+    for (int t = 0; t < D + 2; ++t) rq[t] = row_of(t);
+#pragma unroll
+    for (int t = 0; t < D; ++t) {
+        bool ok = prefetchable && rq[t] >= 0;
+#pragma unroll
+        for (int u = 0; u < t; ++u) ok = ok && rq[t] != rq[u];
+        aq[t] = ok;
+        if (ok) fetch_async(rq[t], t % RING);
+        commit();
+    }
+    float xc0 = 0.f, xc1 = 0.f, xc2 = 0.f, ac = 0.f, xn0 = 0.f, xn1 = 0.f, xn2 = 0.f, an = 0.f;
+    load_x(rq[0], xc0, xc1, xc2, ac);
+    load_x(rq[1], xn0, xn1, xn2, an);
+    if (!ctrl) {
+        if (!PTS) {
+            if (aq[0]) wait_groups<D - 1>();
+            else fetch_sync_costs(rq[0], 0);
+        }
+        load_costs(rq[0], 0, xc0, xc1, xc2);
+    }
+    int i_prev = -1, par = 0;
+    for (int p = 0; p < m; ++p) {
+        const long long k = A.k0 + p;
+        const int i = rq[0];
+        const int s_cur = p % RING;
+        {
+            bool ok = prefetchable && rq[D] >= 0 && rq[D] != i_prev;
+#pragma unroll
+            for (int u = 0; u < D; ++u) ok = ok && rq[D] != rq[u];
+            aq[D] = ok;
+            if (ok) fetch_async(rq[D], (p + D) % RING);
+            commit();
+        }
+        const int r_far = row_of(p + D + 2);
+        float xm0 = 0.f, xm1 = 0.f, xm2 = 0.f, am = 0.f;  // row of update p+2
+        load_x(rq[2 <= D + 1 ? 2 : D + 1], xm0, xm1, xm2, am);
+
+        // ---- phase 1: LMO argmin (compute warps) | away vertex (control) ---
+        int cnt = 0, jk = -1, v = 0x7FFFFFFF;
+        float tk = 0.f, gk = 0.f, t_v = 0.f, gmaxv = 0.f, s1 = 0.f, s2 = 0.f, gmx = 0.f, inv = 0.f;
+        bool have = false;
+        if (!ctrl) {
+            // per quad a two-level tree, then across quads; on equal values the
+            // lower column wins, so ties go to the smallest j overall
+            float qv[G];
+            int qj[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const int j0 = 4 * (tid + NTC * g);
+                const float4 q4 = *reinterpret_cast<const float4 *>(qh + j0);
+                const float2 ga = __fadd2_rn(make_float2(cst[4 * g], cst[4 * g + 1]), make_float2(q4.x, q4.y));
+                const float2 gb = __fadd2_rn(make_float2(cst[4 * g + 2], cst[4 * g + 3]), make_float2(q4.z, q4.w));
+                const bool ta = ga.y < ga.x, tb = gb.y < gb.x;
+                const float va = ta ? ga.y : ga.x, vb = tb ? gb.y : gb.x;
+                const int ia = j0 + (ta ? 1 : 0), ib = j0 + (tb ? 3 : 2);
+                const bool tq = vb < va;
+                qv[g] = tq ? vb : va;
+                qj[g] = tq ? ib : ia;
+            }
+#pragma unroll
+            for (int w = 1; w < G; w <<= 1)
+#pragma unroll
+                for (int g = 0; g + w < G; g += 2 * w)
+                    if (qv[g + w] < qv[g]) { qv[g] = qv[g + w]; qj[g] = qj[g + w]; }
+            const float gmin = qv[0];
+            const int jmin = qj[0];
+            const uint32_t km = f2key(gmin);
+            const uint32_t wk = __reduce_min_sync(FULL, km);
+            const int wj = __reduce_min_sync(FULL, km == wk ? jmin : 0x7FFFFFFF);
+            if (lane == 0) red[par][warp] = SpRed{wk, wj};
+        } else {
+            if (aq[0]) wait_groups<D>();
+            else fetch_sync_record(i, s_cur);
+            __syncwarp();
+            const int2 *rec = aring + (size_t)s_cur * kAtomRecord;
+            cnt = rec[0].x;
+            have = lane < cnt;
+            jk = have ? rec[1 + lane].x : -1;
+            tk = have ? __int_as_float(rec[1 + lane].y) : 0.f;
+            if (have) {
+                float c;
+                if (PTS) {
+                    const float4 y = ys[jk];
+                    const float d0 = xc0 - y.x, d1 = xc1 - y.y, d2 = xc2 - y.z;
+                    c = fmaf(d2, d2, fmaf(d1, d1, __fmul_rn(d0, d0)));
+                } else {
+                    c = __ldg(A.in.C + (size_t)i * n + jk);
+                }
+                gk = c + qh[jk];
+            }
+            // away vertex: argmax of the gradient over the active atoms
+            const uint32_t kx = have ? f2key(gk) : 0u;
+            const uint32_t wkx = __reduce_max_sync(FULL, kx);
+            v = __reduce_min_sync(FULL, (have && kx == wkx) ? jk : 0x7FFFFFFF);
+            const unsigned vmask = __ballot_sync(FULL, have && jk == v);
+            t_v = __shfl_sync(FULL, tk, vmask ? __ffs(vmask) - 1 : 0);
+            gmaxv = key2f(wkx);
+            if (!PAIR) {
+                s1 = warp_sum(have ? tk * gk : 0.f);
+                s2 = warp_sum(have ? tk * tk : 0.f);
+            }
+            // quantities of the step that do not depend on the LMO vertex
+            if (PAIR && ac > 0.f) {
+                gmx = t_v / ac;                            // gamma_max = alpha_v
+                inv = 1.f / (2.f * rho * ac);              // eq. 10 with d = a_i (e_j* - e_v)
+            }
+        }
+        __syncthreads();  // (A)
+
+        // ---- phase 2: decision and update (control) | next costs (compute) -
+        if (ctrl) {
+            const SpRed e = lane < NWC ? red[par][lane] : SpRed{0xFFFFFFFFu, 0x7FFFFFFF};
+            const uint32_t wk = __reduce_min_sync(FULL, e.kmin);
+            const int js = __reduce_min_sync(FULL, e.kmin == wk ? e.jmin : 0x7FFFFFFF);
+            const float gmin_all = key2f(wk);
+            const unsigned jsmask = __ballot_sync(FULL, have && jk == js);
+            const float t_js0 = __shfl_sync(FULL, tk, jsmask ? __ffs(jsmask) - 1 : 0);
+            const float t_js = jsmask ? t_js0 : 0.f;
+            Red<float> R;
+            R.gmin = gmin_all;
+            R.jmin = js;
+            R.gmax = gmaxv;
+            R.jmax = v;
+            R.nnz = cnt;
+            R.s1 = s1;
+            R.s2 = s2;
+            bool stop = false;
+            if (!isfinite(gmin_all)) {
+                if (lane == 0) {
+                    atomicCAS(A.status, 0, (int)kDevNonFinite);
+                    sflag[0] = 1;
+                }
+                stop = true;
+            }
+            Step<float> S{-1, 0.f, js, v, 1.f, 0.f, 0.f, false};
+            if (!stop) {
+                if (PAIR) {
+                    // pairwise step (Alg. A.3): move mass from v to j*
+                    if (ac > 0.f && v >= 0 && v < n) {
+                        S.kind = 2;
+                        if (v != js) {
+                            const float num = gmaxv - gmin_all;
+                            float gam = 0.f;
+                            if (num > 0.f) gam = rho > 0.f ? fminf(num * inv, gmx) : gmx;
+                            S.gamma = gam;
+                            S.drop = gam >= gmx;
+                            const float moved = S.drop ? t_v : gam * ac;
+                            S.add_js = moved;
+                            S.sub_v = moved;
+                        }
+                    }
+                } else {
+                    S = decide<float>(R, ac, t_js, t_v, A.variant, A.step, rho, m, k);
+                }
+            }
+            const bool grows = (S.kind == 0 || S.kind == 2) && S.add_js > 0.f;
+            const bool append = S.kind >= 0 && grows && !jsmask;
+            if (!stop && append && cnt >= K) {
+                if (lane == 0) {
+                    sflag[0] = 2;
+                    if (A.resume) *A.resume = p;
+                }
+                stop = true;
+            }
+            if (!stop && S.kind >= 0) {
+                const int jl = have ? jk : ((append && lane == cnt) ? js : -1);
+                const float told = have ? tk : 0.f;
+                float tnew = told;
+                if (jl >= 0) tnew = apply<float>(S, jl, told);
+                if (jl >= 0 && tnew != told) {
+                    A.T[(size_t)i * n + jl] = tnew;
+                    kahan_add(qh[jl], ql[jl], rho * (tnew - told));
+                }
+                const bool keep = jl >= 0 && tnew > 0.f;
+                const unsigned km = __ballot_sync(FULL, keep);
+                const int idx = __popc(km & ((1u << lane) - 1u));
+                int2 *g = grec + (size_t)i * kAtomRecord;
+                if (keep) g[1 + idx] = make_int2(jl, __float_as_int(tnew));
+                if (lane == 0) g[0] = make_int2(__popc(km), 0);
+            }
+            if (lane == 0 && A.trace && k < A.trace_cap) {
+                A.trace[4 * k] = i;
+                A.trace[4 * k + 1] = js;
+                A.trace[4 * k + 2] = (v >= 0 && v < n) ? v : -1;
+                A.trace[4 * k + 3] = __float_as_int(S.gamma);
+            }
+        } else if (p + 1 < m) {
+            if (!PTS) {
+                if (aq[1]) wait_groups<D - 1>();
+                else fetch_sync_costs(rq[1], (p + 1) % RING);
+            }
+            load_costs(rq[1], (p + 1) % RING, xn0, xn1, xn2);
+        }
+        par ^= 1;
+        __syncthreads();  // (B) residual, records and next costs ready
+        if (sflag[0]) break;
+        i_prev = i;
+#pragma unroll
+        for (int t = 0; t < D + 1; ++t) rq[t] = rq[t + 1];
+        rq[D + 1] = r_far;
+#pragma unroll
+        for (int t = 0; t < D; ++t) aq[t] = aq[t + 1];
+        xc0 = xn0; xc1 = xn1; xc2 = xn2; ac = an;
+        xn0 = xm0; xn1 = xm1; xn2 = xm2; an = am;
+    }
+    wait_groups<0>();
+    __syncthreads();
+    for (int j = tid; j < n; j += NT) A.q[j] = (double)qh[j] - (double)ql[j];
+}
+
+template <int NT, int G, bool PTS>
+static size_t sparse_smem(int ring) {
+    constexpr int WID = NT * 4 * G;  // NT: compute threads
+    size_t b = 2 * (size_t)WID * 4;             // qh, ql
+    if (PTS) b += (size_t)WID * 16;             // y table
+    else b += (size_t)ring * WID * 4;           // cost-row ring
+    b += (size_t)ring * kAtomRecord * 8;        // atom-record ring
+    b += 2 * (NT / kWarp) * sizeof(SpRed) + 16; // reduction slots, flag
+    return b;
+}
+
+template <int NT, int G, bool PTS, int RING, bool PAIR>
+static void launch_sp_ring(const EpochArgs<float> &A, cudaStream_t st) {
+    auto kern = k_epoch_sparse<NT, G, PTS, RING, PAIR>;
+    static bool attr_set = false;  // one attribute call per instantiation and process
+    if (!attr_set) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
+        attr_set = true;
+    }
+    kern<<<1, NT + kWarp, sparse_smem<NT, G, PTS>(RING), st>>>(A);
+}
+
+template <int NT, int G, bool PAIR>
+static void launch_sp_var(const EpochArgs<float> &A, cudaStream_t st) {
+    if (A.in.cost_mode == kCostPts3) {
+        launch_sp_ring<NT, G, true, 4, PAIR>(A, st);
+    } else {
+        if (sparse_smem<NT, G, false>(4) <= (size_t)kSmemMax) launch_sp_ring<NT, G, false, 4, PAIR>(A, st);
+        else launch_sp_ring<NT, G, false, 3, PAIR>(A, st);
+    }
+}
+
+template <int NT, int G>
+static void launch_sp(const EpochArgs<float> &A, cudaStream_t st) {
+    if (A.variant == SR_OT_BCPFW) launch_sp_var<NT, G, true>(A, st);
+    else launch_sp_var<NT, G, false>(A, st);
+}
+
+bool launch_epoch_sparse(const EpochArgs<float> &A, cudaStream_t st) {
+    const int n = A.in.n;
+    if (n <= 256 * 4) launch_sp<256, 1>(A, st);
+    else if (n <= 256 * 8) launch_sp<256, 2>(A, st);
+    else if (n <= 256 * 16) launch_sp<256, 4>(A, st);
+    else if (n <= 512 * 16) launch_sp<512, 4>(A, st);
+    else return false;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Atom records from a dense plan: one warp per row. *overflow is set when a
+// row has more than 31 positive entries.
+// ---------------------------------------------------------------------------
+__global__ void k_build_atoms(int m, int n, const float *__restrict__ T, int2 *__restrict__ rec,
+                              int *__restrict__ overflow) {
+    const int lane = threadIdx.x & 31;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    constexpr int K = kAtomRecord - 1;
+    for (int i = w; i < m; i += nw) {
+        const float *ti = T + (size_t)i * n;
+        int2 *g = rec + (size_t)i * kAtomRecord;
+        int cnt = 0;
+        for (int j0 = 0; j0 < n; j0 += 32) {
+            const int j = j0 + lane;
+            const float t = j < n ? ti[j] : 0.f;
+            const bool act = t > 0.f;
+            const unsigned mk = __ballot_sync(0xffffffffu, act);
+            const int pos = cnt + __popc(mk & ((1u << lane) - 1u));
+            if (act && pos < K) g[1 + pos] = make_int2(j, __float_as_int(t));
+            cnt += __popc(mk);
+        }
+        if (lane == 0) {
+            g[0] = make_int2(cnt < K ? cnt : K, 0);
+            if (cnt > K) atomicExch(overflow, 1);
+        }
+    }
+}
+
+void launch_build_atoms(int m, int n, const float *T, int2 *rec, int *overflow, cudaStream_t st) {
+    int blocks = std::min((m + 7) / 8, 152 * 4);
+    k_build_atoms<<<blocks, 256, 0, st>>>(m, n, T, rec, overflow);
+}
+
+}  // namespace srot

@@ -1,0 +1,140 @@
+// step.cuh -- the per-block decision shared by the dense and sparse epoch
+// kernels: exact line search (eq. 8, eq. 10), the choice between FW, away and
+// pairwise directions (Alg. 1, A.2, A.3), and the new value of one entry.
+#pragma once
+
+#include <type_traits>
+
+#include "common.cuh"
+
+namespace srot {
+
+// Squared-Euclidean cost of one (x_i, y_j) pair in d = 3. The FP32 form is
+// the one every FP32 kernel (solver, certificate) evaluates, so all of them
+// see the same cost matrix; the FP64 form uses the rounding order of the
+// plain definition (no contraction).
+__device__ inline float cost3(float x0, float x1, float x2, float y0, float y1, float y2) {
+    float d0 = x0 - y0, d1 = x1 - y1, d2 = x2 - y2;
+    return fmaf(d2, d2, fmaf(d1, d1, __fmul_rn(d0, d0)));
+}
+__device__ inline double cost3(double x0, double x1, double x2, double y0, double y1, double y2) {
+    double d0 = dsub(x0, y0), d1 = dsub(x1, y1), d2 = dsub(x2, y2);
+    return dadd(dadd(dmul(d0, d0), dmul(d1, d1)), dmul(d2, d2));
+}
+
+// Block-wide result of one reduction (identical in every thread).
+template <typename Real>
+struct Red {
+    Real gmin, s1, s2, gmax;
+    int jmin, jmax, nnz;
+};
+
+// Exact line search on phi(gamma) = -num gamma + (rho/2) dd gamma^2, [0, gmax].
+template <typename Real>
+__device__ inline Real line_search(Real num, Real dd, Real rho, Real gmax) {
+    if (!(num > Real(0))) return Real(0);
+    Real den = rho * dd;
+    if (!(den > Real(0))) return gmax;
+    Real g = num / den;
+    return g < gmax ? g : gmax;
+}
+
+// Decisions of one block update (identical in every thread).
+template <typename Real>
+struct Step {
+    int kind;        // -1 none, 0 FW convex combination, 1 away, 2 pairwise
+    Real gamma;
+    int js, v;
+    Real coef;       // FW: 1-gamma ; away: 1+gamma
+    Real add_js;     // value added at j* (FW: gamma a_i ; pairwise: moved mass)
+    Real sub_v;      // pairwise: moved mass ; away: gamma a_i
+    bool drop;
+};
+
+template <typename Real>
+__device__ inline Step<Real> decide(const Red<Real> &R, Real ai, Real t_js, Real t_v, int variant,
+                                    int step, Real rho, int m, long long k) {
+    Step<Real> S;
+    S.kind = -1; S.gamma = Real(0); S.js = R.jmin; S.v = R.jmax;
+    S.coef = Real(1); S.add_js = Real(0); S.sub_v = Real(0); S.drop = false;
+    if (!(ai > Real(0))) return S;
+    const Real g_fw = R.s1 - ai * R.gmin;
+    if (variant == SR_OT_BCFW) {
+        Real gam;
+        if (step == SR_OT_DEC) {
+            if constexpr (std::is_same<Real, double>::value)
+                gam = __ddiv_rn(2.0 * (double)m, (double)k + 2.0 * (double)m);
+            else
+                gam = (float)((2.0 * (double)m) / ((double)k + 2.0 * (double)m));
+        } else {
+            Real dd = (R.s2 - t_js * t_js) + (ai - t_js) * (ai - t_js);
+            gam = line_search<Real>(g_fw, dd > Real(0) ? dd : Real(0), rho, Real(1));
+        }
+        S.kind = 0; S.gamma = gam;
+        if constexpr (std::is_same<Real, double>::value) {
+            S.coef = dsub(1.0, gam);
+            S.add_js = dmul(gam, ai);
+        } else {
+            S.coef = 1.f - gam;
+            S.add_js = gam * ai;
+        }
+        return S;
+    }
+    if (S.v < 0 || S.v == 0x7FFFFFFF) return S;
+    if (variant == SR_OT_BCAFW) {
+        const Real g_aw = ai * R.gmax - R.s1;
+        if (R.nnz <= 1 || g_fw >= g_aw) {
+            Real dd = (R.s2 - t_js * t_js) + (ai - t_js) * (ai - t_js);
+            Real gam = line_search<Real>(g_fw, dd > Real(0) ? dd : Real(0), rho, Real(1));
+            S.kind = 0; S.gamma = gam; S.coef = Real(1) - gam; S.add_js = gam * ai;
+        } else {
+            Real alpha = t_v / ai;
+            Real gmax = alpha / (Real(1) - alpha);
+            Real dd = (R.s2 - t_v * t_v) + (t_v - ai) * (t_v - ai);
+            Real gam = line_search<Real>(g_aw, dd > Real(0) ? dd : Real(0), rho, gmax);
+            S.kind = 1; S.gamma = gam; S.coef = Real(1) + gam; S.sub_v = gam * ai;
+            S.drop = gam >= gmax;
+        }
+        return S;
+    }
+    // pairwise
+    if (S.v == S.js) { S.kind = 2; return S; }
+    Real g_pw = ai * (R.gmax - R.gmin);
+    Real gmax = t_v / ai;
+    Real gam = line_search<Real>(g_pw, Real(2) * ai * ai, rho, gmax);
+    S.kind = 2; S.gamma = gam;
+    S.drop = gam >= gmax;
+    Real moved = S.drop ? t_v : gam * ai;
+    S.add_js = moved; S.sub_v = moved;
+    return S;
+}
+
+// New value of one owned entry under step S.
+template <typename Real>
+__device__ inline Real apply(const Step<Real> &S, int j, Real t) {
+    if (S.kind == 0) {
+        Real tn;
+        if constexpr (std::is_same<Real, double>::value) {
+            tn = dmul(S.coef, t);
+            if (j == S.js) tn = dadd(tn, S.add_js);
+        } else {
+            tn = S.coef * t;
+            if (j == S.js) tn = tn + S.add_js;
+        }
+        return tn;
+    }
+    if (S.kind == 1) {
+        Real tn = S.coef * t;
+        if (j == S.v) tn = S.drop ? Real(0) : tn - S.sub_v;
+        return tn;
+    }
+    if (S.kind == 2) {
+        if (j == S.js) return t + S.add_js;
+        if (j == S.v) return S.drop ? Real(0) : t - S.sub_v;
+    }
+    return t;
+}
+
+
+
+}  // namespace srot

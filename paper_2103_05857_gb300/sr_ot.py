@@ -1,0 +1,198 @@
+"""ctypes binding of libsr_ot.so (include/sr_ot.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module only turns torch
+tensors into device pointers and host structs. Importing it loads the
+library and raises if it has not been built (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsr_ot.so")
+
+OK, NOT_CONVERGED = 0, 1
+EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENUMERIC, EUNSUPPORTED = -1, -2, -3, -4, -5, -6
+BCFW, BCAFW, BCPFW, FW = 0, 1, 2, 3
+CYCLIC, PERMUTE, UNIFORM, GAP_ADAPTIVE = 0, 1, 2, 3
+DEC, ELS = 0, 1
+FP64, FP32, FP32_BF16COST = 0, 1, 2
+
+EXPORTS = ["sr_ot_default_options", "sr_ot_create", "sr_ot_set_stream", "sr_ot_destroy",
+           "sr_ot_last_error", "sr_ot_solve", "sr_ot_solve_batched", "sr_ot_grad",
+           "sr_ot_grad_batched", "sr_ot_gap", "sr_ot_cost_bf16", "sr_ot_launch_count",
+           "sr_ot_profile_enable", "sr_ot_profile_read"]
+PROF_EPOCH, PROF_CERT, PROF_BATCH, PROF_GRAD, PROF_COST = 0, 1, 2, 3, 4
+
+
+class Options(ct.Structure):
+    _fields_ = [
+        ("variant", ct.c_int), ("order", ct.c_int), ("step", ct.c_int), ("precision", ct.c_int),
+        ("rho", ct.c_double), ("tol_rel_gap", ct.c_double), ("max_epochs", ct.c_longlong),
+        ("gap_every", ct.c_int), ("refresh_every", ct.c_int), ("ga_M", ct.c_int),
+        ("ga_global_only", ct.c_int), ("seed", ct.c_ulonglong), ("trace", ct.c_void_p),
+        ("trace_capacity", ct.c_longlong), ("dense_only", ct.c_int), ("reserved", ct.c_int),
+    ]
+
+
+class Result(ct.Structure):
+    _fields_ = [
+        ("objective", ct.c_double), ("gap", ct.c_double), ("rel_gap", ct.c_double),
+        ("dual", ct.c_double), ("epochs", ct.c_longlong), ("block_updates", ct.c_longlong),
+        ("status", ct.c_int), ("reserved", ct.c_int),
+    ]
+
+    def asdict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class SrOtError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"sr_ot status {status}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -m paper_2103_05857_gb300.build` (no CPU fallback exists)")
+    lib = ct.CDLL(LIB_PATH)
+    vp, i, ll, d = ct.c_void_p, ct.c_int, ct.c_longlong, ct.c_double
+    llp, ip = ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_int)
+    lib.sr_ot_default_options.argtypes = [ct.POINTER(Options)]
+    lib.sr_ot_default_options.restype = None
+    lib.sr_ot_create.argtypes = [ct.POINTER(vp), i, vp]
+    lib.sr_ot_set_stream.argtypes = [vp, vp]
+    lib.sr_ot_destroy.argtypes = [vp]
+    lib.sr_ot_last_error.argtypes = [vp]
+    lib.sr_ot_last_error.restype = ct.c_char_p
+    lib.sr_ot_solve.argtypes = [vp, ct.POINTER(Options), i, i, i, vp, vp, vp, vp, vp, vp, i,
+                                ct.POINTER(Result)]
+    lib.sr_ot_solve_batched.argtypes = [vp, ct.POINTER(Options), i, ip, ip, i, llp, llp, llp, llp,
+                                        llp, vp, vp, vp, vp, vp, ct.POINTER(Result)]
+    lib.sr_ot_grad.argtypes = [vp, ct.POINTER(Options), i, i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.sr_ot_grad_batched.argtypes = [vp, ct.POINTER(Options), i, ip, ip, i, llp, llp, llp, llp,
+                                       vp, vp, vp, vp, vp, vp, vp]
+    lib.sr_ot_gap.argtypes = [vp, ct.POINTER(Options), i, i, i, vp, vp, vp, vp, vp, vp, vp,
+                              ct.POINTER(Result)]
+    lib.sr_ot_cost_bf16.argtypes = [vp, i, i, i, vp, vp, vp]
+    lib.sr_ot_profile_enable.argtypes = [vp, i]
+    lib.sr_ot_profile_read.argtypes = [vp, i, ct.POINTER(d), ct.POINTER(ll)]
+    for name in EXPORTS:
+        fn = getattr(lib, name)
+        if name not in ("sr_ot_default_options", "sr_ot_last_error", "sr_ot_launch_count"):
+            fn.restype = ct.c_int
+    lib.sr_ot_launch_count.argtypes = [vp]
+    lib.sr_ot_launch_count.restype = ll
+    return lib
+
+
+lib = _load()
+
+
+def options(**kw) -> Options:
+    o = Options()
+    lib.sr_ot_default_options(ct.byref(o))
+    for k, v in kw.items():
+        if k == "trace":
+            o.trace = None if v is None else v.data_ptr()
+            continue
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ct.c_void_p(t.data_ptr())
+
+
+def _dtype_of(prec):
+    return torch.float64 if prec == FP64 else torch.float32
+
+
+class Handle:
+    """One library handle bound to a device and (by default) torch's current stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self._h = ct.c_void_p()
+        s = stream if stream is not None else torch.cuda.current_stream(device)
+        st = lib.sr_ot_create(ct.byref(self._h), int(device), ct.c_void_p(s.cuda_stream))
+        if st != OK:
+            raise SrOtError(st, lib.sr_ot_last_error(None).decode())
+        self.device = device
+
+    def close(self):
+        if self._h:
+            lib.sr_ot_destroy(self._h)
+            self._h = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, allow=(OK, NOT_CONVERGED)):
+        if st not in allow:
+            raise SrOtError(st, lib.sr_ot_last_error(self._h).decode())
+        return st
+
+    def set_stream(self, stream):
+        self._check(lib.sr_ot_set_stream(self._h, ct.c_void_p(stream.cuda_stream)))
+
+    def last_error(self) -> str:
+        return lib.sr_ot_last_error(self._h).decode()
+
+    def launch_count(self) -> int:
+        return int(lib.sr_ot_launch_count(self._h))
+
+    def profile(self, enable: bool = True):
+        self._check(lib.sr_ot_profile_enable(self._h, int(bool(enable))), allow=(OK,))
+
+    def profile_read(self, kind: int):
+        ms, groups = ct.c_double(), ct.c_longlong()
+        self._check(lib.sr_ot_profile_read(self._h, kind, ct.byref(ms), ct.byref(groups)), allow=(OK,))
+        return ms.value, groups.value
+
+    # -------------------------------------------------------------------
+    def solve(self, a, b, T, C=None, X=None, Y=None, warm_start=False, opts=None, **kw):
+        """sr_ot_solve. Returns the result dict; T is updated in place."""
+        o = opts if opts is not None else options(**kw)
+        m, n = T.shape
+        d = 0 if X is None else X.shape[1]
+        res = Result()
+        st = lib.sr_ot_solve(self._h, ct.byref(o), m, n, d, _ptr(C), _ptr(X), _ptr(Y), _ptr(a),
+                             _ptr(b), _ptr(T), int(bool(warm_start)), ct.byref(res))
+        self._check(st)
+        return res.asdict()
+
+    def solve_raw(self, a, b, T, C=None, X=None, Y=None, warm_start=False, opts=None, **kw):
+        """sr_ot_solve returning (status, result dict) without raising."""
+        o = opts if opts is not None else options(**kw)
+        m, n = T.shape
+        d = 0 if X is None else X.shape[1]
+        res = Result()
+        st = lib.sr_ot_solve(self._h, ct.byref(o), m, n, d, _ptr(C), _ptr(X), _ptr(Y), _ptr(a),
+                             _ptr(b), _ptr(T), int(bool(warm_start)), ct.byref(res))
+        return st, res.asdict()
+
+    def gap(self, a, b, T, C=None, X=None, Y=None, g_rows=None, opts=None, **kw):
+        """sr_ot_gap: certificate (f, g, w) of plan T."""
+        o = opts if opts is not None else options(**kw)
+        m, n = T.shape
+        d = 0 if X is None else X.shape[1]
+        res = Result()
+        st = lib.sr_ot_gap(self._h, ct.byref(o), m, n, d, _ptr(C), _ptr(X), _ptr(Y), _ptr(a),
+                           _ptr(b), _ptr(T), _ptr(g_rows), ct.byref(res))
+        self._check(st, allow=(OK,))
+        return res.asdict()
