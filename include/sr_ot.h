@@ -203,6 +203,33 @@ sr_ot_status sr_ot_cost_bf16(sr_ot_handle h, int m, int n, int d, const float *X
                              const float *Y, float *C);
 
 /*
+ * The certificate of sr_ot_gap for callers that cannot allocate memory: code
+ * inside a CUDA graph capture or under a caller-owned memory pool, embedded
+ * runtimes that own every allocation, real-time loops where an allocation
+ * (and the synchronisation it may imply) is not allowed. The paper has no
+ * counterpart; this is an interface of this library only.
+ *
+ * It takes no handle and allocates nothing: no cudaMalloc/cudaFree, no
+ * pinned buffer. Its scratch is a fixed 4 MiB array compiled into the
+ * library as a static __device__ variable, present on every device that
+ * loads the library until the process exits. It fits any m with n up to
+ * 208,000 columns; larger n fail with SR_OT_EUNSUPPORTED. The cost must be
+ * C or d = 3 points; precision SR_OT_FP64 or SR_OT_FP32.
+ *
+ * `device` must be the device the pointers live on; `cuda_stream` as in
+ * sr_ot_create. The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture. Every call reuses the same array and leaves its last contents
+ * there, so calls whose kernels overlap on the GPU race: serialise them.
+ * Arguments, outputs (res on the host, g_rows optional device doubles) and
+ * errors are as for sr_ot_gap; the error message is sr_ot_last_error(NULL).
+ */
+sr_ot_status sr_ot_gap_noalloc(int device, void *cuda_stream, const sr_ot_options *opts, int m,
+                               int n, int d, const void *C, const void *X, const void *Y,
+                               const void *a, const void *b, const void *T, double *g_rows,
+                               sr_ot_result *res);
+
+/*
  * Observability (not in the paper). sr_ot_launch_count: number of this
  * library's kernels launched on h since it was created. When profiling is
  * enabled, the library brackets each launch group on the handle's stream with

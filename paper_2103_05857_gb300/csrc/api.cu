@@ -33,6 +33,10 @@ thread_local std::string g_create_error;
 
 }  // namespace
 
+namespace srot {
+void set_handleless_error(const char *msg) { g_create_error = msg; }
+}  // namespace srot
+
 struct ProfPair {
     cudaEvent_t a, b;
     int kind;

@@ -121,4 +121,8 @@ bool launch_epoch(const EpochArgs<Real> &args, cudaStream_t st);
 
 int epoch_max_n(bool fp64);
 
+// Message returned by sr_ot_last_error(NULL) on this thread (errors of calls
+// that have no handle).
+void set_handleless_error(const char *msg);
+
 }  // namespace srot

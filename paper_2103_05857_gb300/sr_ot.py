@@ -24,7 +24,7 @@ FP64, FP32, FP32_BF16COST = 0, 1, 2
 EXPORTS = ["sr_ot_default_options", "sr_ot_create", "sr_ot_set_stream", "sr_ot_destroy",
            "sr_ot_last_error", "sr_ot_solve", "sr_ot_solve_batched", "sr_ot_grad",
            "sr_ot_grad_batched", "sr_ot_gap", "sr_ot_cost_bf16", "sr_ot_launch_count",
-           "sr_ot_profile_enable", "sr_ot_profile_read"]
+           "sr_ot_profile_enable", "sr_ot_profile_read", "sr_ot_gap_noalloc"]
 PROF_EPOCH, PROF_CERT, PROF_BATCH, PROF_GRAD, PROF_COST = 0, 1, 2, 3, 4
 
 
@@ -79,6 +79,8 @@ def _load():
     lib.sr_ot_gap.argtypes = [vp, ct.POINTER(Options), i, i, i, vp, vp, vp, vp, vp, vp, vp,
                               ct.POINTER(Result)]
     lib.sr_ot_cost_bf16.argtypes = [vp, i, i, i, vp, vp, vp]
+    lib.sr_ot_gap_noalloc.argtypes = [i, vp, ct.POINTER(Options), i, i, i, vp, vp, vp, vp, vp, vp,
+                                      vp, ct.POINTER(Result)]
     lib.sr_ot_profile_enable.argtypes = [vp, i]
     lib.sr_ot_profile_read.argtypes = [vp, i, ct.POINTER(d), ct.POINTER(ll)]
     for name in EXPORTS:
