@@ -104,6 +104,8 @@ typedef struct {
     double gap;               /* g(T) at return (Thm 2)                            */
     double rel_gap;           /* g / f                                             */
     double dual;              /* Lagrangian dual value w(T) = f - g (Thm 2)        */
+    double row_err;           /* max_i |sum_j T_ij - a_i| / a_i; the stopping test
+                                 also needs row_err <= 1e-5 (FP32 plans drift)    */
     long long epochs;         /* epochs (FW: iterations) performed                 */
     long long block_updates;  /* block updates performed                           */
     int status;               /* sr_ot_status of this solve                        */

@@ -7,10 +7,12 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
 #include "../../include/sr_ot.h"
+#include "batched.h"
 #include "common.cuh"
 #include "internal.h"
 
@@ -21,7 +23,8 @@ namespace {
 // Workspace slots owned by a handle; each grows on demand.
 enum WsSlot {
     WS_Q = 0, WS_PARTIAL, WS_R64, WS_RQ32, WS_COLPART, WS_ROWPART, WS_CERT, WS_PERM, WS_PERMKEY,
-    WS_PERMIDX, WS_GSTORE, WS_STATUS, WS_COST, WS_CHECK, WS_SCRATCH, WS_ATOMS, WS_COUNT
+    WS_PERMIDX, WS_GSTORE, WS_STATUS, WS_COST, WS_CHECK, WS_SCRATCH, WS_ATOMS, WS_B_INST,
+    WS_B_QUEUE, WS_B_HEAD, WS_B_RES, WS_B_ATOMS, WS_B_BAD, WS_COUNT
 };
 
 struct DevBuf {
@@ -57,6 +60,12 @@ struct sr_ot_ctx {
     std::vector<cudaEvent_t> event_pool;
     double prof_ms[SR_OT_PROF_KINDS] = {0, 0, 0, 0, 0};
     long long prof_groups[SR_OT_PROF_KINDS] = {0, 0, 0, 0, 0};
+    // batched solves: side streams for concurrent tile launches, the tile
+    // chosen per size bucket by the autotuner, captured graphs per shape set
+    cudaStream_t side[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev_fork = nullptr, ev_join[4] = {nullptr, nullptr, nullptr, nullptr};
+    std::map<long long, int> tuned_tile;
+    std::map<unsigned long long, cudaGraphExec_t> graphs;
 };
 
 namespace {
@@ -256,7 +265,7 @@ sr_ot_status cert_work(sr_ot_handle h, int m, int n, CertWork *w) {
     if ((st = ws_typed(h, WS_R64, (size_t)n, &w->r64))) return st;
     if ((st = ws_typed(h, WS_RQ32, (size_t)n, &w->rq32))) return st;
     if ((st = ws_typed(h, WS_COLPART, (size_t)2 * ncolb, &w->colpart))) return st;
-    if ((st = ws_typed(h, WS_ROWPART, (size_t)2 * nrowb, &w->rowpart))) return st;
+    if ((st = ws_typed(h, WS_ROWPART, (size_t)3 * nrowb, &w->rowpart))) return st;
     if ((st = ws_typed(h, WS_CERT, (size_t)kCertCount, &w->cert))) return st;
     return SR_OT_OK;
 }
@@ -268,6 +277,7 @@ void fill_result(sr_ot_result *res, const double *cert, long long epochs, long l
     res->gap = cert[kCertG];
     res->rel_gap = cert[kCertRel];
     res->dual = cert[kCertW];
+    res->row_err = cert[kCertFeas];
     res->epochs = epochs;
     res->block_updates = updates;
     res->status = status;
@@ -395,7 +405,7 @@ sr_ot_status solve_impl(sr_ot_handle h, const sr_ot_options *o, int m, int n, in
     // row fits its atom record; an overflow hands the rest of the solve to
     // the dense kernel.
     bool use_sparse = false;
-    int2 *atoms = nullptr;
+    int4 *atoms = nullptr;
     if constexpr (std::is_same<Real, float>::value) {
         if ((o->variant == SR_OT_BCAFW || o->variant == SR_OT_BCPFW) && !o->dense_only &&
             n <= epoch_max_n(false)) {
@@ -530,6 +540,285 @@ sr_ot_status check_sizes(sr_ot_handle h, int m, int n) {
     return SR_OT_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Batched solve
+// ---------------------------------------------------------------------------
+// Size buckets by n and the tile shapes the autotuner tries for each.
+constexpr int kNumBuckets = 4;
+const int kBucketMaxN[kNumBuckets] = {256, 512, 1024, 2048};
+const std::vector<int> kBucketTiles[kNumBuckets] = {{0, 1, 2}, {1, 2, 3}, {3, 4}, {5, 6}};
+
+int bucket_of(int n) {
+    for (int k = 0; k < kNumBuckets; ++k)
+        if (n <= kBucketMaxN[k]) return k;
+    return -1;
+}
+
+__global__ void k_batch_check(const BatchInst *inst, int batch, const float *X, const float *Y,
+                              const float *a, const float *b, int *bad) {
+    for (int k = blockIdx.x; k < batch; k += gridDim.x) {
+        const BatchInst I = inst[k];
+        int c = 0;
+        for (int e = threadIdx.x; e < I.m; e += blockDim.x) {
+            const float v = a[I.off_a + e];
+            c += !(isfinite(v) && v >= 0.f);
+            for (int t = 0; t < 3; ++t) c += !isfinite(X[I.off_X + 3 * (long long)e + t]);
+        }
+        for (int e = threadIdx.x; e < I.n; e += blockDim.x) {
+            const float v = b[I.off_b + e];
+            c += !(isfinite(v) && v >= 0.f);
+            for (int t = 0; t < 3; ++t) c += !isfinite(Y[I.off_Y + 3 * (long long)e + t]);
+        }
+        if (c) atomicAdd(&bad[k], c);
+    }
+}
+
+sr_ot_status ensure_side_streams(sr_ot_handle h) {
+    if (h->ev_fork) return SR_OT_OK;
+    for (int k = 0; k < 4; ++k) {
+        CK(h, cudaStreamCreateWithFlags(&h->side[k], cudaStreamNonBlocking));
+        CK(h, cudaEventCreateWithFlags(&h->ev_join[k], cudaEventDisableTiming));
+    }
+    CK(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    return SR_OT_OK;
+}
+
+sr_ot_status solve_batched_impl(sr_ot_handle h, const sr_ot_options *o, int batch, const int *m,
+                                const int *n, int d, const long long *off_X, const long long *off_Y,
+                                const long long *off_a, const long long *off_b,
+                                const long long *off_T, const float *X, const float *Y,
+                                const float *a, const float *b, float *T, sr_ot_result *res) {
+    if (batch <= 0) return fail(h, SR_OT_EINVAL, "batch must be >= 1");
+    if (!m || !n || !off_X || !off_Y || !off_a || !off_b || !off_T || !res)
+        return fail(h, SR_OT_EINVAL, "size, offset and result arrays must be non-NULL");
+    if (!X || !Y || !a || !b || !T) return fail(h, SR_OT_EINVAL, "X, Y, a, b, T must be non-NULL");
+    if (d != 3) return fail(h, SR_OT_EUNSUPPORTED, "batched solves take points with d = 3 (got %d)", d);
+    if (o->precision != SR_OT_FP32) return fail(h, SR_OT_EUNSUPPORTED, "batched solves run in SR_OT_FP32");
+    if (o->variant == SR_OT_FW) return fail(h, SR_OT_EUNSUPPORTED, "batched solves run the block-coordinate variants");
+    if (o->order == SR_OT_GAP_ADAPTIVE) return fail(h, SR_OT_EUNSUPPORTED, "batched solves take cyclic, permuted or uniform order");
+    sr_ot_status st;
+    // ---- descriptors, size checks, buckets --------------------------------
+    std::vector<BatchInst> inst(batch);
+    std::vector<std::vector<int>> buckets(kNumBuckets);
+    std::vector<int> solo;  // instances solved one at a time (n above the tile widths)
+    long long atoms_total = 0;
+    for (int k = 0; k < batch; ++k) {
+        if (m[k] <= 0 || n[k] <= 0) return fail(h, SR_OT_EINVAL, "instance %d: m and n must be >= 1", k);
+        if (off_X[k] < 0 || off_Y[k] < 0 || off_a[k] < 0 || off_b[k] < 0 || off_T[k] < 0)
+            return fail(h, SR_OT_EINVAL, "instance %d: negative offset", k);
+        if (o->order == SR_OT_PERMUTE && m[k] > 2048)
+            return fail(h, SR_OT_EUNSUPPORTED, "instance %d: permuted order in a batch needs m <= 2048", k);
+        inst[k] = BatchInst{m[k], n[k], off_X[k], off_Y[k], off_a[k], off_b[k], off_T[k], atoms_total};
+        atoms_total += (long long)m[k] * kAtomRecord;
+        const int bk = bucket_of(n[k]);
+        if (bk < 0) solo.push_back(k);
+        else buckets[bk].push_back(k);
+    }
+    for (auto &bq : buckets)
+        std::stable_sort(bq.begin(), bq.end(), [&](int x, int y) {
+            return (long long)m[x] * n[x] > (long long)m[y] * n[y];
+        });
+    BatchInst *d_inst;
+    int *d_queue, *d_head, *d_bad;
+    BatchResult *d_res;
+    int4 *d_atoms;
+    if ((st = ws_typed(h, WS_B_INST, (size_t)batch, &d_inst))) return st;
+    if ((st = ws_typed(h, WS_B_QUEUE, (size_t)batch, &d_queue))) return st;
+    if ((st = ws_typed(h, WS_B_HEAD, (size_t)kNumBuckets, &d_head))) return st;
+    if ((st = ws_typed(h, WS_B_RES, (size_t)batch, &d_res))) return st;
+    if ((st = ws_typed(h, WS_B_BAD, (size_t)batch, &d_bad))) return st;
+    if ((st = ws_typed(h, WS_B_ATOMS, (size_t)std::max(atoms_total, 1LL), &d_atoms))) return st;
+    std::vector<int> queue;
+    std::vector<int> qstart(kNumBuckets + 1, 0);
+    for (int bk = 0; bk < kNumBuckets; ++bk) {
+        qstart[bk] = (int)queue.size();
+        queue.insert(queue.end(), buckets[bk].begin(), buckets[bk].end());
+    }
+    qstart[kNumBuckets] = (int)queue.size();
+    CK(h, cudaMemcpyAsync(d_inst, inst.data(), sizeof(BatchInst) * batch, cudaMemcpyHostToDevice, h->stream));
+    if (!queue.empty())
+        CK(h, cudaMemcpyAsync(d_queue, queue.data(), sizeof(int) * queue.size(), cudaMemcpyHostToDevice, h->stream));
+    // ---- input checks ------------------------------------------------------
+    CK(h, cudaMemsetAsync(d_bad, 0, sizeof(int) * batch, h->stream));
+    k_batch_check<<<std::min(batch, 152 * 4), 256, 0, h->stream>>>(d_inst, batch, X, Y, a, b, d_bad);
+    h->launches += 1;
+    CKL(h);
+    {
+        std::vector<int> bad(batch);
+        CK(h, cudaMemcpyAsync(bad.data(), d_bad, sizeof(int) * batch, cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        for (int k = 0; k < batch; ++k)
+            if (bad[k]) return fail(h, SR_OT_EINVAL, "instance %d: %d negative or non-finite entries in a, b, X or Y", k, bad[k]);
+    }
+    if ((st = ensure_side_streams(h))) return st;
+
+    BatchArgs base;
+    base.inst = d_inst;
+    base.X = X;
+    base.Y = Y;
+    base.a = a;
+    base.b = b;
+    base.T = T;
+    base.atoms = d_atoms;
+    base.res = d_res;
+    base.rho = o->rho;
+    base.tol = o->tol_rel_gap;
+    base.max_epochs = o->max_epochs;
+    base.gap_every = o->gap_every;
+    base.variant = o->variant;
+    base.order = o->order;
+    base.step = o->step;
+    base.seed = o->seed;
+    int sms = 152;
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    auto args_for = [&](int bk, int tile) {
+        BatchArgs B = base;
+        B.queue = d_queue + qstart[bk];
+        B.queue_len = qstart[bk + 1] - qstart[bk];
+        B.queue_head = d_head + bk;
+        return B;
+    };
+    auto grid_for = [&](int bk, int tile) {
+        const int len = qstart[bk + 1] - qstart[bk];
+        return std::max(1, std::min(len, sms * batch_tile_ctas_per_sm(tile)));
+    };
+    // ---- autotune the tile of each bucket (first call per bucket and rule) --
+    for (int bk = 0; bk < kNumBuckets; ++bk) {
+        if (buckets[bk].empty()) continue;
+        const long long key = bk * 64 + o->variant * 8 + o->step;
+        if (h->tuned_tile.count(key)) continue;
+        int best = kBucketTiles[bk][0];
+        if (kBucketTiles[bk].size() > 1) {
+            double best_rate = -1.0;
+            for (int tile : kBucketTiles[bk]) {
+                BatchArgs B = args_for(bk, tile);
+                B.max_epochs = 1;
+                B.tol = 0.0;
+                B.gap_every = 1;
+                cudaEvent_t e0 = prof_event(h), e1 = prof_event(h);
+                CK(h, cudaMemsetAsync(d_head + bk, 0, sizeof(int), h->stream));
+                CK(h, cudaEventRecord(e0, h->stream));
+                launch_batched_tile(tile, B, grid_for(bk, tile), h->stream);
+                h->launches += 1;
+                CK(h, cudaEventRecord(e1, h->stream));
+                CKL(h);
+                CK(h, cudaStreamSynchronize(h->stream));
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                h->event_pool.push_back(e0);
+                h->event_pool.push_back(e1);
+                long long upd = 0;
+                for (int k : buckets[bk]) upd += m[k];
+                const double rate = upd / std::max(1e-6, (double)ms);
+                if (rate > best_rate) { best_rate = rate; best = tile; }
+            }
+        }
+        h->tuned_tile[key] = best;
+    }
+    // ---- the solve: one graph per shape set ----------------------------------
+    unsigned long long hsh = 1469598103934665603ULL;
+    auto mix = [&](unsigned long long v) { hsh = (hsh ^ v) * 1099511628211ULL; };
+    mix((unsigned long long)batch);
+    for (int k = 0; k < batch; ++k) {
+        mix((unsigned long long)m[k]); mix((unsigned long long)n[k]);
+        mix((unsigned long long)off_X[k]); mix((unsigned long long)off_Y[k]); mix((unsigned long long)off_a[k]);
+        mix((unsigned long long)off_b[k]); mix((unsigned long long)off_T[k]);
+    }
+    mix((uintptr_t)X); mix((uintptr_t)Y); mix((uintptr_t)a); mix((uintptr_t)b); mix((uintptr_t)T);
+    mix((uintptr_t)d_inst); mix((uintptr_t)d_atoms); mix((uintptr_t)d_res);
+    mix((uintptr_t)d_queue); mix((uintptr_t)d_head);
+    unsigned long long ob[8];
+    std::memcpy(ob, o, std::min(sizeof(ob), sizeof(*o)));
+    for (unsigned long long w : ob) mix(w);
+    cudaGraphExec_t exec = nullptr;
+    auto it = h->graphs.find(hsh);
+    if (it != h->graphs.end()) {
+        exec = it->second;
+    } else {
+        // Captured on the handle's own stream (capture is not allowed on the
+        // legacy default stream); the graph is then launched on the caller's.
+        cudaGraph_t graph;
+        cudaStream_t origin = h->side[0];
+        CK(h, cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal));
+        cudaMemsetAsync(d_head, 0, sizeof(int) * kNumBuckets, origin);
+        cudaEventRecord(h->ev_fork, origin);
+        int used = 0;
+        for (int bk = 0; bk < kNumBuckets; ++bk) {
+            if (buckets[bk].empty()) continue;
+            const int tile = h->tuned_tile[bk * 64 + o->variant * 8 + o->step];
+            cudaStream_t s = h->side[used];
+            if (used > 0) cudaStreamWaitEvent(s, h->ev_fork, 0);
+            launch_batched_tile(tile, args_for(bk, tile), grid_for(bk, tile), s);
+            if (used > 0) cudaEventRecord(h->ev_join[used], s);
+            ++used;
+        }
+        for (int k = 1; k < used; ++k) cudaStreamWaitEvent(origin, h->ev_join[k], 0);
+        cudaError_t ce = cudaStreamEndCapture(origin, &graph);
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, SR_OT_ECUDA, "graph capture of the batched solve failed: %s", cudaGetErrorString(ce));
+        }
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, SR_OT_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ce));
+        }
+        h->graphs[hsh] = exec;
+    }
+    {
+        ProfScope ps(h, SR_OT_PROF_BATCH);
+        CK(h, cudaGraphLaunch(exec, h->stream));
+    }
+    int nlaunch = 0;
+    for (int bk = 0; bk < kNumBuckets; ++bk) nlaunch += !buckets[bk].empty();
+    h->launches += nlaunch;
+    std::vector<BatchResult> hres(batch);
+    CK(h, cudaMemcpyAsync(hres.data(), d_res, sizeof(BatchResult) * batch, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    prof_collect(h);
+    // ---- fill results; dense or oversize instances one at a time ------------
+    sr_ot_status worst = SR_OT_OK;
+    auto account = [&](sr_ot_status s) {
+        if (s < 0 && (worst >= 0 || s < worst)) worst = s;
+        else if (s == SR_OT_NOT_CONVERGED && worst == SR_OT_OK) worst = s;
+    };
+    for (int k = 0; k < batch; ++k) {
+        if (bucket_of(n[k]) < 0) continue;
+        const BatchResult &r = hres[k];
+        sr_ot_result &o2 = res[k];
+        o2.objective = r.f;
+        o2.gap = r.g;
+        o2.rel_gap = r.f != 0.0 ? r.g / r.f : 0.0;
+        o2.dual = r.f - r.g;
+        o2.row_err = r.feas;
+        o2.epochs = r.epochs;
+        o2.block_updates = r.updates;
+        o2.reserved = 0;
+        o2.status = r.status == kInstOk ? SR_OT_OK
+                  : r.status == kInstNotConverged ? SR_OT_NOT_CONVERGED
+                  : r.status == kInstNonFinite ? SR_OT_ENUMERIC : SR_OT_OK;
+        if (r.status == kInstNeedsDense) solo.push_back(k);
+        else account((sr_ot_status)o2.status);
+    }
+    for (int k : solo) {
+        sr_ot_options o1 = *o;
+        o1.dense_only = bucket_of(n[k]) >= 0 ? 1 : o->dense_only;
+        o1.trace = nullptr;
+        o1.trace_capacity = 0;
+        sr_ot_status s = solve_impl<float>(h, &o1, m[k], n[k], 3, nullptr, X + off_X[k], Y + off_Y[k],
+                                           a + off_a[k], b + off_b[k], T + off_T[k], 0, &res[k]);
+        if (s < 0) res[k].status = s;
+        account(s);
+    }
+    return worst;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -599,6 +888,12 @@ sr_ot_status sr_ot_destroy(sr_ot_handle h) {
     if (h->h_check) cudaFreeHost(h->h_check);
     for (auto &p : h->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto e : h->event_pool) cudaEventDestroy(e);
+    for (auto &g : h->graphs) cudaGraphExecDestroy(g.second);
+    for (int k = 0; k < 4; ++k) {
+        if (h->side[k]) cudaStreamDestroy(h->side[k]);
+        if (h->ev_join[k]) cudaEventDestroy(h->ev_join[k]);
+    }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     delete h;
     return SR_OT_OK;
 }
@@ -644,7 +939,14 @@ sr_ot_status sr_ot_solve_batched(sr_ot_handle h, const sr_ot_options *opts, int 
                                  const long long *off_T, const void *X, const void *Y, const void *a,
                                  const void *b, void *T, sr_ot_result *res) {
     if (!h) return fail(nullptr, SR_OT_EINVAL, "handle is NULL");
-    return fail(h, SR_OT_EUNSUPPORTED, "batched solve is not available in this build");
+    h->err.clear();
+    sr_ot_status st;
+    if ((st = check_opts(h, opts))) return st;
+    if ((st = check_stream_device(h))) return st;
+    return solve_batched_impl(h, opts, batch, m, n, d, off_X, off_Y, off_a, off_b, off_T,
+                              static_cast<const float *>(X), static_cast<const float *>(Y),
+                              static_cast<const float *>(a), static_cast<const float *>(b),
+                              static_cast<float *>(T), res);
 }
 
 sr_ot_status sr_ot_grad(sr_ot_handle h, const sr_ot_options *opts, int m, int n, int d,

@@ -1,0 +1,174 @@
+// atoms.cuh -- the control warp of the active-set kernels: one row's atom
+// record (active set S_i with double-float weights, up to 63 atoms, two per
+// lane), the away vertex, the step decision and the update of atoms,
+// residual and dense plan. Shared by the single-instance and batched kernels.
+#pragma once
+
+#include "common.cuh"
+#include "internal.h"
+#include "step.cuh"
+
+namespace srot {
+
+// Record layout: entry 0 = {count, 0, 0, 0}; entry 1+k = atom k =
+// {column, weight hi bits, weight lo bits, 0}. Lane l holds atoms l (slot 0)
+// and 32+l (slot 1).
+constexpr int kAtomsMax = kAtomRecord - 1;
+
+struct LaneAtoms {
+    int cnt;
+    int j[2];
+    DF t[2];
+    float g[2];
+};
+
+// Load lane-local atoms from a record in shared or global memory.
+__device__ inline LaneAtoms load_atoms(const int4 *rec, int lane) {
+    LaneAtoms A;
+    A.cnt = rec[0].x;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const int k = lane + 32 * s;
+        const bool have = k < A.cnt;
+        const int4 e = rec[1 + (k < kAtomsMax ? k : 0)];
+        A.j[s] = have ? e.x : -1;
+        A.t[s] = have ? DF{__int_as_float(e.y), __int_as_float(e.z)} : DF{0.f, 0.f};
+        A.g[s] = 0.f;
+    }
+    return A;
+}
+
+// Gradient statistics over the atoms (see AtomStats). grad(j) evaluates the
+// row gradient of column j; ai is the row weight.
+template <typename GradF>
+__device__ inline AtomStats atom_stats(LaneAtoms &A, GradF grad, float ai, bool want_sums, DF *t_v_df) {
+    const unsigned FULL = 0xffffffffu;
+    uint32_t kx = 0u;
+    int jx = 0x7FFFFFFF;
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+        if (A.j[s] >= 0) {
+            A.g[s] = grad(A.j[s]);
+            const uint32_t kk = f2key(A.g[s]);
+            if (kk > kx || (kk == kx && A.j[s] < jx)) { kx = kk; jx = A.j[s]; }
+        }
+    AtomStats S;
+    const uint32_t wkx = __reduce_max_sync(FULL, kx);
+    S.v = __reduce_min_sync(FULL, kx == wkx ? jx : 0x7FFFFFFF);
+    S.gmax = key2f(wkx);
+    S.nnz = A.cnt;
+    DF tv{0.f, 0.f};
+    int vl = -1;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const unsigned mk = __ballot_sync(FULL, A.j[s] >= 0 && A.j[s] == S.v);
+        if (mk) vl = 32 * s + __ffs(mk) - 1;
+    }
+    {
+        const int src = vl >= 0 ? (vl & 31) : 0, sl = vl >> 5;  // vl is warp-uniform
+        const float h0 = __shfl_sync(FULL, A.t[0].hi, src), h1 = __shfl_sync(FULL, A.t[1].hi, src);
+        const float l0 = __shfl_sync(FULL, A.t[0].lo, src), l1 = __shfl_sync(FULL, A.t[1].lo, src);
+        if (vl >= 0) tv = sl ? DF{h1, l1} : DF{h0, l0};
+    }
+    *t_v_df = tv;
+    S.t_v = tv.hi;
+    S.g_aw = S.s2 = S.dda = 0.f;
+    if (want_sums) {
+        float aw = 0.f, s2 = 0.f, dd = 0.f;
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+            if (A.j[s] >= 0) {
+                const float t = A.t[s].hi;
+                aw += t * (S.gmax - A.g[s]);
+                s2 += t * t;
+                const float dv = (A.j[s] == S.v) ? t - ai : t;
+                dd += dv * dv;
+            }
+        S.g_aw = warp_sum(aw);
+        S.s2 = warp_sum(s2);
+        S.dda = warp_sum(dd);
+    }
+    return S;
+}
+
+// Weight of column js among the atoms (0 if absent) and whether it is one.
+__device__ inline float atom_weight(const LaneAtoms &A, int js, bool *present) {
+    const unsigned FULL = 0xffffffffu;
+    int where = -1;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const unsigned mk = __ballot_sync(FULL, A.j[s] >= 0 && A.j[s] == js);
+        if (mk) where = 32 * s + __ffs(mk) - 1;
+    }
+    const int src = where >= 0 ? (where & 31) : 0;
+    const float h0 = __shfl_sync(FULL, A.t[0].hi, src), h1 = __shfl_sync(FULL, A.t[1].hi, src);
+    *present = where >= 0;
+    return where < 0 ? 0.f : ((where >> 5) ? h1 : h0);
+}
+
+// Apply step S of row i: atoms (with j* appended when it enters), dense
+// plan entries, residual pair (qh, ql); writes the compacted record back to
+// grec. Returns false (and changes nothing) if j* would be atom 64.
+__device__ inline bool apply_atoms(const Step<float> &S, LaneAtoms &A, bool js_present, DF t_v, float ai,
+                                   float rho, float *trow, float *qh, float *ql, int4 *grec, int lane) {
+    const unsigned FULL = 0xffffffffu;
+    if (S.kind < 0) return true;
+    const bool grows = (S.kind == 0 || S.kind == 2) && S.add_js > 0.f;
+    const bool append = grows && !js_present;
+    if (append && A.cnt >= kAtomsMax) return false;
+    const DF mv = (S.kind == 2 && S.drop) ? t_v : DF{S.add_js, 0.f};
+    bool keep[2];
+    DF tn[2];
+    int jl[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const int k = lane + 32 * s;
+        jl[s] = A.j[s];
+        DF told = A.t[s];
+        if (append && k == A.cnt) {
+            jl[s] = S.js;
+            told = DF{0.f, 0.f};
+        }
+        tn[s] = told;
+        if (jl[s] >= 0) {
+            tn[s] = apply_atom(S, jl[s], told, mv, ai);
+            if (tn[s].hi != told.hi || tn[s].lo != told.lo) {
+                trow[jl[s]] = tn[s].hi;
+                const float dlt = __fadd_rn(__fsub_rn(tn[s].hi, told.hi), __fsub_rn(tn[s].lo, told.lo));
+                const float d = rho * dlt;
+                const float y = __fsub_rn(d, ql[jl[s]]);
+                const float tt = __fadd_rn(qh[jl[s]], y);
+                ql[jl[s]] = __fsub_rn(__fsub_rn(tt, qh[jl[s]]), y);
+                qh[jl[s]] = tt;
+            }
+        }
+        keep[s] = jl[s] >= 0 && tn[s].hi > 0.f;
+    }
+    const unsigned k0 = __ballot_sync(FULL, keep[0]), k1 = __ballot_sync(FULL, keep[1]);
+    const unsigned lt = (1u << lane) - 1u;
+    if (keep[0]) grec[1 + __popc(k0 & lt)] = make_int4(jl[0], __float_as_int(tn[0].hi), __float_as_int(tn[0].lo), 0);
+    if (keep[1]) grec[1 + __popc(k0) + __popc(k1 & lt)] = make_int4(jl[1], __float_as_int(tn[1].hi), __float_as_int(tn[1].lo), 0);
+    if (lane == 0) grec[0] = make_int4(__popc(k0) + __popc(k1), 0, 0, 0);
+    return true;
+}
+
+// Pairwise step (Alg. A.3) from the away statistics: gmx = t_v / a_i and
+// inv = 1 / (2 rho a_i) computed before the LMO vertex is known.
+__device__ inline Step<float> decide_pairwise(const AtomStats &st, float gmin, int js, float ai, float rho,
+                                              float gmx, float inv, int n) {
+    Step<float> S{-1, 0.f, js, st.v, 1.f, 0.f, 0.f, false};
+    if (!(ai > 0.f) || st.v < 0 || st.v >= n) return S;
+    S.kind = 2;
+    if (st.v == js) return S;
+    const float num = st.gmax - gmin;
+    float gam = 0.f;
+    if (num > 0.f) gam = rho > 0.f ? fminf(num * inv, gmx) : gmx;
+    S.gamma = gam;
+    S.drop = gam >= gmx;
+    const float moved = S.drop ? st.t_v : gam * ai;
+    S.add_js = moved;
+    S.sub_v = moved;
+    return S;
+}
+
+}  // namespace srot

@@ -144,13 +144,13 @@ k_gap_rows(Inst<Real> in, const Real *__restrict__ T, double rho, const double *
            const float *__restrict__ rq32, double *__restrict__ g_rows, double *__restrict__ rowpart) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n = in.n;
-    double acc_tc = 0.0, acc_amin = 0.0;  // lane 0 of each warp accumulates its rows
+    double acc_tc = 0.0, acc_amin = 0.0, acc_feas = 0.0;  // lane 0 of each warp accumulates its rows
     for (int i = blockIdx.x * kRowWarps + warp; i < in.m; i += gridDim.x * kRowWarps) {
         const Real *ti = T + (size_t)i * n;
-        double tc_row, tr_row;
+        double tc_row, tr_row, rs_row;
         int jb;
         if constexpr (std::is_same<Real, float>::value) {
-            Kahan32 tc, tr;
+            Kahan32 tc, tr, rs;
             float tc_err = 0.f;
             uint32_t kb = 0xFFFFFFFFu;
             jb = 0x7FFFFFFF;
@@ -160,6 +160,7 @@ k_gap_rows(Inst<Real> in, const Real *__restrict__ T, double rho, const double *
                 uint32_t k = f2key(c + __ldg(rq32 + j));
                 if (k < kb || jb == 0x7FFFFFFF) { kb = k; jb = j; }
                 if (t != 0.f) {
+                    rs.add(t);
                     float p = __fmul_rn(t, c);
                     tc_err += fmaf(t, c, -p);  // exact rounding error of p (TwoProduct)
                     tc.add(p);
@@ -170,8 +171,9 @@ k_gap_rows(Inst<Real> in, const Real *__restrict__ T, double rho, const double *
             jb = __reduce_min_sync(0xffffffffu, kb == wk ? jb : 0x7FFFFFFF);
             tc_row = warp_sum(tc.value() + (double)tc_err);
             tr_row = warp_sum(tr.value());
+            rs_row = warp_sum(rs.value());
         } else {
-            double tc = 0.0, tr = 0.0, gb = 0.0;
+            double tc = 0.0, tr = 0.0, gb = 0.0, rs = 0.0;
             jb = 0x7FFFFFFF;
             for (int j = lane; j < n; j += kWarp) {
                 double t = __ldg(ti + j);
@@ -180,6 +182,7 @@ k_gap_rows(Inst<Real> in, const Real *__restrict__ T, double rho, const double *
                 if (jb == 0x7FFFFFFF || g < gb) { gb = g; jb = j; }
                 tc += t * c;
                 tr += t * __ldg(r64 + j);
+                rs += t;
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -191,6 +194,7 @@ k_gap_rows(Inst<Real> in, const Real *__restrict__ T, double rho, const double *
             }
             tc_row = warp_sum(tc);
             tr_row = warp_sum(tr);
+            rs_row = warp_sum(rs);
         }
         if (lane == 0) {
             double ai = (double)in.a[i];
@@ -198,35 +202,44 @@ k_gap_rows(Inst<Real> in, const Real *__restrict__ T, double rho, const double *
             double gmin = (jb >= 0 && jb < n) ? (double)cost_at<Real>(in, i, jb) + rho * r64[jb] : NAN;
             acc_tc += tc_row;
             acc_amin += ai * gmin;
+            const double dfe = fabs(rs_row - ai) / (ai > 0.0 ? ai : 1e-300);
+            acc_feas = fmax(acc_feas, dfe);
             if (g_rows) g_rows[i] = tc_row + rho * tr_row - ai * gmin;
         }
     }
-    __shared__ double sh[2][kRowWarps];
-    if (lane == 0) { sh[0][warp] = acc_tc; sh[1][warp] = acc_amin; }
+    __shared__ double sh[3][kRowWarps];
+    if (lane == 0) { sh[0][warp] = acc_tc; sh[1][warp] = acc_amin; sh[2][warp] = acc_feas; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double a0 = 0.0, a1 = 0.0;
-        for (int w = 0; w < kRowWarps; ++w) { a0 += sh[0][w]; a1 += sh[1][w]; }
-        rowpart[2 * blockIdx.x + 0] = a0;
-        rowpart[2 * blockIdx.x + 1] = a1;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        for (int w = 0; w < kRowWarps; ++w) { a0 += sh[0][w]; a1 += sh[1][w]; a2 = fmax(a2, sh[2][w]); }
+        rowpart[3 * blockIdx.x + 0] = a0;
+        rowpart[3 * blockIdx.x + 1] = a1;
+        rowpart[3 * blockIdx.x + 2] = a2;
     }
 }
 
 __global__ void __launch_bounds__(kFinalThreads)
 k_cert_final(const double *__restrict__ colpart, int ncol, const double *__restrict__ rowpart,
              int nrow, double rho, double tol, double *__restrict__ cert) {
-    double rr = 0.0, sr = 0.0, tc = 0.0, am = 0.0;
+    double rr = 0.0, sr = 0.0, tc = 0.0, am = 0.0, fe = 0.0;
     for (int k = threadIdx.x; k < ncol; k += kFinalThreads) {
         rr += colpart[2 * k];
         sr += colpart[2 * k + 1];
     }
     for (int k = threadIdx.x; k < nrow; k += kFinalThreads) {
-        tc += rowpart[2 * k];
-        am += rowpart[2 * k + 1];
+        tc += rowpart[3 * k];
+        am += rowpart[3 * k + 1];
+        fe = fmax(fe, rowpart[3 * k + 2]);
     }
     block_sum2(rr, sr);
     block_sum2(tc, am);
+    __shared__ double shf[32];
+    for (int o = 16; o > 0; o >>= 1) fe = fmax(fe, __shfl_xor_sync(0xffffffffu, fe, o));
+    if ((threadIdx.x & 31) == 0) shf[threadIdx.x >> 5] = fe;
+    __syncthreads();
     if (threadIdx.x == 0) {
+        for (int w = 0; w < kFinalThreads / 32; ++w) fe = fmax(fe, shf[w]);
         double lin = tc, pen = 0.5 * rho * rr;
         double f = lin + pen;
         double g = lin + rho * sr - am;
@@ -236,7 +249,8 @@ k_cert_final(const double *__restrict__ colpart, int ncol, const double *__restr
         cert[kCertLin] = lin;
         cert[kCertPen] = pen;
         cert[kCertRel] = (f != 0.0) ? g / f : (g == 0.0 ? 0.0 : INFINITY);
-        cert[kCertStop] = (tol > 0.0 && g <= tol * f) ? 1.0 : 0.0;
+        cert[kCertFeas] = fe;
+        cert[kCertStop] = (tol > 0.0 && g <= tol * f && fe <= kFeasTol) ? 1.0 : 0.0;
     }
 }
 

@@ -20,7 +20,8 @@ enum CertSlot : int {
     kCertLin = 3,    // <C, T>
     kCertPen = 4,    // (rho/2) ||T^T 1 - b||^2
     kCertRel = 5,    // g / f
-    kCertStop = 6,   // 1.0 when g <= tol * f
+    kCertStop = 6,   // 1.0 when g <= tol * f and the plan is feasible
+    kCertFeas = 7,   // max_i |sum_j T_ij - a_i| / a_i (row-sum defect)
     kCertCount = 8
 };
 
@@ -36,6 +37,10 @@ struct Inst {
     const Real *b;
 };
 
+// A plan counts as feasible for the stopping test when every row sum is
+// within this relative distance of a_i (FP32 plans drift by rounding).
+constexpr double kFeasTol = 1e-5;
+
 // Workspace the certificate needs (all device pointers).
 struct CertWork {
     double *partial;     // nchunks * n
@@ -44,7 +49,7 @@ struct CertWork {
     float *rq32;         // n: (float)(rho * r) for the FP32 argmin
     double *colpart;     // per-block partials of the column pass (2 per block)
     int ncolblocks;
-    double *rowpart;     // per-block partials of the row pass (3 per block)
+    double *rowpart;     // per-block partials of the row pass (3 per block: <C,T>, sum a min, max defect)
     int nrowblocks;
     double *cert;        // kCertCount doubles
 };
@@ -100,20 +105,21 @@ struct EpochArgs {
     long long trace_cap;
     int *status;
     bool vec;                // T (and C) rows start on 16-byte boundaries
-    int2 *atoms;             // sparse kernel: per-row atom records (m x kAtomRecord)
+    int4 *atoms;             // sparse kernel: per-row atom records (m x kAtomRecord)
     int *resume;             // sparse kernel: set to the update index where it stopped
     const int *resume_in;    // dense kernel: start at *resume_in, or return if it is < 0
 };
 
-// Atom record of one row for the sparse kernel: {count, 0} then up to 31
-// (column, value bits) pairs; 256 bytes.
-constexpr int kAtomRecord = 32;
+// Atom record of one row for the active-set kernels: entry 0 = {count, 0, 0,
+// 0}, then up to 63 entries {column, weight hi bits, weight lo bits, 0}
+// (double-float weights); 1 KiB.
+constexpr int kAtomRecord = 64;
 
 // Sparse-support epoch (FP32, away / pairwise steps). False if n is too large.
 bool launch_epoch_sparse(const EpochArgs<float> &args, cudaStream_t st);
 
-// Atom records of a dense plan; *overflow becomes 1 if a row has > 31 atoms.
-void launch_build_atoms(int m, int n, const float *T, int2 *rec, int *overflow, cudaStream_t st);
+// Atom records of a dense plan; *overflow becomes 1 if a row has > 63 atoms.
+void launch_build_atoms(int m, int n, const float *T, int4 *rec, int *overflow, cudaStream_t st);
 
 // Returns false when n exceeds the single-instance kernel's limit.
 template <typename Real>

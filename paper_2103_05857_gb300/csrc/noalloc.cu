@@ -131,7 +131,7 @@ sr_ot_status gap_noalloc(int device, cudaStream_t st, const sr_ot_options *o, in
     cert_work_shape(m, n, &w.nchunks, &w.rows_per_chunk, &w.ncolblocks, &w.nrowblocks);
     const size_t need = rounded((size_t)w.nchunks * n * sizeof(double)) + rounded((size_t)n * sizeof(double)) +
                         rounded((size_t)n * sizeof(float)) + rounded((size_t)2 * w.ncolblocks * sizeof(double)) +
-                        rounded((size_t)2 * w.nrowblocks * sizeof(double)) +
+                        rounded((size_t)3 * w.nrowblocks * sizeof(double)) +
                         rounded(kCertCount * sizeof(double)) + rounded(4 * sizeof(int));
     if (need > kNoAllocScratchBytes)
         return nfail(SR_OT_EUNSUPPORTED,
@@ -146,7 +146,7 @@ sr_ot_status gap_noalloc(int device, cudaStream_t st, const sr_ot_options *o, in
     w.r64 = carve<double>(cur, n);
     w.rq32 = carve<float>(cur, n);
     w.colpart = carve<double>(cur, (size_t)2 * w.ncolblocks);
-    w.rowpart = carve<double>(cur, (size_t)2 * w.nrowblocks);
+    w.rowpart = carve<double>(cur, (size_t)3 * w.nrowblocks);
     w.cert = carve<double>(cur, kCertCount);
     int *bad = carve<int>(cur, 4);
 
@@ -180,6 +180,7 @@ sr_ot_status gap_noalloc(int device, cudaStream_t st, const sr_ot_options *o, in
         res->gap = cert[kCertG];
         res->rel_gap = cert[kCertRel];
         res->dual = cert[kCertW];
+        res->row_err = cert[kCertFeas];
         res->epochs = 0;
         res->block_updates = 0;
         res->status = SR_OT_OK;

@@ -14,21 +14,23 @@
 // q = rho (T^T 1 - b) lives in shared memory as a compensated FP32 pair
 // (qh, ql), initialised from the exact FP64 column sums and updated only at
 // the columns an update changes, so its value never drifts by the FP32
-// rounding of large partial sums. Each row's atoms are a 256-byte record
-// {count, (j, t) x 31} in global memory, streamed into a shared-memory ring
-// RING-2 updates ahead (cp.async) by warp 0, which alone applies the update.
-// The dense plan T is kept exact by storing the changed entries.
+// rounding of large partial sums. Each row's atoms are a 1 KiB record
+// {count, (j, t) x 63} with double-float weights (so steps conserve the row's
+// mass) in global memory, streamed into a shared-memory ring RING-2 updates
+// ahead (cp.async) by a control warp, which alone applies the update. The
+// dense plan T is kept exact by storing the changed entries.
 //
 // Per update: argmin pass (all threads) -> barrier -> warp 0: global argmin,
 // away vertex, decision, atom / T / q updates -> barrier.
 //
-// If a row would need more than 31 atoms, the kernel stops before changing
+// If a row would need more than 63 atoms, the kernel stops before changing
 // it and records the update index in *resume; the dense kernel then finishes
 // the epoch from there and the solve continues on the dense path.
 #include <limits>
 
 #include <algorithm>
 
+#include "atoms.cuh"
 #include "common.cuh"
 #include "internal.h"
 #include "step.cuh"
@@ -43,13 +45,6 @@ struct SpRed {
     uint32_t kmin;
     int jmin;
 };
-
-__device__ inline void kahan_add(float &hi, float &lo, float d) {
-    float y = __fsub_rn(d, lo);
-    float t = __fadd_rn(hi, y);
-    lo = __fsub_rn(__fsub_rn(t, hi), y);
-    hi = t;
-}
 
 __device__ inline void cp16(void *smem_dst, const void *gsrc) {
     unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
@@ -72,13 +67,12 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_sparse(EpochArgs<float
     constexpr int CPT = 4 * G;
     constexpr int WID = NTC * CPT;
     constexpr int D = RING - 2;
-    constexpr int K = kAtomRecord - 1;
     extern __shared__ __align__(16) unsigned char smem[];
     float *qh = reinterpret_cast<float *>(smem);
     float *ql = qh + WID;
     float4 *ys = reinterpret_cast<float4 *>(ql + WID);
     float *cring = reinterpret_cast<float *>(ys + (PTS ? WID : 0));
-    int2 *aring = reinterpret_cast<int2 *>(cring + (PTS ? 0 : RING * WID));
+    int4 *aring = reinterpret_cast<int4 *>(cring + (PTS ? 0 : RING * WID));
     SpRed(*red)[NWC] = reinterpret_cast<SpRed(*)[NWC]>(aring + RING * kAtomRecord);
     int *sflag = reinterpret_cast<int *>(red + 2);
 
@@ -89,7 +83,7 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_sparse(EpochArgs<float
     const float rho = (float)A.rho;
     const int order = A.order;
     const bool vec = A.vec;
-    int2 *grec = A.atoms;
+    int4 *grec = A.atoms;
 
     // ---- one-time set-up: residual pair, point table, padding ------------
     for (int j = tid; j < WID; j += NT) {
@@ -138,8 +132,8 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_sparse(EpochArgs<float
     // control warp: atom record; compute threads: their quads of the cost row
     auto fetch_async = [&](int i, int s) {
         if (ctrl) {
-            if (lane < kAtomRecord / 2)
-                cp16(aring + (size_t)s * kAtomRecord + 2 * lane, grec + (size_t)i * kAtomRecord + 2 * lane);
+            cp16(aring + (size_t)s * kAtomRecord + lane, grec + (size_t)i * kAtomRecord + lane);
+            cp16(aring + (size_t)s * kAtomRecord + 32 + lane, grec + (size_t)i * kAtomRecord + 32 + lane);
         } else if (!PTS) {
             float *dst = cring + (size_t)s * WID;
             const float *src = A.in.C + (size_t)i * n;
@@ -155,6 +149,7 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_sparse(EpochArgs<float
     };
     auto fetch_sync_record = [&](int i, int s) {
         aring[(size_t)s * kAtomRecord + lane] = grec[(size_t)i * kAtomRecord + lane];
+        aring[(size_t)s * kAtomRecord + 32 + lane] = grec[(size_t)i * kAtomRecord + 32 + lane];
     };
     auto fetch_sync_costs = [&](int i, int s) {
         float *dst = cring + (size_t)s * WID;
@@ -248,9 +243,10 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_sparse(EpochArgs<float
         load_x(rq[2 <= D + 1 ? 2 : D + 1], xm0, xm1, xm2, am);
 
         // ---- phase 1: LMO argmin (compute warps) | away vertex (control) ---
-        int cnt = 0, jk = -1, v = 0x7FFFFFFF;
-        float tk = 0.f, gk = 0.f, t_v = 0.f, gmaxv = 0.f, s1 = 0.f, s2 = 0.f, gmx = 0.f, inv = 0.f;
-        bool have = false;
+        LaneAtoms at;
+        AtomStats st;
+        DF t_vdf{0.f, 0.f};
+        float gmx = 0.f, inv = 0.f;
         if (!ctrl) {
             // per quad a two-level tree, then across quads; on equal values the
             // lower column wins, so ties go to the smallest j overall
@@ -284,37 +280,23 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_sparse(EpochArgs<float
             if (aq[0]) wait_groups<D>();
             else fetch_sync_record(i, s_cur);
             __syncwarp();
-            const int2 *rec = aring + (size_t)s_cur * kAtomRecord;
-            cnt = rec[0].x;
-            have = lane < cnt;
-            jk = have ? rec[1 + lane].x : -1;
-            tk = have ? __int_as_float(rec[1 + lane].y) : 0.f;
-            if (have) {
+            at = load_atoms(aring + (size_t)s_cur * kAtomRecord, lane);
+            auto grad = [&](int j) -> float {
                 float c;
                 if (PTS) {
-                    const float4 y = ys[jk];
+                    const float4 y = ys[j];
                     const float d0 = xc0 - y.x, d1 = xc1 - y.y, d2 = xc2 - y.z;
                     c = fmaf(d2, d2, fmaf(d1, d1, __fmul_rn(d0, d0)));
                 } else {
-                    c = __ldg(A.in.C + (size_t)i * n + jk);
+                    c = __ldg(A.in.C + (size_t)i * n + j);
                 }
-                gk = c + qh[jk];
-            }
-            // away vertex: argmax of the gradient over the active atoms
-            const uint32_t kx = have ? f2key(gk) : 0u;
-            const uint32_t wkx = __reduce_max_sync(FULL, kx);
-            v = __reduce_min_sync(FULL, (have && kx == wkx) ? jk : 0x7FFFFFFF);
-            const unsigned vmask = __ballot_sync(FULL, have && jk == v);
-            t_v = __shfl_sync(FULL, tk, vmask ? __ffs(vmask) - 1 : 0);
-            gmaxv = key2f(wkx);
-            if (!PAIR) {
-                s1 = warp_sum(have ? tk * gk : 0.f);
-                s2 = warp_sum(have ? tk * tk : 0.f);
-            }
-            // quantities of the step that do not depend on the LMO vertex
+                return c + qh[j];
+            };
+            st = atom_stats(at, grad, ac, !PAIR, &t_vdf);
+            // quantities of the pairwise step that do not depend on the LMO vertex
             if (PAIR && ac > 0.f) {
-                gmx = t_v / ac;                            // gamma_max = alpha_v
-                inv = 1.f / (2.f * rho * ac);              // eq. 10 with d = a_i (e_j* - e_v)
+                gmx = st.t_v / ac;                 // gamma_max = alpha_v
+                inv = 1.f / (2.f * rho * ac);      // eq. 10 with d = a_i (e_j* - e_v)
             }
         }
         __syncthreads();  // (A)
@@ -325,17 +307,8 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_sparse(EpochArgs<float
             const uint32_t wk = __reduce_min_sync(FULL, e.kmin);
             const int js = __reduce_min_sync(FULL, e.kmin == wk ? e.jmin : 0x7FFFFFFF);
             const float gmin_all = key2f(wk);
-            const unsigned jsmask = __ballot_sync(FULL, have && jk == js);
-            const float t_js0 = __shfl_sync(FULL, tk, jsmask ? __ffs(jsmask) - 1 : 0);
-            const float t_js = jsmask ? t_js0 : 0.f;
-            Red<float> R;
-            R.gmin = gmin_all;
-            R.jmin = js;
-            R.gmax = gmaxv;
-            R.jmax = v;
-            R.nnz = cnt;
-            R.s1 = s1;
-            R.s2 = s2;
+            bool present = false;
+            const float t_js = atom_weight(at, js, &present);
             bool stop = false;
             if (!isfinite(gmin_all)) {
                 if (lane == 0) {
@@ -344,56 +317,21 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_sparse(EpochArgs<float
                 }
                 stop = true;
             }
-            Step<float> S{-1, 0.f, js, v, 1.f, 0.f, 0.f, false};
-            if (!stop) {
-                if (PAIR) {
-                    // pairwise step (Alg. A.3): move mass from v to j*
-                    if (ac > 0.f && v >= 0 && v < n) {
-                        S.kind = 2;
-                        if (v != js) {
-                            const float num = gmaxv - gmin_all;
-                            float gam = 0.f;
-                            if (num > 0.f) gam = rho > 0.f ? fminf(num * inv, gmx) : gmx;
-                            S.gamma = gam;
-                            S.drop = gam >= gmx;
-                            const float moved = S.drop ? t_v : gam * ac;
-                            S.add_js = moved;
-                            S.sub_v = moved;
-                        }
-                    }
-                } else {
-                    S = decide<float>(R, ac, t_js, t_v, A.variant, A.step, rho, m, k);
-                }
-            }
-            const bool grows = (S.kind == 0 || S.kind == 2) && S.add_js > 0.f;
-            const bool append = S.kind >= 0 && grows && !jsmask;
-            if (!stop && append && cnt >= K) {
+            Step<float> S{-1, 0.f, js, st.v, 1.f, 0.f, 0.f, false};
+            if (!stop)
+                S = PAIR ? decide_pairwise(st, gmin_all, js, ac, rho, gmx, inv, n)
+                         : decide_atoms(st, gmin_all, js, t_js, ac, A.variant, A.step, rho, m, k);
+            if (!stop && !apply_atoms(S, at, present, t_vdf, ac, rho, A.T + (size_t)i * n, qh, ql,
+                                      grec + (size_t)i * kAtomRecord, lane)) {
                 if (lane == 0) {
-                    sflag[0] = 2;
+                    sflag[0] = 2;  // j* would be a 64th atom: the dense kernel takes over here
                     if (A.resume) *A.resume = p;
                 }
-                stop = true;
-            }
-            if (!stop && S.kind >= 0) {
-                const int jl = have ? jk : ((append && lane == cnt) ? js : -1);
-                const float told = have ? tk : 0.f;
-                float tnew = told;
-                if (jl >= 0) tnew = apply<float>(S, jl, told);
-                if (jl >= 0 && tnew != told) {
-                    A.T[(size_t)i * n + jl] = tnew;
-                    kahan_add(qh[jl], ql[jl], rho * (tnew - told));
-                }
-                const bool keep = jl >= 0 && tnew > 0.f;
-                const unsigned km = __ballot_sync(FULL, keep);
-                const int idx = __popc(km & ((1u << lane) - 1u));
-                int2 *g = grec + (size_t)i * kAtomRecord;
-                if (keep) g[1 + idx] = make_int2(jl, __float_as_int(tnew));
-                if (lane == 0) g[0] = make_int2(__popc(km), 0);
             }
             if (lane == 0 && A.trace && k < A.trace_cap) {
                 A.trace[4 * k] = i;
                 A.trace[4 * k + 1] = js;
-                A.trace[4 * k + 2] = (v >= 0 && v < n) ? v : -1;
+                A.trace[4 * k + 2] = (st.v >= 0 && st.v < n) ? st.v : -1;
                 A.trace[4 * k + 3] = __float_as_int(S.gamma);
             }
         } else if (p + 1 < m) {
@@ -426,7 +364,7 @@ static size_t sparse_smem(int ring) {
     size_t b = 2 * (size_t)WID * 4;             // qh, ql
     if (PTS) b += (size_t)WID * 16;             // y table
     else b += (size_t)ring * WID * 4;           // cost-row ring
-    b += (size_t)ring * kAtomRecord * 8;        // atom-record ring
+    b += (size_t)ring * kAtomRecord * 16;       // atom-record ring (1 KiB per slot)
     b += 2 * (NT / kWarp) * sizeof(SpRed) + 16; // reduction slots, flag
     return b;
 }
@@ -470,9 +408,9 @@ bool launch_epoch_sparse(const EpochArgs<float> &A, cudaStream_t st) {
 
 // ---------------------------------------------------------------------------
 // Atom records from a dense plan: one warp per row. *overflow is set when a
-// row has more than 31 positive entries.
+// row has more than 63 positive entries.
 // ---------------------------------------------------------------------------
-__global__ void k_build_atoms(int m, int n, const float *__restrict__ T, int2 *__restrict__ rec,
+__global__ void k_build_atoms(int m, int n, const float *__restrict__ T, int4 *__restrict__ rec,
                               int *__restrict__ overflow) {
     const int lane = threadIdx.x & 31;
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -480,7 +418,7 @@ __global__ void k_build_atoms(int m, int n, const float *__restrict__ T, int2 *_
     constexpr int K = kAtomRecord - 1;
     for (int i = w; i < m; i += nw) {
         const float *ti = T + (size_t)i * n;
-        int2 *g = rec + (size_t)i * kAtomRecord;
+        int4 *g = rec + (size_t)i * kAtomRecord;
         int cnt = 0;
         for (int j0 = 0; j0 < n; j0 += 32) {
             const int j = j0 + lane;
@@ -488,17 +426,17 @@ __global__ void k_build_atoms(int m, int n, const float *__restrict__ T, int2 *_
             const bool act = t > 0.f;
             const unsigned mk = __ballot_sync(0xffffffffu, act);
             const int pos = cnt + __popc(mk & ((1u << lane) - 1u));
-            if (act && pos < K) g[1 + pos] = make_int2(j, __float_as_int(t));
+            if (act && pos < K) g[1 + pos] = make_int4(j, __float_as_int(t), 0, 0);
             cnt += __popc(mk);
         }
         if (lane == 0) {
-            g[0] = make_int2(cnt < K ? cnt : K, 0);
+            g[0] = make_int4(cnt < K ? cnt : K, 0, 0, 0);
             if (cnt > K) atomicExch(overflow, 1);
         }
     }
 }
 
-void launch_build_atoms(int m, int n, const float *T, int2 *rec, int *overflow, cudaStream_t st) {
+void launch_build_atoms(int m, int n, const float *T, int4 *rec, int *overflow, cudaStream_t st) {
     int blocks = std::min((m + 7) / 8, 152 * 4);
     k_build_atoms<<<blocks, 256, 0, st>>>(m, n, T, rec, overflow);
 }

@@ -137,4 +137,107 @@ __device__ inline Real apply(const Step<Real> &S, int j, Real t) {
 
 
 
+// Double-float values hi + lo (|lo| <= ulp(hi)/2) for the atom weights of the
+// active-set kernels: a pairwise step adds and subtracts the same amount, and
+// in this representation it does so exactly enough that a row's mass does not
+// drift over many thousands of steps. Round-to-nearest intrinsics throughout
+// (never contracted or reordered).
+struct DF {
+    float hi, lo;
+};
+__device__ inline DF df_norm(float s, float e) {
+    const float h = __fadd_rn(s, e);
+    return DF{h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ inline DF df_add(DF x, DF y) {
+    const float s = __fadd_rn(x.hi, y.hi);
+    const float bb = __fsub_rn(s, x.hi);
+    float e = __fadd_rn(__fsub_rn(x.hi, __fsub_rn(s, bb)), __fsub_rn(y.hi, bb));
+    e = __fadd_rn(e, __fadd_rn(x.lo, y.lo));
+    return df_norm(s, e);
+}
+__device__ inline DF df_mulf(DF x, float c) {
+    const float p = __fmul_rn(x.hi, c);
+    float e = __fmaf_rn(x.hi, c, -p);
+    e = __fmaf_rn(x.lo, c, e);
+    return df_norm(p, e);
+}
+
+// Exact product x * y of two floats as a double-float (TwoProduct).
+__device__ inline DF df_prod(float x, float y) {
+    const float p = __fmul_rn(x, y);
+    return DF{p, __fmaf_rn(x, y, -p)};
+}
+
+// New weight of atom column j under step S (the atom-list form of apply()).
+// The convex-combination steps are evaluated as t - gamma t (+ gamma a_i at
+// j*) and t + gamma t (- gamma a_i at v), with gamma a_i an exact product, so
+// that the rounding of 1 -/+ gamma never enters: the row's mass changes by
+// gamma (a_i - sum t) + O(eps^2), as it does in exact arithmetic (where it is
+// 0). ai is the row weight; mv is the mass a pairwise step moves (the whole
+// away atom on a drop step).
+__device__ inline DF apply_atom(const Step<float> &S, int j, DF t, DF mv, float ai) {
+    if (S.kind == 0) {
+        const DF gt = df_mulf(t, S.gamma);
+        DF r = df_add(t, DF{-gt.hi, -gt.lo});
+        if (j == S.js) r = df_add(r, df_prod(S.gamma, ai));
+        return r;
+    }
+    if (S.kind == 1) {
+        if (j == S.v && S.drop) return DF{0.f, 0.f};
+        DF r = df_add(t, df_mulf(t, S.gamma));
+        if (j == S.v) {
+            const DF ga = df_prod(S.gamma, ai);
+            r = df_add(r, DF{-ga.hi, -ga.lo});
+        }
+        return r;
+    }
+    if (S.kind == 2) {
+        if (j == S.js) return df_add(t, mv);
+        if (j == S.v) return S.drop ? DF{0.f, 0.f} : df_add(t, DF{-mv.hi, -mv.lo});
+    }
+    return t;
+}
+
+// Row quantities the control warp of the active-set kernels gathers over the
+// atoms before the LMO vertex is known. With gmax the largest gradient over
+// the active atoms (away vertex v):
+//   g_aw = sum_k t_k (gmax - g_k) >= 0            (away-direction decrease)
+//   s2   = sum_k t_k^2,  dda = ||t - a e_v||^2    (sums of squares)
+// Because the atom weights sum to a_i, the FW gap follows without the
+// cancellation of sum t g - a gmin:  g_fw = a (gmax - gmin) - g_aw.
+struct AtomStats {
+    float gmax, g_aw, s2, dda, t_v;
+    int v, nnz;
+};
+
+// Decision of one block update from the atom statistics (Alg. 1 / A.2 with
+// the line search of eq. 8 / eq. 10; pairwise steps are decided separately).
+__device__ inline Step<float> decide_atoms(const AtomStats &A, float gmin, int js, float t_js, float ai,
+                                           int variant, int step, float rho, int m, long long k) {
+    Step<float> S;
+    S.kind = -1; S.gamma = 0.f; S.js = js; S.v = A.v;
+    S.coef = 1.f; S.add_js = 0.f; S.sub_v = 0.f; S.drop = false;
+    if (!(ai > 0.f)) return S;
+    const float g_fw = ai * (A.gmax - gmin) - A.g_aw;
+    const bool fw = variant == SR_OT_BCFW || A.nnz <= 1 || g_fw >= A.g_aw;
+    if (fw) {
+        float gam;
+        if (variant == SR_OT_BCFW && step == SR_OT_DEC) {
+            gam = (float)((2.0 * (double)m) / ((double)k + 2.0 * (double)m));
+        } else {
+            const float dd = (A.s2 - t_js * t_js) + (ai - t_js) * (ai - t_js);
+            gam = line_search<float>(g_fw, dd > 0.f ? dd : 0.f, rho, 1.f);
+        }
+        S.kind = 0; S.gamma = gam; S.coef = 1.f - gam; S.add_js = gam * ai;
+        return S;
+    }
+    const float alpha = A.t_v / ai;
+    const float gmx = alpha / (1.f - alpha);
+    const float gam = line_search<float>(A.g_aw, A.dda, rho, gmx);
+    S.kind = 1; S.gamma = gam; S.coef = 1.f + gam; S.sub_v = gam * ai;
+    S.drop = gam >= gmx;
+    return S;
+}
+
 }  // namespace srot

@@ -41,7 +41,8 @@ class Options(ct.Structure):
 class Result(ct.Structure):
     _fields_ = [
         ("objective", ct.c_double), ("gap", ct.c_double), ("rel_gap", ct.c_double),
-        ("dual", ct.c_double), ("epochs", ct.c_longlong), ("block_updates", ct.c_longlong),
+        ("dual", ct.c_double), ("row_err", ct.c_double), ("epochs", ct.c_longlong),
+        ("block_updates", ct.c_longlong),
         ("status", ct.c_int), ("reserved", ct.c_int),
     ]
 
@@ -187,6 +188,24 @@ class Handle:
         st = lib.sr_ot_solve(self._h, ct.byref(o), m, n, d, _ptr(C), _ptr(X), _ptr(Y), _ptr(a),
                              _ptr(b), _ptr(T), int(bool(warm_start)), ct.byref(res))
         return st, res.asdict()
+
+    def solve_batched(self, X, Y, a, b, T, sizes, offsets, opts=None, **kw):
+        """sr_ot_solve_batched over packed device buffers.
+
+        sizes: list of (m, n); offsets: list of (off_X, off_Y, off_a, off_b, off_T)
+        element offsets. Returns (status, list of result dicts)."""
+        o = opts if opts is not None else options(**kw)
+        B = len(sizes)
+        mm = (ct.c_int * B)(*[int(s[0]) for s in sizes])
+        nn = (ct.c_int * B)(*[int(s[1]) for s in sizes])
+        cols = list(zip(*offsets))
+        arrs = [(ct.c_longlong * B)(*[int(v) for v in c]) for c in cols]
+        res = (Result * B)()
+        st = lib.sr_ot_solve_batched(self._h, ct.byref(o), B, mm, nn, 3, arrs[0], arrs[1], arrs[2],
+                                     arrs[3], arrs[4], _ptr(X), _ptr(Y), _ptr(a), _ptr(b), _ptr(T),
+                                     res)
+        self._check(st)
+        return st, [r.asdict() for r in res]
 
     def gap(self, a, b, T, C=None, X=None, Y=None, g_rows=None, opts=None, **kw):
         """sr_ot_gap: certificate (f, g, w) of plan T."""
