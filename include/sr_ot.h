@@ -143,6 +143,12 @@ const char *sr_ot_last_error(sr_ot_handle h);
  * a); otherwise it is overwritten with T0 = (a_i e_0) (Thm 1). On return it
  * holds the final plan.
  * res: host pointer, filled on return.
+ * Limits: block-coordinate variants take n <= 8192 (FP32) or n <= 2048
+ * (FP64); SR_OT_GAP_ADAPTIVE also needs m <= 8192 (its per-row gaps are
+ * refreshed by a certificate pass every ga_M epochs, or every epoch with
+ * ga_global_only). SR_OT_FW has no size limit beyond memory: each iteration
+ * is a certificate pass (which gives every row's LMO vertex and the gap) and
+ * one pass over T, so gap_every is not used.
  */
 sr_ot_status sr_ot_solve(sr_ot_handle h, const sr_ot_options *opts, int m, int n, int d,
                          const void *C, const void *X, const void *Y, const void *a,
@@ -165,18 +171,30 @@ sr_ot_status sr_ot_solve_batched(sr_ot_handle h, const sr_ot_options *opts, int 
 
 /*
  * Gradients of the optimal value through the envelope theorem at a (converged)
- * plan T, for the squared-Euclidean point cost (not in the paper):
+ * plan T, for the squared-Euclidean point cost C_ij = ||x_i - y_j||^2. The
+ * paper does not differentiate its solver; at an optimum the derivative of
+ * the optimal value of the problem of Sec. 2 is the partial derivative of the
+ * objective at fixed T:
  *   dC = T,  dX = 2 (diag(T 1) X - T Y),  dY = 2 (diag(T^T 1) Y - T^T X),
  *   db = -rho (T^T 1 - b).
- * X, Y (points, d <= 16) may be NULL when only dC/db are requested; any
- * output may be NULL to skip it. Uses opts->precision and opts->rho only.
+ * All pointers are DEVICE pointers in opts->precision (double for SR_OT_FP64,
+ * float otherwise), row-major: X (m x d), Y (n x d), b (n), T (m x n); the
+ * caller owns every buffer. Any output may be NULL to skip it. X and Y are
+ * needed for dX or dY (1 <= d <= 31), b for db; a is unused (kept for the
+ * signature of sr_ot_solve). T is read once; partial sums are reduced in a
+ * fixed order in FP64, so results are deterministic. Uses opts->precision and
+ * opts->rho only. Errors: SR_OT_EINVAL (NULL/size/offset problems),
+ * SR_OT_EUNSUPPORTED (d out of range), SR_OT_ENOMEM, SR_OT_ECUDA. Returns
+ * after the stream has synchronised.
  */
 sr_ot_status sr_ot_grad(sr_ot_handle h, const sr_ot_options *opts, int m, int n, int d,
                         const void *X, const void *Y, const void *a, const void *b,
                         const void *T, void *dC, void *dX, void *dY, void *db);
 
-/* Batched form of sr_ot_grad over packed instances (offsets as in
- * sr_ot_solve_batched; off_dX/off_dY/off_db index the outputs). */
+/* Batched form of sr_ot_grad over packed instances, one launch for all.
+ * m, n, off_X, off_Y, off_b, off_T: HOST arrays (ELEMENT offsets, as in
+ * sr_ot_solve_batched). The outputs are packed like the inputs: dX uses the
+ * offsets of X, dY those of Y, db those of b. No dC output. */
 sr_ot_status sr_ot_grad_batched(sr_ot_handle h, const sr_ot_options *opts, int batch,
                                 const int *m, const int *n, int d, const long long *off_X,
                                 const long long *off_Y, const long long *off_b,

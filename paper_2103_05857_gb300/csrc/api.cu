@@ -24,7 +24,7 @@ namespace {
 enum WsSlot {
     WS_Q = 0, WS_PARTIAL, WS_R64, WS_RQ32, WS_COLPART, WS_ROWPART, WS_CERT, WS_PERM, WS_PERMKEY,
     WS_PERMIDX, WS_GSTORE, WS_STATUS, WS_COST, WS_CHECK, WS_SCRATCH, WS_ATOMS, WS_B_INST,
-    WS_B_QUEUE, WS_B_HEAD, WS_B_RES, WS_B_ATOMS, WS_B_BAD, WS_COUNT
+    WS_B_QUEUE, WS_B_HEAD, WS_B_RES, WS_B_ATOMS, WS_B_BAD, WS_ADJ_INST, WS_ADJ_CP, WS_ADJ_RP, WS_FW_JS, WS_FW_UPART, WS_BF16, WS_BF16_ERR, WS_COUNT
 };
 
 struct DevBuf {
@@ -360,6 +360,59 @@ sr_ot_status dev_status_error(sr_ot_handle h, int dstat) {
     return fail(h, SR_OT_ECUDA, "device reported status %d", dstat);
 }
 
+// Full Frank-Wolfe (Alg. A.1): per iteration a certificate (which also gives
+// every row's LMO vertex and the gap), then one global step.
+template <typename Real>
+sr_ot_status solve_fw_impl(sr_ot_handle h, const sr_ot_options *o, const Inst<Real> &in, Real *T,
+                           int warm_start, sr_ot_result *res) {
+    sr_ot_status st;
+    const int m = in.m, n = in.n;
+    double *q, *upart;
+    int *js, *dstat_d;
+    if ((st = ws_typed(h, WS_Q, (size_t)n, &q))) return st;
+    if ((st = ws_typed(h, WS_STATUS, 4, &dstat_d))) return st;
+    if ((st = ws_typed(h, WS_FW_JS, (size_t)m, &js))) return st;
+    if ((st = ws_typed(h, WS_FW_UPART, (size_t)fw_upart_size(n) + 1, &upart))) return st;
+    CK(h, cudaMemsetAsync(dstat_d, 0, sizeof(int), h->stream));
+    CertWork w;
+    if ((st = cert_work(h, m, n, &w))) return st;
+    launch_init_plan<Real>(in, T, warm_start, o->rho, q, h->stream);
+    h->launches += warm_start ? 1 : 2;
+    CKL(h);
+    double *gamma_dev = upart + fw_upart_size(n);
+    long long it = 0;
+    bool converged = false;
+    for (it = 0; it < o->max_epochs; ++it) {
+        {
+            ProfScope ps(h, SR_OT_PROF_CERT);
+            launch_certificate<Real>(in, T, o->rho, o->tol_rel_gap, w, nullptr, nullptr, h->stream, js);
+        }
+        h->launches += 4;
+        CKL(h);
+        int dstat = 0;
+        if ((st = read_cert(h, w, dstat_d, &dstat))) return st;
+        if (!std::isfinite(h->h_cert[kCertG])) return fail(h, SR_OT_ENUMERIC, "non-finite gap at iteration %lld", it);
+        if (h->h_cert[kCertStop] != 0.0) { converged = true; break; }
+        {
+            ProfScope ps(h, SR_OT_PROF_EPOCH);
+            launch_fw_step<Real>(in, T, js, w.r64, w.cert, o->step, it, o->rho, upart, gamma_dev, h->stream);
+        }
+        h->launches += o->step == SR_OT_ELS ? 3 : 2;
+        CKL(h);
+    }
+    if (!converged) {
+        launch_certificate<Real>(in, T, o->rho, o->tol_rel_gap, w, nullptr, nullptr, h->stream);
+        h->launches += 4;
+        CKL(h);
+        int dstat = 0;
+        if ((st = read_cert(h, w, dstat_d, &dstat))) return st;
+        converged = h->h_cert[kCertStop] != 0.0;
+    }
+    sr_ot_status out = (o->tol_rel_gap > 0.0 && !converged) ? SR_OT_NOT_CONVERGED : SR_OT_OK;
+    fill_result(res, h->h_cert, it, it * (long long)m, out);
+    return out;
+}
+
 template <typename Real>
 sr_ot_status solve_impl(sr_ot_handle h, const sr_ot_options *o, int m, int n, int d, const void *C,
                         const void *X, const void *Y, const void *a, const void *b, void *T_inout,
@@ -368,10 +421,10 @@ sr_ot_status solve_impl(sr_ot_handle h, const sr_ot_options *o, int m, int n, in
     Inst<Real> in;
     if ((st = make_inst<Real>(h, o, m, n, d, C, X, Y, a, b, &in))) return st;
     const bool fp64 = std::is_same<Real, double>::value;
-    if (o->variant == SR_OT_FW)
-        return fail(h, SR_OT_EUNSUPPORTED, "full Frank-Wolfe is not available in this build");
-    if (o->order == SR_OT_GAP_ADAPTIVE)
-        return fail(h, SR_OT_EUNSUPPORTED, "gap-adaptive sampling is not available in this build");
+    if (o->variant == SR_OT_FW) return solve_fw_impl<Real>(h, o, in, static_cast<Real *>(T_inout), warm_start, res);
+    const bool ga = o->order == SR_OT_GAP_ADAPTIVE;
+    if (ga && m > epoch_ga_max_m())
+        return fail(h, SR_OT_EUNSUPPORTED, "gap-adaptive sampling takes m <= %d (got %d)", epoch_ga_max_m(), m);
     if (n > epoch_max_n(fp64))
         return fail(h, SR_OT_EUNSUPPORTED, "n = %d exceeds the single-instance limit %d for this precision",
                     n, epoch_max_n(fp64));
@@ -407,7 +460,7 @@ sr_ot_status solve_impl(sr_ot_handle h, const sr_ot_options *o, int m, int n, in
     bool use_sparse = false;
     int4 *atoms = nullptr;
     if constexpr (std::is_same<Real, float>::value) {
-        if ((o->variant == SR_OT_BCAFW || o->variant == SR_OT_BCPFW) && !o->dense_only &&
+        if ((o->variant == SR_OT_BCAFW || o->variant == SR_OT_BCPFW) && !o->dense_only && !ga &&
             n <= epoch_max_n(false)) {
             if ((st = ws_typed(h, WS_ATOMS, (size_t)m * kAtomRecord, &atoms))) return st;
             CK(h, cudaMemsetAsync(dstat_d + 2, 0, sizeof(int), h->stream));
@@ -434,6 +487,15 @@ sr_ot_status solve_impl(sr_ot_handle h, const sr_ot_options *o, int m, int n, in
     A.perm = perm;
     A.g_store = nullptr;
     A.ga_inner = 0;
+    const int ga_every = o->ga_global_only ? 1 : std::max(1, o->ga_M);
+    if (ga) {
+        // every g_i exact at the start (the reading of Alg. A.4's initialisation)
+        if ((st = ws_typed(h, WS_GSTORE, (size_t)m, &A.g_store))) return st;
+        A.ga_inner = o->ga_global_only ? 0 : 1;
+        launch_certificate<Real>(in, T, o->rho, o->tol_rel_gap, w, nullptr, A.g_store, h->stream);
+        h->launches += 4;
+        CKL(h);
+    }
     A.trace = o->trace;
     A.trace_cap = o->trace ? o->trace_capacity : 0;
     A.status = dstat_d;
@@ -460,7 +522,9 @@ sr_ot_status solve_impl(sr_ot_handle h, const sr_ot_options *o, int m, int n, in
         A.epoch = ep;
         {
             ProfScope ps(h, SR_OT_PROF_EPOCH);
-            if constexpr (std::is_same<Real, float>::value) {
+            if (ga) {
+                launch_epoch_ga<Real>(A, h->stream);
+            } else if constexpr (std::is_same<Real, float>::value) {
                 if (use_sparse) {
                     EpochArgs<float> As = A;
                     As.resume = dstat_d + 1;
@@ -479,12 +543,21 @@ sr_ot_status solve_impl(sr_ot_handle h, const sr_ot_options *o, int m, int n, in
         h->launches += 1;
         CKL(h);
         const bool last = ep + 1 == o->max_epochs;
-        if ((ep + 1) % o->gap_every == 0 || last) {
+        const bool ga_global = ga && (ep + 1) % ga_every == 0;  // every g_i again (Alg. A.4)
+        const bool cert_due = (ep + 1) % o->gap_every == 0 || last;
+        if (ga_global && !cert_due) {
+            ProfScope ps(h, SR_OT_PROF_CERT);
+            launch_certificate<Real>(in, T, o->rho, o->tol_rel_gap, w, nullptr, A.g_store, h->stream);
+            h->launches += 4;
+            CKL(h);
+        }
+        if (cert_due) {
             ++ncert;
             double *refresh = (refresh_every > 0 && ncert % refresh_every == 0) ? q : nullptr;
             {
                 ProfScope ps(h, SR_OT_PROF_CERT);
-                launch_certificate<Real>(in, T, o->rho, o->tol_rel_gap, w, refresh, nullptr, h->stream);
+                launch_certificate<Real>(in, T, o->rho, o->tol_rel_gap, w, refresh,
+                                         ga_global ? A.g_store : nullptr, h->stream);
             }
             h->launches += 4;
             CKL(h);
@@ -572,6 +645,70 @@ __global__ void k_batch_check(const BatchInst *inst, int batch, const float *X, 
         }
         if (c) atomicAdd(&bad[k], c);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Envelope-theorem gradients (adjoint pass) for one or many instances.
+// ---------------------------------------------------------------------------
+template <typename Real>
+sr_ot_status grad_impl(sr_ot_handle h, const sr_ot_options *o, int ninst, const int *m, const int *n,
+                       int d, const long long *oX, const long long *oY, const long long *ob,
+                       const long long *oT, const void *X, const void *Y, const void *b, const void *T,
+                       void *dC, void *dX, void *dY, void *db) {
+    if (!o) return fail(h, SR_OT_EINVAL, "opts is NULL");
+    if (!std::isfinite(o->rho) || o->rho < 0.0) return fail(h, SR_OT_EINVAL, "rho must be finite and >= 0");
+    if (!T) return fail(h, SR_OT_EINVAL, "T must be non-NULL");
+    if ((dX || dY) && (!X || !Y)) return fail(h, SR_OT_EINVAL, "dX and dY need the points X and Y");
+    if (db && !b) return fail(h, SR_OT_EINVAL, "db needs b");
+    if ((dX || dY) && (d < 1 || d > 31)) return fail(h, SR_OT_EUNSUPPORTED, "gradients take 1 <= d <= 31 (got %d)", d);
+    if (!(dX || dY) && (d < 1 || d > 31)) d = 3;  // d unused: no point gradients requested
+    if (!dC && !dX && !dY && !db) return SR_OT_OK;
+    for (int k = 0; k < ninst; ++k) {
+        if (m[k] <= 0 || n[k] <= 0) return fail(h, SR_OT_EINVAL, "instance %d: m and n must be >= 1", k);
+        if (oX[k] < 0 || oY[k] < 0 || ob[k] < 0 || oT[k] < 0) return fail(h, SR_OT_EINVAL, "instance %d: negative offset", k);
+    }
+    std::vector<AdjInst> inst(ninst);
+    const AdjTotals tot = adj_plan(ninst, m, n, d, inst.data());
+    if (tot.tiles > 0x7FFFFFFFLL) return fail(h, SR_OT_EUNSUPPORTED, "adjoint launch too large (%lld tiles)", tot.tiles);
+    for (int k = 0; k < ninst; ++k) {
+        inst[k].oX = oX[k];
+        inst[k].oY = oY[k];
+        inst[k].ob = ob[k];
+        inst[k].oT = oT[k];
+    }
+    sr_ot_status st;
+    AdjInst *d_inst;
+    Real *cp, *rp;
+    if ((st = ws_typed(h, WS_ADJ_INST, (size_t)ninst, &d_inst))) return st;
+    if ((st = ws_typed(h, WS_ADJ_CP, (size_t)tot.colpart, &cp))) return st;
+    if ((st = ws_typed(h, WS_ADJ_RP, (size_t)tot.rowpart, &rp))) return st;
+    CK(h, cudaMemcpyAsync(d_inst, inst.data(), sizeof(AdjInst) * ninst, cudaMemcpyHostToDevice, h->stream));
+    AdjArgs<Real> A;
+    A.inst = d_inst;
+    A.ninst = ninst;
+    A.d = d;
+    A.rho = o->rho;
+    A.X = static_cast<const Real *>(X);
+    A.Y = static_cast<const Real *>(Y);
+    A.b = static_cast<const Real *>(b);
+    A.T = static_cast<const Real *>(T);
+    A.dC = static_cast<Real *>(dC);
+    A.dX = static_cast<Real *>(dX);
+    A.dY = static_cast<Real *>(dY);
+    A.db = static_cast<Real *>(db);
+    A.colpart = cp;
+    A.rowpart = rp;
+    A.total_tiles = (int)tot.tiles;
+    A.total_cols = tot.cols;
+    A.total_rows = tot.rows;
+    {
+        ProfScope ps(h, SR_OT_PROF_GRAD);
+        if (!launch_adjoint<Real>(A, h->stream)) return fail(h, SR_OT_EUNSUPPORTED, "d = %d out of range", d);
+    }
+    h->launches += 1 + ((dY || db) ? 1 : 0) + (dX ? 1 : 0);
+    CKL(h);
+    CK(h, cudaStreamSynchronize(h->stream));
+    return SR_OT_OK;
 }
 
 sr_ot_status ensure_side_streams(sr_ot_handle h) {
@@ -952,8 +1089,17 @@ sr_ot_status sr_ot_solve_batched(sr_ot_handle h, const sr_ot_options *opts, int 
 sr_ot_status sr_ot_grad(sr_ot_handle h, const sr_ot_options *opts, int m, int n, int d,
                         const void *X, const void *Y, const void *a, const void *b, const void *T,
                         void *dC, void *dX, void *dY, void *db) {
+    (void)a;
     if (!h) return fail(nullptr, SR_OT_EINVAL, "handle is NULL");
-    return fail(h, SR_OT_EUNSUPPORTED, "gradients are not available in this build");
+    h->err.clear();
+    sr_ot_status st;
+    if (!opts) return fail(h, SR_OT_EINVAL, "opts is NULL");
+    if ((st = check_sizes(h, m, n))) return st;
+    if ((st = check_stream_device(h))) return st;
+    const long long z = 0;
+    if (opts->precision == SR_OT_FP64)
+        return grad_impl<double>(h, opts, 1, &m, &n, d, &z, &z, &z, &z, X, Y, b, T, dC, dX, dY, db);
+    return grad_impl<float>(h, opts, 1, &m, &n, d, &z, &z, &z, &z, X, Y, b, T, dC, dX, dY, db);
 }
 
 sr_ot_status sr_ot_grad_batched(sr_ot_handle h, const sr_ot_options *opts, int batch, const int *m,
@@ -962,7 +1108,17 @@ sr_ot_status sr_ot_grad_batched(sr_ot_handle h, const sr_ot_options *opts, int b
                                 const void *Y, const void *b, const void *T, void *dX, void *dY,
                                 void *db) {
     if (!h) return fail(nullptr, SR_OT_EINVAL, "handle is NULL");
-    return fail(h, SR_OT_EUNSUPPORTED, "batched gradients are not available in this build");
+    h->err.clear();
+    sr_ot_status st;
+    if (batch <= 0) return fail(h, SR_OT_EINVAL, "batch must be >= 1");
+    if (!m || !n || !off_X || !off_Y || !off_b || !off_T)
+        return fail(h, SR_OT_EINVAL, "size and offset arrays must be non-NULL");
+    if ((st = check_stream_device(h))) return st;
+    if (opts && opts->precision == SR_OT_FP64)
+        return grad_impl<double>(h, opts, batch, m, n, d, off_X, off_Y, off_b, off_T, X, Y, b, T, nullptr,
+                                 dX, dY, db);
+    return grad_impl<float>(h, opts, batch, m, n, d, off_X, off_Y, off_b, off_T, X, Y, b, T, nullptr, dX,
+                            dY, db);
 }
 
 long long sr_ot_launch_count(sr_ot_handle h) { return h ? h->launches : 0; }
@@ -989,7 +1145,27 @@ sr_ot_status sr_ot_profile_read(sr_ot_handle h, int kind, double *total_ms, long
 sr_ot_status sr_ot_cost_bf16(sr_ot_handle h, int m, int n, int d, const float *X, const float *Y,
                              float *C) {
     if (!h) return fail(nullptr, SR_OT_EINVAL, "handle is NULL");
-    return fail(h, SR_OT_EUNSUPPORTED, "the BF16 tensor-core cost is not available in this build");
+    sr_ot_status st;
+    if ((st = check_sizes(h, m, n))) return st;
+    if (!X || !Y || !C) return fail(h, SR_OT_EINVAL, "X, Y and C must be non-NULL");
+    if ((st = check_stream_device(h))) return st;
+    void *ws;
+    int *err;
+    if ((st = ws_get(h, WS_BF16, cost_bf16_workspace(m, n, d), &ws))) return st;
+    if ((st = ws_typed(h, WS_BF16_ERR, 1, &err))) return st;
+    CK(h, cudaMemsetAsync(err, 0, sizeof(int), h->stream));
+    const char *msg;
+    {
+        ProfScope ps(h, SR_OT_PROF_COST);
+        msg = launch_cost_bf16(m, n, d, X, Y, C, ws, err, h->stream);
+    }
+    if (msg) return fail(h, SR_OT_EUNSUPPORTED, "BF16 cost: %s", msg);
+    h->launches += 3;
+    CKL(h);
+    CK(h, cudaMemcpyAsync(h->h_status, err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (h->h_status[0]) return fail(h, SR_OT_ETIMEOUT, "BF16 cost: a bounded device wait gave up");
+    return SR_OT_OK;
 }
 
 }  // extern "C"

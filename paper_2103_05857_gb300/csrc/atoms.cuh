@@ -26,15 +26,14 @@ struct LaneAtoms {
 __device__ inline LaneAtoms load_atoms(const int4 *rec, int lane) {
     LaneAtoms A;
     A.cnt = rec[0].x;
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-        const int k = lane + 32 * s;
-        const bool have = k < A.cnt;
-        const int4 e = rec[1 + (k < kAtomsMax ? k : 0)];
-        A.j[s] = have ? e.x : -1;
-        A.t[s] = have ? DF{__int_as_float(e.y), __int_as_float(e.z)} : DF{0.f, 0.f};
-        A.g[s] = 0.f;
-    }
+    const int4 e0 = rec[1 + lane];
+    const int4 e1 = rec[1 + (lane + 32 < kAtomsMax ? lane + 32 : 0)];
+    const bool h0 = lane < A.cnt, h1 = lane + 32 < A.cnt;
+    A.j[0] = h0 ? e0.x : -1;
+    A.t[0] = h0 ? DF{__int_as_float(e0.y), __int_as_float(e0.z)} : DF{0.f, 0.f};
+    A.j[1] = h1 ? e1.x : -1;
+    A.t[1] = h1 ? DF{__int_as_float(e1.y), __int_as_float(e1.z)} : DF{0.f, 0.f};
+    A.g[0] = A.g[1] = 0.f;
     return A;
 }
 
@@ -43,15 +42,19 @@ __device__ inline LaneAtoms load_atoms(const int4 *rec, int lane) {
 template <typename GradF>
 __device__ inline AtomStats atom_stats(LaneAtoms &A, GradF grad, float ai, bool want_sums, DF *t_v_df) {
     const unsigned FULL = 0xffffffffu;
+    const bool two = A.cnt > 32;  // warp-uniform: slot 1 holds atoms
     uint32_t kx = 0u;
     int jx = 0x7FFFFFFF;
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
-        if (A.j[s] >= 0) {
-            A.g[s] = grad(A.j[s]);
-            const uint32_t kk = f2key(A.g[s]);
-            if (kk > kx || (kk == kx && A.j[s] < jx)) { kx = kk; jx = A.j[s]; }
-        }
+    if (A.j[0] >= 0) {
+        A.g[0] = grad(A.j[0]);
+        kx = f2key(A.g[0]);
+        jx = A.j[0];
+    }
+    if (two && A.j[1] >= 0) {
+        A.g[1] = grad(A.j[1]);
+        const uint32_t kk = f2key(A.g[1]);
+        if (kk > kx || (kk == kx && A.j[1] < jx)) { kx = kk; jx = A.j[1]; }
+    }
     AtomStats S;
     const uint32_t wkx = __reduce_max_sync(FULL, kx);
     S.v = __reduce_min_sync(FULL, kx == wkx ? jx : 0x7FFFFFFF);
@@ -59,16 +62,19 @@ __device__ inline AtomStats atom_stats(LaneAtoms &A, GradF grad, float ai, bool 
     S.nnz = A.cnt;
     DF tv{0.f, 0.f};
     int vl = -1;
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-        const unsigned mk = __ballot_sync(FULL, A.j[s] >= 0 && A.j[s] == S.v);
-        if (mk) vl = 32 * s + __ffs(mk) - 1;
+    {
+        const unsigned mk = __ballot_sync(FULL, A.j[0] >= 0 && A.j[0] == S.v);
+        if (mk) vl = __ffs(mk) - 1;
+    }
+    if (two) {
+        const unsigned mk = __ballot_sync(FULL, A.j[1] >= 0 && A.j[1] == S.v);
+        if (mk) vl = 32 + __ffs(mk) - 1;
     }
     {
         const int src = vl >= 0 ? (vl & 31) : 0, sl = vl >> 5;  // vl is warp-uniform
-        const float h0 = __shfl_sync(FULL, A.t[0].hi, src), h1 = __shfl_sync(FULL, A.t[1].hi, src);
-        const float l0 = __shfl_sync(FULL, A.t[0].lo, src), l1 = __shfl_sync(FULL, A.t[1].lo, src);
-        if (vl >= 0) tv = sl ? DF{h1, l1} : DF{h0, l0};
+        const float h = __shfl_sync(FULL, sl ? A.t[1].hi : A.t[0].hi, src);
+        const float l = __shfl_sync(FULL, sl ? A.t[1].lo : A.t[0].lo, src);
+        if (vl >= 0) tv = DF{h, l};
     }
     *t_v_df = tv;
     S.t_v = tv.hi;
@@ -77,7 +83,7 @@ __device__ inline AtomStats atom_stats(LaneAtoms &A, GradF grad, float ai, bool 
         float aw = 0.f, s2 = 0.f, dd = 0.f;
 #pragma unroll
         for (int s = 0; s < 2; ++s)
-            if (A.j[s] >= 0) {
+            if (A.j[s] >= 0 && (s == 0 || two)) {
                 const float t = A.t[s].hi;
                 aw += t * (S.gmax - A.g[s]);
                 s2 += t * t;
@@ -95,15 +101,18 @@ __device__ inline AtomStats atom_stats(LaneAtoms &A, GradF grad, float ai, bool 
 __device__ inline float atom_weight(const LaneAtoms &A, int js, bool *present) {
     const unsigned FULL = 0xffffffffu;
     int where = -1;
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-        const unsigned mk = __ballot_sync(FULL, A.j[s] >= 0 && A.j[s] == js);
-        if (mk) where = 32 * s + __ffs(mk) - 1;
+    {
+        const unsigned mk = __ballot_sync(FULL, A.j[0] >= 0 && A.j[0] == js);
+        if (mk) where = __ffs(mk) - 1;
+    }
+    if (A.cnt > 32) {
+        const unsigned mk = __ballot_sync(FULL, A.j[1] >= 0 && A.j[1] == js);
+        if (mk) where = 32 + __ffs(mk) - 1;
     }
     const int src = where >= 0 ? (where & 31) : 0;
-    const float h0 = __shfl_sync(FULL, A.t[0].hi, src), h1 = __shfl_sync(FULL, A.t[1].hi, src);
+    const float h = __shfl_sync(FULL, (where >> 5) > 0 ? A.t[1].hi : A.t[0].hi, src);
     *present = where >= 0;
-    return where < 0 ? 0.f : ((where >> 5) ? h1 : h0);
+    return where < 0 ? 0.f : h;
 }
 
 // Apply step S of row i: atoms (with j* appended when it enters), dense
@@ -117,11 +126,13 @@ __device__ inline bool apply_atoms(const Step<float> &S, LaneAtoms &A, bool js_p
     const bool append = grows && !js_present;
     if (append && A.cnt >= kAtomsMax) return false;
     const DF mv = (S.kind == 2 && S.drop) ? t_v : DF{S.add_js, 0.f};
-    bool keep[2];
+    const bool two = A.cnt + (append ? 1 : 0) > 32;  // warp-uniform
+    bool keep[2] = {false, false};
     DF tn[2];
-    int jl[2];
+    int jl[2] = {-1, -1};
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
+        if (s == 1 && !two) break;
         const int k = lane + 32 * s;
         jl[s] = A.j[s];
         DF told = A.t[s];
@@ -144,7 +155,8 @@ __device__ inline bool apply_atoms(const Step<float> &S, LaneAtoms &A, bool js_p
         }
         keep[s] = jl[s] >= 0 && tn[s].hi > 0.f;
     }
-    const unsigned k0 = __ballot_sync(FULL, keep[0]), k1 = __ballot_sync(FULL, keep[1]);
+    const unsigned k0 = __ballot_sync(FULL, keep[0]);
+    const unsigned k1 = two ? __ballot_sync(FULL, keep[1]) : 0u;
     const unsigned lt = (1u << lane) - 1u;
     if (keep[0]) grec[1 + __popc(k0 & lt)] = make_int4(jl[0], __float_as_int(tn[0].hi), __float_as_int(tn[0].lo), 0);
     if (keep[1]) grec[1 + __popc(k0) + __popc(k1 & lt)] = make_int4(jl[1], __float_as_int(tn[1].hi), __float_as_int(tn[1].lo), 0);

@@ -141,7 +141,8 @@ k_colsum_final(const double *__restrict__ partial, int nchunks, int n, const Rea
 template <typename Real>
 __global__ void __launch_bounds__(kRowThreads)
 k_gap_rows(Inst<Real> in, const Real *__restrict__ T, double rho, const double *__restrict__ r64,
-           const float *__restrict__ rq32, double *__restrict__ g_rows, double *__restrict__ rowpart) {
+           const float *__restrict__ rq32, double *__restrict__ g_rows, double *__restrict__ rowpart,
+           int *__restrict__ js_out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n = in.n;
     double acc_tc = 0.0, acc_amin = 0.0, acc_feas = 0.0;  // lane 0 of each warp accumulates its rows
@@ -205,6 +206,7 @@ k_gap_rows(Inst<Real> in, const Real *__restrict__ T, double rho, const double *
             const double dfe = fabs(rs_row - ai) / (ai > 0.0 ? ai : 1e-300);
             acc_feas = fmax(acc_feas, dfe);
             if (g_rows) g_rows[i] = tc_row + rho * tr_row - ai * gmin;
+            if (js_out) js_out[i] = jb;
         }
     }
     __shared__ double sh[3][kRowWarps];
@@ -256,22 +258,23 @@ k_cert_final(const double *__restrict__ colpart, int ncol, const double *__restr
 
 template <typename Real>
 void launch_certificate(const Inst<Real> &in, const Real *T, double rho, double tol,
-                        const CertWork &w, double *refresh_q, double *g_rows, cudaStream_t st) {
+                        const CertWork &w, double *refresh_q, double *g_rows, cudaStream_t st,
+                        int *js_out) {
     dim3 g1(ceil_div(in.n, kColThreads), w.nchunks);
     k_colsum_partial<Real><<<g1, kColThreads, 0, st>>>(T, in.m, in.n, w.rows_per_chunk, w.partial);
     k_colsum_final<Real><<<w.ncolblocks, kColThreads, 0, st>>>(w.partial, w.nchunks, in.n, in.b,
                                                                rho, w.r64, w.rq32, refresh_q,
                                                                w.colpart);
     k_gap_rows<Real><<<w.nrowblocks, kRowThreads, 0, st>>>(in, T, rho, w.r64, w.rq32, g_rows,
-                                                           w.rowpart);
+                                                           w.rowpart, js_out);
     k_cert_final<<<1, kFinalThreads, 0, st>>>(w.colpart, w.ncolblocks, w.rowpart, w.nrowblocks,
                                               rho, tol, w.cert);
 }
 
 template void launch_certificate<float>(const Inst<float> &, const float *, double, double,
-                                        const CertWork &, double *, double *, cudaStream_t);
+                                        const CertWork &, double *, double *, cudaStream_t, int *);
 template void launch_certificate<double>(const Inst<double> &, const double *, double, double,
-                                         const CertWork &, double *, double *, cudaStream_t);
+                                         const CertWork &, double *, double *, cudaStream_t, int *);
 
 // ---------------------------------------------------------------------------
 // Initial plan T0 = (a_i e_0) (Thm 1) and the solver's initial residual.

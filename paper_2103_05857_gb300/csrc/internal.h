@@ -61,10 +61,11 @@ void cert_work_shape(int m, int n, int *nchunks, int *rows_per_chunk, int *ncolb
 // Certificate of plan T (Thm 2). If refresh_q is non-null, the solver's
 // running residual is overwritten from the exact column sums: the FP32 path
 // keeps q = rho * r, the FP64 path keeps r (both in double). g_rows
-// (optional) receives per-row gaps.
+// (optional) receives per-row gaps, js_out (optional) each row's LMO vertex.
 template <typename Real>
 void launch_certificate(const Inst<Real> &in, const Real *T, double rho, double tol,
-                        const CertWork &w, double *refresh_q, double *g_rows, cudaStream_t st);
+                        const CertWork &w, double *refresh_q, double *g_rows, cudaStream_t st,
+                        int *js_out = nullptr);
 
 // T = (a_i e_0) (Thm 1) and the solver's initial residual (FP32: q = rho (T^T1 - b);
 // FP64: r = T^T1 - b with the column sums taken in ascending row order).
@@ -81,6 +82,14 @@ void launch_init_residual(const Inst<Real> &in, const Real *T, double rho, doubl
 void launch_make_perm(unsigned long long seed, long long epoch, int m, int *perm,
                       uint64_t *keybuf, int *idxbuf, cudaStream_t st);
 size_t make_perm_scratch_bytes(int m);
+
+// BF16 tensor-core cost C = |x~|^2 + |y~|^2 - 2 X~ Y~^T (X~, Y~: BF16-rounded
+// points; FP32 accumulation and norms). ws: cost_bf16_workspace(m, n, d)
+// bytes; err_dev: an int set to 1 if a bounded wait gave up. Returns an error
+// message for unsupported arguments (nothing launched), else nullptr.
+size_t cost_bf16_workspace(int m, int n, int d);
+const char *launch_cost_bf16(int m, int n, int d, const float *X, const float *Y, float *C, void *ws,
+                             int *err_dev, cudaStream_t st);
 
 // Materialise C_ij = ||x_i - y_j||^2 for general d on the CUDA cores.
 template <typename Real>
@@ -110,6 +119,23 @@ struct EpochArgs {
     const int *resume_in;    // dense kernel: start at *resume_in, or return if it is < 0
 };
 
+// Gap-adaptive epoch (Alg. A.4): rows drawn with probability proportional to
+// max(g_i, 0) from A.g_store; A.ga_inner re-evaluates g_i after each update.
+// False if m or n is too large.
+template <typename Real>
+bool launch_epoch_ga(const EpochArgs<Real> &args, cudaStream_t st);
+int epoch_ga_max_m();
+
+// Full Frank-Wolfe step (Alg. A.1) after a certificate that wrote every
+// row's LMO vertex js: exact line search (step == ELS, gap g read from
+// cert[kCertG]) or the decay 2 / (it + 2), then T <- (1 - gamma) T + gamma S.
+// upart: workspace of fw_upart_size(n) doubles; gamma_dev: one double.
+int fw_upart_size(int n);
+template <typename Real>
+void launch_fw_step(const Inst<Real> &in, Real *T, const int *js, const double *r64,
+                    const double *cert, int step, long long it, double rho, double *upart,
+                    double *gamma_dev, cudaStream_t st);
+
 // Atom record of one row for the active-set kernels: entry 0 = {count, 0, 0,
 // 0}, then up to 63 entries {column, weight hi bits, weight lo bits, 0}
 // (double-float weights); 1 KiB.
@@ -130,5 +156,42 @@ int epoch_max_n(bool fp64);
 // Message returned by sr_ot_last_error(NULL) on this thread (errors of calls
 // that have no handle).
 void set_handleless_error(const char *msg);
+
+// ---- adjoint (envelope-theorem gradients) ---------------------------------
+// One instance of an adjoint launch. Offsets are in elements; dX, dY and db
+// use the offsets of X, Y and b.
+struct AdjInst {
+    int m, n;
+    long long oX, oY, ob, oT;
+    int nbands, rh, ncol;  // row bands of rh rows; column tiles of 256
+    int tile0;             // first tile (CTA) of this instance
+    long long col0, row0;  // prefix sums of n and m over the instances
+    long long ocp, orp;    // offsets of the column / row partials
+};
+
+struct AdjTotals {
+    long long tiles, cols, rows, colpart, rowpart;
+};
+
+template <typename Real>
+struct AdjArgs {
+    const AdjInst *inst;
+    int ninst, d;
+    double rho;
+    const Real *X, *Y, *b, *T;
+    Real *dC, *dX, *dY, *db;  // any may be null (dC only for one instance)
+    Real *colpart, *rowpart;  // workspace from adj_plan's totals
+    int total_tiles;
+    long long total_cols, total_rows;
+};
+
+// Padded width of the per-entry partial vector (x or y, then 1): 4, 8, 16 or 32.
+int adj_width(int d);
+// Tiles and workspace of a set of instances; fills out[k] except the offsets
+// oX, oY, ob, oT.
+AdjTotals adj_plan(int ninst, const int *m, const int *n, int d, AdjInst *out);
+// Launch the tile pass and the two reductions; false if d is out of range.
+template <typename Real>
+bool launch_adjoint(const AdjArgs<Real> &A, cudaStream_t st);
 
 }  // namespace srot

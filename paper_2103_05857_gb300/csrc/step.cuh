@@ -27,6 +27,7 @@ template <typename Real>
 struct Red {
     Real gmin, s1, s2, gmax;
     int jmin, jmax, nnz;
+    Real rs;  // FP32 away steps: sum_j t_ij as stored
 };
 
 // Exact line search on phi(gamma) = -num gamma + (rho/2) dd gamma^2, [0, gmax].
@@ -50,6 +51,28 @@ struct Step {
     Real sub_v;      // pairwise: moved mass ; away: gamma a_i
     bool drop;
 };
+
+// Unit in the last place of a nonnegative float (0 for 0; the smallest
+// normal spacing below 2^-103).
+__device__ inline float ulpf(float x) {
+    const int e = __float_as_int(x) & 0x7F800000;
+    if (e == 0) return 0.f;
+    return e > (23 << 23) + (1 << 23) ? __int_as_float(e - (23 << 23)) : __int_as_float(1 << 23);
+}
+
+// Mass moved between two FP32 plan entries a and b (a gains, b loses),
+// rounded to a multiple of the coarser spacing of the two so that both
+// a + moved and b - moved are exact: otherwise a move below half an ulp of
+// the larger entry is absorbed there but not at the other one, and the row
+// mass drifts systematically over many small steps. Never exceeds b.
+__device__ inline float conserving_move(float moved, float a, float b) {
+    const float u = fmaxf(ulpf(a), ulpf(b));
+    if (!(u > 0.f) || u < 0x1.0p-100f) return moved;
+    const float inv = 1.f / u;  // a power of two: exact
+    float q = rintf(moved * inv) * u;
+    if (q > b) q = floorf(b * inv) * u;
+    return q;
+}
 
 template <typename Real>
 __device__ inline Step<Real> decide(const Red<Real> &R, Real ai, Real t_js, Real t_v, int variant,
@@ -83,16 +106,33 @@ __device__ inline Step<Real> decide(const Red<Real> &R, Real ai, Real t_js, Real
     if (S.v < 0 || S.v == 0x7FFFFFFF) return S;
     if (variant == SR_OT_BCAFW) {
         const Real g_aw = ai * R.gmax - R.s1;
-        if (R.nnz <= 1 || g_fw >= g_aw) {
+        // Mass of the other atoms: a_i - t_v in exact arithmetic. FP32 uses
+        // the stored row minus t_v, so that the step conserves the row as
+        // stored: with alpha_v near 1, gamma_max = alpha/(1-alpha) is huge
+        // and a_i - t_v would multiply the row's rounding drift by it.
+        Real s_oth;
+        if constexpr (std::is_same<Real, float>::value) s_oth = R.rs - t_v;
+        else s_oth = ai - t_v;
+        // alpha_v >= 1 (all the mass on v): the away direction is zero
+        if (R.nnz <= 1 || g_fw >= g_aw || !(s_oth > Real(0))) {
             Real dd = (R.s2 - t_js * t_js) + (ai - t_js) * (ai - t_js);
             Real gam = line_search<Real>(g_fw, dd > Real(0) ? dd : Real(0), rho, Real(1));
             S.kind = 0; S.gamma = gam; S.coef = Real(1) - gam; S.add_js = gam * ai;
         } else {
-            Real alpha = t_v / ai;
-            Real gmax = alpha / (Real(1) - alpha);
-            Real dd = (R.s2 - t_v * t_v) + (t_v - ai) * (t_v - ai);
+            Real gmax, dd;
+            if constexpr (std::is_same<Real, float>::value) {
+                gmax = t_v / s_oth;  // = alpha / (1 - alpha)
+                dd = (R.s2 - t_v * t_v) + s_oth * s_oth;
+            } else {
+                const Real alpha = t_v / ai;
+                gmax = alpha / (Real(1) - alpha);
+                dd = (R.s2 - t_v * t_v) + (t_v - ai) * (t_v - ai);
+            }
             Real gam = line_search<Real>(g_aw, dd > Real(0) ? dd : Real(0), rho, gmax);
-            S.kind = 1; S.gamma = gam; S.coef = Real(1) + gam; S.sub_v = gam * ai;
+            S.kind = 1; S.gamma = gam; S.coef = Real(1) + gam;
+            // FP32: v loses gamma * s_oth directly; FP64: (1 + gamma) t_v - gamma a_i
+            if constexpr (std::is_same<Real, float>::value) S.sub_v = gam * s_oth;
+            else S.sub_v = gam * ai;
             S.drop = gam >= gmax;
         }
         return S;
@@ -105,6 +145,8 @@ __device__ inline Step<Real> decide(const Red<Real> &R, Real ai, Real t_js, Real
     S.kind = 2; S.gamma = gam;
     S.drop = gam >= gmax;
     Real moved = S.drop ? t_v : gam * ai;
+    if constexpr (std::is_same<Real, float>::value)
+        if (!S.drop) moved = conserving_move(moved, t_js, t_v);
     S.add_js = moved; S.sub_v = moved;
     return S;
 }
@@ -124,9 +166,12 @@ __device__ inline Real apply(const Step<Real> &S, int j, Real t) {
         return tn;
     }
     if (S.kind == 1) {
-        Real tn = S.coef * t;
-        if (j == S.v) tn = S.drop ? Real(0) : tn - S.sub_v;
-        return tn;
+        if (j == S.v) {
+            if (S.drop) return Real(0);
+            if constexpr (std::is_same<Real, float>::value) return t - S.sub_v;
+            else return S.coef * t - S.sub_v;
+        }
+        return S.coef * t;
     }
     if (S.kind == 2) {
         if (j == S.js) return t + S.add_js;
@@ -220,7 +265,7 @@ __device__ inline Step<float> decide_atoms(const AtomStats &A, float gmin, int j
     S.coef = 1.f; S.add_js = 0.f; S.sub_v = 0.f; S.drop = false;
     if (!(ai > 0.f)) return S;
     const float g_fw = ai * (A.gmax - gmin) - A.g_aw;
-    const bool fw = variant == SR_OT_BCFW || A.nnz <= 1 || g_fw >= A.g_aw;
+    const bool fw = variant == SR_OT_BCFW || A.nnz <= 1 || g_fw >= A.g_aw || !(A.t_v < ai);
     if (fw) {
         float gam;
         if (variant == SR_OT_BCFW && step == SR_OT_DEC) {

@@ -217,3 +217,56 @@ class Handle:
                            _ptr(b), _ptr(T), _ptr(g_rows), ct.byref(res))
         self._check(st, allow=(OK,))
         return res.asdict()
+
+    def grad(self, T, X=None, Y=None, b=None, want=("dX", "dY", "db"), opts=None, **kw):
+        """sr_ot_grad: envelope-theorem gradients at plan T. Returns a dict with
+        the requested entries of dC, dX, dY, db (new tensors, T's dtype)."""
+        o = opts if opts is not None else options(**kw)
+        m, n = T.shape
+        d = 3 if X is None else X.shape[1]  # without points the library rejects dX / dY
+        out = {}
+        shapes = {"dC": (m, n), "dX": (m, d), "dY": (n, d), "db": (n,)}
+        for k in want:
+            out[k] = torch.empty(shapes[k], dtype=T.dtype, device=T.device)
+        st = lib.sr_ot_grad(self._h, ct.byref(o), m, n, 0 if X is None else d, _ptr(X), _ptr(Y), None,
+                            _ptr(b), _ptr(T),
+                            _ptr(out.get("dC")), _ptr(out.get("dX")), _ptr(out.get("dY")),
+                            _ptr(out.get("db")))
+        self._check(st, allow=(OK,))
+        return out
+
+    def grad_batched(self, X, Y, b, T, sizes, offsets, want=("dX", "dY", "db"), d=3, opts=None, **kw):
+        """sr_ot_grad_batched over packed buffers (offsets as in solve_batched:
+        (off_X, off_Y, off_a, off_b, off_T) per instance). Returns packed dX,
+        dY, db laid out like X, Y, b."""
+        o = opts if opts is not None else options(**kw)
+        B = len(sizes)
+        mm = (ct.c_int * B)(*[int(s[0]) for s in sizes])
+        nn = (ct.c_int * B)(*[int(s[1]) for s in sizes])
+        oX = (ct.c_longlong * B)(*[int(v[0]) for v in offsets])
+        oY = (ct.c_longlong * B)(*[int(v[1]) for v in offsets])
+        ob = (ct.c_longlong * B)(*[int(v[3]) for v in offsets])
+        oT = (ct.c_longlong * B)(*[int(v[4]) for v in offsets])
+        out = {}
+        if "dX" in want:
+            out["dX"] = torch.zeros_like(X)
+        if "dY" in want:
+            out["dY"] = torch.zeros_like(Y)
+        if "db" in want:
+            out["db"] = torch.zeros_like(b)
+        st = lib.sr_ot_grad_batched(self._h, ct.byref(o), B, mm, nn, int(d), oX, oY, ob, oT, _ptr(X),
+                                    _ptr(Y), _ptr(b), _ptr(T), _ptr(out.get("dX")),
+                                    _ptr(out.get("dY")), _ptr(out.get("db")))
+        self._check(st, allow=(OK,))
+        return out
+
+    def cost_bf16(self, X, Y, C=None):
+        """sr_ot_cost_bf16: C = |x~|^2 + |y~|^2 - 2 X~ Y~^T on the tensor cores
+        (float32 X, Y; BF16-rounded inside). Returns C (m x n float32)."""
+        m, d = X.shape
+        n = Y.shape[0]
+        if C is None:
+            C = torch.empty((m, n), dtype=torch.float32, device=X.device)
+        st = lib.sr_ot_cost_bf16(self._h, m, n, d, _ptr(X), _ptr(Y), _ptr(C))
+        self._check(st, allow=(OK,))
+        return C

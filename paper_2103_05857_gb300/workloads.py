@@ -175,3 +175,31 @@ def workload(name: str, **override):
         return [colour_instance(p["seed"] * 100003 + 17 * k + 1, p["m"], p["n"], p["rho"])
                 for k in range(p["count"])]
     raise KeyError(name)
+
+
+def feasible_plan(seed: int, a: np.ndarray, n: int, support: int = 8) -> tuple:
+    """A sparse feasible plan for a: row i has `support` distinct random
+    columns with uniform positive weights scaled to sum to a_i (the shape of a
+    converged plan, whose rows carry few atoms). Returns (rows, cols, vals)
+    in row-major order."""
+    m = len(a)
+    support = min(support, n)
+    u = uniform(seed, 20, m * support).reshape(m, support)
+    # distinct columns per row: sorted draws of a stride pattern
+    base = (uniform(seed, 21, m) * n).astype(np.int64)
+    step = 1 + (uniform(seed, 22, m) * max(n // support - 1, 1)).astype(np.int64)
+    cols = (base[:, None] + step[:, None] * np.arange(support)[None, :]) % n
+    w = 0.05 + u
+    w = w / w.sum(1, keepdims=True) * np.asarray(a, dtype=np.float64)[:, None]
+    rows = np.repeat(np.arange(m), support)
+    return rows, cols.ravel(), w.ravel()
+
+
+def bf16_round(x) -> np.ndarray:
+    """Values rounded to bfloat16 (round to nearest, ties to even) from their
+    float32 images, returned as float64: the exact inputs a BF16 tensor-core
+    cost sees. Finite inputs only."""
+    f = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    b = f.view(np.uint32).astype(np.uint64)
+    b = (b + np.uint64(0x7FFF) + ((b >> np.uint64(16)) & np.uint64(1))) & np.uint64(0xFFFF0000)
+    return b.astype(np.uint32).view(np.float32).astype(np.float64).reshape(f.shape)

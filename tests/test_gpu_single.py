@@ -490,3 +490,28 @@ def test_not_converged_status(S, h):
                           X=dev(inst.X, torch.float32), Y=dev(inst.Y, torch.float32),
                           tol_rel_gap=1e-12, max_epochs=3)
     assert st == S.NOT_CONVERGED and res["status"] == S.NOT_CONVERGED and res["epochs"] == 3
+
+
+@pytest.mark.parametrize("variant,order", [("BCPFW", "CYCLIC"), ("BCPFW", "GAP_ADAPTIVE"),
+                                           ("BCAFW", "GAP_ADAPTIVE")])
+def test_fp32_dense_steps_conserve_row_mass(S, h, oracle_mod, variant, order):
+    """Thousands of FP32 away / pairwise steps on the dense row kernels keep
+    every row sum at a_i (the stopping test requires it): pairwise moves are
+    rounded so both entries change exactly, away steps take the other atoms'
+    stored mass instead of a_i - t_v. (Cyclic dense BCAFW, whose FW and away
+    steps rescale every entry in FP32, drifts by ~4e-5 over 8000 epochs; the
+    default BCAFW path keeps double-float atoms and does not.)"""
+    inst = W.colour_instance(79, 150, 210, rho=10.0, b_dirichlet=True).rounded()
+    C = oracle_mod.cost(inst.X, inst.Y)
+    _, ro, *_ = oracle_mod.solve(C, inst.a, inst.b, rho=inst.rho, variant=oracle_mod.BCPFW,
+                                 step=oracle_mod.ELS, max_epochs=50000, tol_rel_gap=1e-10, gap_every=5)
+    T = torch.zeros((inst.m, inst.n), dtype=torch.float32, device="cuda")
+    res = h.solve(dev(inst.a, torch.float32), dev(inst.b, torch.float32), T, X=dev(inst.X, torch.float32),
+                  Y=dev(inst.Y, torch.float32), precision=S.FP32, variant=getattr(S, variant), step=S.ELS,
+                  order=getattr(S, order), seed=3, rho=inst.rho, max_epochs=12000, tol_rel_gap=1e-6,
+                  dense_only=1)
+    assert res["status"] == S.OK and res["row_err"] <= 1e-5, res
+    Tc = host(T)
+    assert Tc.min() >= 0.0
+    assert np.abs(Tc.sum(1) - inst.a).max() <= 1e-5 * inst.a.max()
+    assert ro["f"] - 1e-9 <= res["objective"] <= ro["f"] * (1 + 1.2e-6)
