@@ -1,18 +1,26 @@
 """Benchmark: block-coordinate Frank-Wolfe solves of semi-relaxed OT on GB300.
 
-One step = one complete solve of the colour4096_fp32 workload (m = n = 4096
-RGB-like points from seeded 8-component Gaussian mixtures, Dirichlet(1)
-target weights, rho = 10, squared-Euclidean cost on the fly) to relative
-duality gap 1e-6, with the certificate (Thm 2) taken every epoch. `value` is
-block updates per second over the timed solves; `ms_per_step` is the time to
-gap. Inputs are resident in HBM when the timed region starts; L2 is flushed
-(256 MB write) between timed solves.
+Default (the headline): one step = one complete solve of colour4096_fp32
+(m = n = 4096 RGB-like points from seeded 8-component Gaussian mixtures,
+Dirichlet(1) target weights, rho = 10, squared-Euclidean cost on the fly)
+to relative duality gap 1e-6 with pairwise steps and the exact line search,
+the certificate (Thm 2) taken every epoch. `value` = block updates per
+second over the timed solves; `ms_per_step` = time to gap. Inputs are
+resident in HBM when the timed region starts; L2 is flushed (256 MB write)
+between timed steps.
+
+Other workloads (--workload):
+  colour256_fp64       FP64 BCFW, decay rule, cyclic, 200 epochs
+  colour_batch512      512 instances, m, n ~ U{64..2048}, one persistent launch
+  feature8192_d128     BF16 tensor-core cost (d = 128) + FP32 solve to 1e-6
+  colour_batch64_2048  64 x (2048 x 2048): batched solve + adjoint (backward)
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun with N > 1, every rank solves its own independent replica
-(a single solve does not shard: each block update reads the residual the
-previous one wrote); value = all ranks' block updates / max rank time.
+Under torchrun with N > 1: single-instance workloads run one replica per
+rank (weak scaling); batched workloads split the instances over the ranks
+by longest-processing-time-first on m*n (strong scaling). No data-path
+collective either way; value = all ranks' block updates / max rank time.
 """
 from __future__ import annotations
 
@@ -30,10 +38,13 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "block-updates/s to rel. duality gap 1e-6"
 UNIT = "block-updates/s"
 VARIANTS = {"BCFW": 0, "BCAFW": 1, "BCPFW": 2}
 L2_FLUSH_BYTES = 256 << 20
+SMS = 152                 # GB300: 2 dies x 76 SMs
+FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM
+FLOPS_PER_GRAD = 8        # d = 3 cost (3 sub, 3 mul/fma) + residual add + compare
+BATCH_WORKLOADS = ("colour_batch512", "colour_batch64_2048")
 
 
 def parse():
@@ -45,9 +56,9 @@ def parse():
     ap.add_argument("--workload", default="colour4096_fp32")
     ap.add_argument("--variant", default="BCPFW", choices=list(VARIANTS))
     ap.add_argument("--step-rule", default="ELS", choices=["DEC", "ELS"])
-    ap.add_argument("--tol", type=float, default=1e-6)
-    ap.add_argument("--max-epochs", type=int, default=6000)
-    ap.add_argument("--cpu-epochs", type=int, default=48, help="oracle sample size (epochs)")
+    ap.add_argument("--tol", type=float, default=None)
+    ap.add_argument("--max-epochs", type=int, default=None)
+    ap.add_argument("--cpu-epochs", type=int, default=None, help="oracle sample size (epochs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -66,17 +77,6 @@ def dist_setup():
     return ws, rank, local
 
 
-def allreduce_max(x, ws):
-    if ws == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    dev = "cuda" if torch.cuda.is_available() else "cpu"
-    t = torch.tensor([x], dtype=torch.float64, device=dev)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
-
-
 def barrier(ws):
     if ws > 1:
         import torch.distributed as dist
@@ -87,9 +87,15 @@ def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as fh:
-            d = json.load(fh)
-        return d, "measured"
-    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_peak_tflops(peaks):
+    """CUDA-core FP32 peak from unit counts and the maximum SM clock
+    (152 SMs x 128 lanes x 2 flops per FMA x clock)."""
+    return SMS * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
 
 
 class ClockSampler:
@@ -147,11 +153,6 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def load_instance(name):
-    from paper_2103_05857_gb300 import workloads as W
-    return W.workload(name).rounded()
-
-
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -159,16 +160,78 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
-def run_oracle_sample(inst, variant, step_rule, epochs):
-    """The FP64 oracle (single thread, as written) on `epochs` epochs of the
-    same workload, certificate every epoch. Returns (updates, seconds)."""
+# ---------------------------------------------------------------------------
+# Workload settings
+# ---------------------------------------------------------------------------
+def settings(args):
+    w = args.workload
+    s = {"variant": args.variant, "step": args.step_rule, "tol": 1e-6, "max_epochs": 6000,
+         "precision": "FP32", "cpu_epochs": 48, "cpu_rows": None}
+    if w == "colour256_fp64":
+        s.update(variant="BCFW", step="DEC", tol=0.0, max_epochs=200, precision="FP64", cpu_epochs=200)
+    elif w == "colour_batch512":
+        s.update(max_epochs=20000, cpu_epochs=20)
+    elif w == "feature8192_d128":
+        s.update(max_epochs=20000, precision="FP32_BF16COST", cpu_epochs=10, cpu_rows=512)
+    elif w == "colour_batch64_2048":
+        s.update(tol=1e-7, max_epochs=20000, cpu_epochs=10)
+    if args.tol is not None:
+        s["tol"] = args.tol
+    if args.max_epochs is not None:
+        s["max_epochs"] = args.max_epochs
+    if args.cpu_epochs is not None:
+        s["cpu_epochs"] = args.cpu_epochs
+    return s
+
+
+def load(name):
+    from paper_2103_05857_gb300 import workloads as W
+    x = W.workload(name)
+    if isinstance(x, list):
+        return [i.rounded() for i in x]
+    return x if name == "colour256_fp64" else x.rounded()
+
+
+def oracle_sample(insts, s):
+    """The FP64 oracle as written (single thread) on a bounded sample of the
+    workload: `cpu_epochs` epochs of the first instance (for the feature
+    workload, of its first `cpu_rows` rows against all n columns: a block
+    update's cost depends on n only). Returns (updates, seconds, text)."""
     from oracle import oracle as O
     O.build()
+    inst = insts[0] if isinstance(insts, list) else insts
+    X, a = inst.X, inst.a
+    if s["cpu_rows"]:
+        X, a = X[: s["cpu_rows"]], a[: s["cpu_rows"]]
     t0 = time.perf_counter()
-    C = O.cost(inst.X, inst.Y)
-    _, res, *_ = O.solve(C, inst.a, inst.b, rho=inst.rho, variant=VARIANTS[variant],
-                         step=1 if step_rule == "ELS" else 0, max_epochs=epochs, gap_every=1)
-    return res["updates"], time.perf_counter() - t0
+    C = O.cost(X, inst.Y)
+    _, res, *_ = O.solve(C, a, inst.b, rho=inst.rho, variant=VARIANTS[s["variant"]],
+                         step=1 if s["step"] == "ELS" else 0, max_epochs=s["cpu_epochs"], gap_every=1)
+    dt = time.perf_counter() - t0
+    text = (f"{s['cpu_epochs']} epochs ({res['updates']} block updates) of {s['variant']}-{s['step']} "
+            f"on a {len(a)} x {inst.n} instance of the workload, FP64 oracle incl. cost and "
+            f"certificates, {dt:.1f} s on 1 of {cpu_cores()} host cores")
+    return res["updates"], dt, text
+
+
+def metric_for(s):
+    if s["tol"] > 0:
+        return f"block-updates/s to rel. duality gap {s['tol']:g}"
+    return f"block-updates/s over {s['max_epochs']} epochs"
+
+
+def config_for(args, s, insts, ws):
+    """The `config` object of both arms' JSON lines."""
+    cfg = {"workload": args.workload, "variant": f"{s['variant']}-{s['step']}", "order": "cyclic",
+           "precision": s["precision"], "tol_rel_gap": s["tol"], "max_epochs": s["max_epochs"],
+           "certificate_every_epochs": 1, "l2": "flushed (256 MB write) between steps"}
+    if isinstance(insts, list):
+        cfg.update(instances=len(insts), m_range=[min(i.m for i in insts), max(i.m for i in insts)],
+                   n_range=[min(i.n for i in insts), max(i.n for i in insts)], d=3, rho=insts[0].rho,
+                   backward=args.workload == "colour_batch64_2048", parallelism=f"lpt{ws}")
+    else:
+        cfg.update(m=insts.m, n=insts.n, d=int(insts.X.shape[1]), rho=insts.rho, parallelism=f"replicas{ws}")
+    return cfg
 
 
 # ---------------------------------------------------------------------------
@@ -176,159 +239,270 @@ def bench_reference(args, ws, rank):
     """The oracle timed on the host cores: K steps, each a bounded sample."""
     if rank != 0:
         return
-    inst = load_instance(args.workload)
-    ep = max(1, args.cpu_epochs // 4)
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        run_oracle_sample(inst, args.variant, args.step_rule, 1)
-    tot_u, tot_s = 0, 0.0
+    s = settings(args)
+    insts = load(args.workload)
+    small = dict(s)
+    small["cpu_epochs"] = 1
+    oracle_sample(insts, small)
+    tot_u, tot_s, text = 0, 0.0, ""
     for _ in range(args.steps):
-        u, s = run_oracle_sample(inst, args.variant, args.step_rule, ep)
+        u, dt, text = oracle_sample(insts, s)
         tot_u += u
-        tot_s += s
+        tot_s += dt
     v = tot_u / tot_s
-    sample = (f"{ep} epochs ({ep * inst.m} block updates) of {args.variant}-{args.step_rule} "
-              f"on {args.workload} per step, FP64 oracle, certificate every epoch")
     line = {
-        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "impl": "reference", "metric": metric_for(s), "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "m": inst.m, "n": inst.n, "rho": inst.rho,
-                   "variant": args.variant, "step_rule": args.step_rule},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "config": config_for(args, s, insts, ws),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": text},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def bench_ours(args, ws, rank, local):
+# ---------------------------------------------------------------------------
+class Harness:
+    """Warm-up, timed steps (CUDA events on the handle's stream, L2 flushed
+    before each step, barrier + synchronize on both sides), clocks, launches."""
+
+    def __init__(self, h, dev, stream, ws):
+        import torch
+        self.torch = torch
+        self.h, self.dev, self.stream, self.ws = h, dev, stream, ws
+        self.flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def run(self, step, steps, warmup, profile_kinds=()):
+        torch = self.torch
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize(self.dev)
+        clocks = ClockSampler(self.dev.index)
+        clocks.start()
+        self.h.profile(True)
+        l0 = self.h.launch_count()
+        out, ms = [], []
+        for _ in range(steps):
+            self.flush.zero_()
+            barrier(self.ws)
+            torch.cuda.synchronize(self.dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            out.append(step())
+            e1.record(self.stream)
+            torch.cuda.synchronize(self.dev)
+            ms.append(e0.elapsed_time(e1))
+        barrier(self.ws)
+        launches = self.h.launch_count() - l0
+        prof = {k: self.h.profile_read(k) for k in profile_kinds}
+        self.h.profile(False)
+        return out, ms, launches, prof, clocks.stop()
+
+    def e2e(self, step_with_copies, steps):
+        torch = self.torch
+        ms = []
+        for _ in range(steps):
+            self.flush.zero_()
+            barrier(self.ws)
+            torch.cuda.synchronize(self.dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            step_with_copies()
+            e1.record(self.stream)
+            torch.cuda.synchronize(self.dev)
+            ms.append(e0.elapsed_time(e1))
+        return ms
+
+
+def alu_roofline(flops, avg_ms, peaks, peak_src, kernel, extra=None):
+    peak = fp32_peak_tflops(peaks)
+    achieved = flops / (avg_ms / 1e3) / 1e12
+    r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+         "traffic": None, "peak_source": f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                                        f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({peak_src} clock)",
+         "kernel": kernel, "avg_launch_ms": avg_ms}
+    if extra:
+        r.update(extra)
+    return r
+
+
+def hbm_roofline(nbytes, avg_ms, peaks, peak_src, kernel, extra=None):
+    achieved = nbytes / (avg_ms / 1e3) / 1e9
+    r = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+         "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": peak_src,
+         "kernel": kernel, "avg_launch_ms": avg_ms}
+    if extra:
+        r.update(extra)
+    return r
+
+
+def bench_single(args, s, ws, rank, local):
+    """One instance per rank (replicas): colour4096_fp32, colour256_fp64,
+    feature8192_d128."""
     import torch
     from paper_2103_05857_gb300 import sr_ot as S
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    inst = load_instance(args.workload)
-    m, n = inst.m, inst.n
+    inst = load(args.workload)
+    m, n, d = inst.m, inst.n, inst.X.shape[1]
+    fp64 = s["precision"] == "FP64"
+    dt = torch.float64 if fp64 else torch.float32
+    npdt = np.float64 if fp64 else np.float32
     stream = torch.cuda.current_stream(dev)
     h = S.Handle(local, stream)
+    H = Harness(h, dev, stream, ws)
 
-    # pinned host copies (for the end-to-end leg) and resident device copies
-    hX = torch.from_numpy(inst.X.astype(np.float32)).pin_memory()
-    hY = torch.from_numpy(inst.Y.astype(np.float32)).pin_memory()
-    ha = torch.from_numpy(inst.a.astype(np.float32)).pin_memory()
-    hb = torch.from_numpy(inst.b.astype(np.float32)).pin_memory()
-    hT = torch.empty((m, n), dtype=torch.float32).pin_memory()
+    hX, hY, ha, hb = (torch.from_numpy(np.ascontiguousarray(v, dtype=npdt)).pin_memory()
+                      for v in (inst.X, inst.Y, inst.a, inst.b))
+    hT = torch.empty((m, n), dtype=dt).pin_memory()
     X, Y, a, b = (t.to(dev) for t in (hX, hY, ha, hb))
-    T = torch.zeros((m, n), dtype=torch.float32, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    T = torch.zeros((m, n), dtype=dt, device=dev)
+    opts = S.options(variant=VARIANTS[s["variant"]], step=1 if s["step"] == "ELS" else 0, order=S.CYCLIC,
+                     precision=getattr(S, s["precision"]), rho=inst.rho, tol_rel_gap=s["tol"],
+                     max_epochs=s["max_epochs"], gap_every=1, refresh_every=1)
 
-    opts = S.options(variant=VARIANTS[args.variant], step=1 if args.step_rule == "ELS" else 0,
-                     order=S.CYCLIC, precision=S.FP32, rho=inst.rho, tol_rel_gap=args.tol,
-                     max_epochs=args.max_epochs, gap_every=1, refresh_every=1)
-
-    def solve_once():
+    def step():
         return h.solve(a, b, T, X=X, Y=Y, opts=opts)
 
-    for _ in range(args.warmup):
-        solve_once()
-    torch.cuda.synchronize(dev)
+    out, ms, launches, prof, clk = H.run(step, args.steps, args.warmup,
+                                         (S.PROF_EPOCH, S.PROF_CERT, S.PROF_COST))
+    updates = sum(r["block_updates"] for r in out)
+    from paper_2103_05857_gb300.shard import gather_max
+    tot_max = gather_max(sum(ms), ws)
+    value = updates * ws / (tot_max / 1e3)
 
-    # ---- timed region: inputs resident in HBM --------------------------------
-    clocks = ClockSampler(local)
-    clocks.start()
-    h.profile(True)
-    launches0 = h.launch_count()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    results = []
-    for k in range(args.steps):
-        flush.zero_()
-        barrier(ws)
-        torch.cuda.synchronize(dev)
-        ev[k][0].record(stream)
-        results.append(solve_once())
-        ev[k][1].record(stream)
-        torch.cuda.synchronize(dev)
-    launches = h.launch_count() - launches0
-    ep_ms, ep_groups = h.profile_read(S.PROF_EPOCH)
-    ce_ms, ce_groups = h.profile_read(S.PROF_CERT)
-    h.profile(False)
-    clk = clocks.stop()
-    step_ms = [e[0].elapsed_time(e[1]) for e in ev]
-    tot_ms = sum(step_ms)
-    updates = sum(r["block_updates"] for r in results)
-    tot_ms_max = allreduce_max(tot_ms, ws)
-    updates_all = updates * ws
-    value = updates_all / (tot_ms_max / 1e3)
-
-    # ---- end to end through the public API with host buffers -----------------
-    e2e_ms = []
-    for k in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize(dev)
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
+    def step_e2e():
         X.copy_(hX, non_blocking=True)
         Y.copy_(hY, non_blocking=True)
         a.copy_(ha, non_blocking=True)
         b.copy_(hb, non_blocking=True)
-        r = h.solve(a, b, T, X=X, Y=Y, opts=opts)
+        h.solve(a, b, T, X=X, Y=Y, opts=opts)
         hT.copy_(T, non_blocking=True)
-        t1.record(stream)
-        torch.cuda.synchronize(dev)
-        e2e_ms.append(t0.elapsed_time(t1))
-    e2e_updates = updates / args.steps * args.steps
-    e2e_value = updates_all / (allreduce_max(sum(e2e_ms), ws) / 1e3)
-    h2d = sum(t.numel() * 4 for t in (hX, hY, ha, hb))
+
+    e2e_ms = H.e2e(step_e2e, args.steps)
+    e2e_value = updates * ws / (gather_max(sum(e2e_ms), ws) / 1e3)
+    h2d = sum(t.numel() * t.element_size() for t in (hX, hY, ha, hb))
+    d2h = hT.numel() * hT.element_size()
+
+    peaks, peak_src = measured_peaks()
+    ep_ms, ep_n = prof[S.PROF_EPOCH]
+    ce_ms, ce_n = prof[S.PROF_CERT]
+    co_ms, co_n = prof[S.PROF_COST]
+    avg = ep_ms / max(ep_n, 1)
+    supp = float((T > 0).sum().item()) / m
+    extra = {"launches": ep_n, "chain_ns_per_update": 1e6 * avg / m, "cert_avg_ms": ce_ms / max(ce_n, 1),
+             "hbm_bytes_per_update": 8 * supp, "mean_support": supp}
+    kname = ("k_epoch_sparse (one CTA, m block updates; active-set, pairwise)" if s["variant"] != "BCFW"
+             else "k_epoch (one CTA, m block updates; dense rows)")
+    roof = alu_roofline(FLOPS_PER_GRAD * n * m, avg, peaks, peak_src, kname, extra)
+    cfg = config_for(args, s, inst, ws)
+    line = {"metric": metric_for(s),
+            "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tot_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if fp64 else "f32", "data": "synthetic", "config": cfg,
+            "time_to_gap_s": tot_max / args.steps / 1e3,
+            "epochs_per_solve": [r["epochs"] for r in out],
+            "final_rel_gap": [r["rel_gap"] for r in out],
+            "converged": all(r["status"] == 0 for r in out),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "roofline": roof, "clocks": clk}
+    if co_n:
+        co_avg = co_ms / co_n
+        line["roofline_cost"] = hbm_roofline(4.0 * m * n + 4.0 * (m + n) * d + 2.0 * (m + n) * d, co_avg,
+                                             peaks, peak_src, "k_round_bf16 x2 + k_cost_umma (tcgen05)",
+                                             {"tflops_bf16": 2.0 * m * n * d / (co_avg / 1e3) / 1e12})
+    h.close()
+    return line, inst
+
+
+def bench_batch(args, s, ws, rank, local):
+    """colour_batch512 and colour_batch64_2048: this rank's share of the
+    instances in one persistent launch (plus the adjoint for the latter)."""
+    import torch
+    from paper_2103_05857_gb300 import sr_ot as S
+    from paper_2103_05857_gb300.batch import PackedBatch
+    from paper_2103_05857_gb300.shard import gather_max, gather_sum, lpt_partition
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    allinst = load(args.workload)
+    share = lpt_partition([i.m * i.n for i in allinst], ws)[rank]
+    insts = [allinst[k] for k in share]
+    stream = torch.cuda.current_stream(dev)
+    h = S.Handle(local, stream)
+    H = Harness(h, dev, stream, ws)
+    pb = PackedBatch(insts, device=dev, pin=True)
+    hT = torch.empty(pb.total_T, dtype=torch.float32).pin_memory()
+    kw = dict(variant=VARIANTS[s["variant"]], step=1 if s["step"] == "ELS" else 0, rho=insts[0].rho,
+              tol_rel_gap=s["tol"], max_epochs=s["max_epochs"], gap_every=1)
+    backward = args.workload == "colour_batch64_2048"
+
+    def step():
+        st, res = h.solve_batched(pb.X, pb.Y, pb.a, pb.b, pb.T, pb.sizes, pb.offsets, **kw)
+        if backward:
+            h.grad_batched(pb.X, pb.Y, pb.b, pb.T, pb.sizes, pb.offsets, rho=insts[0].rho, precision=S.FP32)
+        return res
+
+    out, ms, launches, prof, clk = H.run(step, args.steps, args.warmup, (S.PROF_BATCH, S.PROF_GRAD))
+    updates = sum(r["block_updates"] for res in out for r in res)
+    tot_max = gather_max(sum(ms), ws)
+    updates_all = gather_sum(updates, ws)
+    value = updates_all / (tot_max / 1e3)
+
+    def step_e2e():
+        pb.X.copy_(pb.hX, non_blocking=True)
+        pb.Y.copy_(pb.hY, non_blocking=True)
+        pb.a.copy_(pb.ha, non_blocking=True)
+        pb.b.copy_(pb.hb, non_blocking=True)
+        step()
+        hT.copy_(pb.T, non_blocking=True)
+
+    e2e_ms = H.e2e(step_e2e, args.steps)
+    e2e_value = updates_all / (gather_max(sum(e2e_ms), ws) / 1e3)
+    h2d = sum(t.numel() * 4 for t in (pb.hX, pb.hY, pb.ha, pb.hb))
     d2h = hT.numel() * 4
 
-    # ---- roofline of the dominant kernel (the epoch kernel) --------------------
     peaks, peak_src = measured_peaks()
-    per_update_bytes = 4 * n + 8  # FP32 row of T read once, the two changed entries written
-    if args.variant != "BCPFW":
-        per_update_bytes = 4 * n + 4 * n  # dense convex combination rewrites the row support
-    launch_bytes = per_update_bytes * m
-    avg_launch_ms = ep_ms / max(ep_groups, 1)
-    achieved = launch_bytes / (avg_launch_ms / 1e3) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                "peak_source": peak_src, "kernel": "k_epoch (one CTA, m block updates)",
-                "avg_launch_ms": avg_launch_ms, "launches": ep_groups,
-                "cert_avg_ms": ce_ms / max(ce_groups, 1),
-                "chain_ns_per_update": 1e6 * avg_launch_ms / m}
+    b_ms, b_n = prof[S.PROF_BATCH]
+    flops = FLOPS_PER_GRAD * sum(r["block_updates"] * insts[k].n for res in out for k, r in enumerate(res))
+    roof = alu_roofline(flops / max(len(out), 1), b_ms / max(b_n, 1), peaks, peak_src,
+                        "k_batched (persistent, one CTA per instance at a time)",
+                        {"launches": b_n, "instances": len(insts)})
+    res0 = out[-1]
+    line = {"metric": metric_for(s),
+            "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tot_max / args.steps, "higher_is_better": True,
+            "scaling": "strong" if ws > 1 else "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": config_for(args, s, allinst, ws),
+            "converged": sum(r["status"] == 0 for r in res0), "instances_on_rank0": len(insts),
+            "epochs_max": max(r["epochs"] for r in res0), "epochs_median": float(np.median([r["epochs"] for r in res0])),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "roofline": roof, "clocks": clk}
+    g_ms, g_n = prof[S.PROF_GRAD]
+    if g_n:
+        tbytes = 4.0 * pb.total_T + 4.0 * sum(3 * (i.m + i.n) * 2 + i.n * 2 for i in insts)
+        line["roofline_adjoint"] = hbm_roofline(tbytes, g_ms / g_n, peaks, peak_src,
+                                                "k_adj_tiles + k_adj_cols + k_adj_rows", {"launches": g_n})
+    h.close()
+    return line, allinst
 
-    line = None
+
+def bench_ours(args, ws, rank, local):
+    s = settings(args)
+    if args.workload in BATCH_WORKLOADS:
+        line, insts = bench_batch(args, s, ws, rank, local)
+    else:
+        line, insts = bench_single(args, s, ws, rank, local)
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
-            u, s = run_oracle_sample(inst, args.variant, args.step_rule, args.cpu_epochs)
-            cpu = {"value": u / s, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"{args.cpu_epochs} epochs ({u} block updates) of {args.variant}-"
-                             f"{args.step_rule} on {args.workload}, FP64, certificate every epoch, "
-                             f"{s:.1f} s on 1 of {cpu_cores()} host cores"}
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": tot_ms_max / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": args.workload, "m": m, "n": n, "d": 3, "rho": inst.rho,
-                       "variant": f"{args.variant}-{args.step_rule}", "order": "cyclic",
-                       "tol_rel_gap": args.tol, "certificate_every_epochs": 1,
-                       "parallelism": f"replicas{ws}", "l2": "flushed (256 MB write) between solves"},
-            "time_to_gap_s": tot_ms_max / args.steps / 1e3,
-            "epochs_per_solve": [r["epochs"] for r in results],
-            "final_rel_gap": [r["rel_gap"] for r in results],
-            "converged": all(r["status"] == 0 for r in results),
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches,
-            "roofline": roofline,
-            "cpu_baseline": cpu,
-            "clocks": clk,
-        }
+            u, dt, text = oracle_sample(insts, s)
+            cpu = {"value": u / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": text}
+        line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
-    h.close()
     return line
 
 

@@ -216,7 +216,7 @@ sr_ot_status sr_ot_gap(sr_ot_handle h, const sr_ot_options *opts, int m, int n, 
  * built on the tensor cores from BF16-rounded points with FP32 accumulation
  * and FP32 norms of the rounded points: C = |x~|^2 + |y~|^2 - 2 X~ Y~^T.
  * X (m x d), Y (n x d) are float; d must be a multiple of 64. The paper uses
- * the Euclidean cost of colour centroids (Sec. 6.1); the GEMM form is this
+ * the Euclidean cost of colour centroids (Sec. 5.1); the GEMM form is this
  * library's route for feature dimensions d >= 64.
  */
 sr_ot_status sr_ot_cost_bf16(sr_ot_handle h, int m, int n, int d, const float *X,

@@ -113,7 +113,7 @@ def permutation(seed: int, epoch: int, m: int) -> np.ndarray:
 
 
 def cost(X, Y, squared: bool = True) -> np.ndarray:
-    """C_ij = ||x_i - y_j||^2 (squared) or ||x_i - y_j|| (Sec. 6.1)."""
+    """C_ij = ||x_i - y_j||^2 (squared) or ||x_i - y_j|| (Sec. 5.1)."""
     X, Y = _f64(X), _f64(Y)
     m, d = X.shape
     n = Y.shape[0]

@@ -64,7 +64,7 @@ static int or_scale(uint64_t u, int m) {
 /* ---------------------------------------------------------------------------
  * Cost: C_ij = ||x_i - y_j||_2^2 (squared Euclidean), summed over the
  * feature axis in ascending order. The paper's colour experiments use the
- * non-squared distance (Sec. 6.1); the squared cost is this library's
+ * non-squared distance (Sec. 5.1); the squared cost is this library's
  * workload and is selected by `squared` = 1 (0 takes the square root).
  * ------------------------------------------------------------------------- */
 void srot_or_cost(int m, int n, int d, const double *X, const double *Y,

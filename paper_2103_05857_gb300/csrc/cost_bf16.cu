@@ -6,7 +6,7 @@
 // x~, y~ = the points rounded to BF16 (round to nearest even), the inner
 // products accumulated in FP32 in tensor memory, the norms of the rounded
 // points summed in FP32. The paper's costs are Euclidean distances between
-// colour centroids (Sec. 6.1); this GEMM form is the library's route for the
+// colour centroids (Sec. 5.1); this GEMM form is the library's route for the
 // squared cost of high-dimensional features.
 //
 // Kernel: one CTA of 4 warps per 128 x 128 tile of C. With d <= 256 the whole

@@ -1,7 +1,7 @@
 """Seeded synthetic inputs shaped like the paper's colour-transfer workloads.
 
 The paper's inputs are k-means colour centroids of two public photographs with
-histogram weights (Sec. 6.1); the photographs are not available, so these
+histogram weights (Sec. 5.1); the photographs are not available, so these
 generators stand in for them: RGB-like point clouds in [0,1]^3 drawn from
 seeded Gaussian mixtures (source and reference palettes use different
 mixtures), uniform or Dirichlet(1) weights, and a clustered feature-space

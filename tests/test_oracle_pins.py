@@ -512,3 +512,19 @@ def test_paper_printed_iterates_are_feasible():
         Tb = np.array(it["T_paper"]).T  # build orientation
         np.testing.assert_allclose(Tb.sum(1), target, atol=0.011, err_msg=it["where"])
         assert Tb.min() >= 0
+
+
+def test_gap_adaptive_sampling_support(oracle_mod):
+    """Alg. A.4 draws block i with probability proportional to max(g_i, 0):
+    rows of zero weight (g_i = 0 at every feasible T) are never drawn, and
+    every row with a positive gap is drawn within a few epochs."""
+    X, Y, a, b, rho = random_problem(11, 12, 9, 5.0)
+    a = a.copy()
+    a[::3] = 0.0
+    a /= a.sum()
+    C = oracle_mod.cost(X, Y)
+    _, _, ti, _, _ = oracle_mod.solve(C, a, b, rho=rho, variant=oracle_mod.BCFW, step=oracle_mod.ELS,
+                                      order=oracle_mod.GAP, seed=3, max_epochs=6, trace=True)
+    drawn = set(ti.tolist())
+    assert not drawn & set(range(0, 12, 3))
+    assert drawn == {i for i in range(12) if i % 3}
