@@ -96,7 +96,10 @@ typedef struct {
     long long trace_capacity;
     int dense_only;           /* 1: FP32 away/pairwise solves keep the dense row
                                  kernel instead of the active-set kernel          */
-    int reserved;
+    int pipeline;             /* 1: FP32 pairwise solves use the pipelined
+                                 active-set kernel (the next row's LMO overlaps
+                                 the current update); same decisions as the
+                                 default two-phase kernel                          */
 } sr_ot_options;
 
 typedef struct {

@@ -78,6 +78,7 @@ __device__ inline AtomStats atom_stats(LaneAtoms &A, GradF grad, float ai, bool 
     }
     *t_v_df = tv;
     S.t_v = tv.hi;
+    S.vpos = vl;
     S.g_aw = S.s2 = S.dda = 0.f;
     if (want_sums) {
         float aw = 0.f, s2 = 0.f, dd = 0.f;
@@ -97,8 +98,9 @@ __device__ inline AtomStats atom_stats(LaneAtoms &A, GradF grad, float ai, bool 
     return S;
 }
 
-// Weight of column js among the atoms (0 if absent) and whether it is one.
-__device__ inline float atom_weight(const LaneAtoms &A, int js, bool *present) {
+// Weight of column js among the atoms (0 if absent) and whether it is one;
+// *pos (optional) receives its position in the record (-1 if absent).
+__device__ inline float atom_weight(const LaneAtoms &A, int js, bool *present, int *pos = nullptr) {
     const unsigned FULL = 0xffffffffu;
     int where = -1;
     {
@@ -112,7 +114,79 @@ __device__ inline float atom_weight(const LaneAtoms &A, int js, bool *present) {
     const int src = where >= 0 ? (where & 31) : 0;
     const float h = __shfl_sync(FULL, (where >> 5) > 0 ? A.t[1].hi : A.t[0].hi, src);
     *present = where >= 0;
+    if (pos) *pos = where;
     return where < 0 ? 0.f : h;
+}
+
+// Pairwise step (Alg. A.3) on the atom record: only the atoms j* and v
+// change, so only the lanes holding them work. The moved mass is added to j*
+// (appended at the end of the record when it enters) and taken from v with
+// double-float arithmetic as in apply_atoms; an atom whose weight reaches 0
+// is removed by moving the last atom into its place (the record's order
+// carries no meaning: every reduction over it is by column). Plan entries
+// and the residual pair change exactly as in apply_atoms. jpos, vpos: the
+// record positions of j* (-1 if absent) and v. Returns false (and changes
+// nothing) if j* would be atom 64.
+__device__ inline bool apply_pairwise(const Step<float> &S, const LaneAtoms &A, int jpos, int vpos, DF t_v,
+                                      float rho, float *trow, float *qh, float *ql, int4 *grec, int lane) {
+    const unsigned FULL = 0xffffffffu;
+    if (S.kind != 2 || S.v == S.js || vpos < 0) return true;
+    const bool grows = S.add_js > 0.f;
+    const bool append = grows && jpos < 0;
+    if (append && A.cnt >= kAtomsMax) return false;
+    const DF mv = S.drop ? t_v : DF{S.add_js, 0.f};
+    // old weights of j* and v, from the lanes holding them
+    const int jsrc = jpos >= 0 ? (jpos & 31) : 0;
+    const float jh = __shfl_sync(FULL, (jpos >> 5) > 0 ? A.t[1].hi : A.t[0].hi, jsrc);
+    const float jl = __shfl_sync(FULL, (jpos >> 5) > 0 ? A.t[1].lo : A.t[0].lo, jsrc);
+    const DF tj_old = jpos >= 0 ? DF{jh, jl} : DF{0.f, 0.f};
+    const DF tj_new = grows ? df_add(tj_old, mv) : tj_old;
+    const DF tv_new = S.drop ? DF{0.f, 0.f} : df_add(t_v, DF{-mv.hi, -mv.lo});
+    // plan entries and residual: lane 0 takes j*, lane 1 takes v
+    if (lane < 2) {
+        const int col = lane == 0 ? S.js : S.v;
+        const DF told = lane == 0 ? tj_old : t_v;
+        const DF tn = lane == 0 ? tj_new : tv_new;
+        if (tn.hi != told.hi || tn.lo != told.lo) {
+            trow[col] = tn.hi;
+            const float dlt = __fadd_rn(__fsub_rn(tn.hi, told.hi), __fsub_rn(tn.lo, told.lo));
+            const float d = rho * dlt;
+            const float y = __fsub_rn(d, ql[col]);
+            const float tt = __fadd_rn(qh[col], y);
+            ql[col] = __fsub_rn(__fsub_rn(tt, qh[col]), y);
+            qh[col] = tt;
+        }
+    }
+    // record: positions of j* and v after the step
+    int cnt = A.cnt;
+    const int jp = append ? cnt : jpos;
+    if (append) ++cnt;
+    const bool vgone = !(tv_new.hi > 0.f);
+    int4 *rec = grec + 1;
+    if (lane == 0 && jp >= 0 && (grows || append))
+        rec[jp] = make_int4(S.js, __float_as_int(tj_new.hi), __float_as_int(tj_new.lo), 0);
+    if (!vgone) {
+        if (lane == 1) rec[vpos] = make_int4(S.v, __float_as_int(tv_new.hi), __float_as_int(tv_new.lo), 0);
+    } else {
+        const int last = cnt - 1;
+        if (last != vpos) {
+            // move the last atom into v's place; it is j* when j* was just appended
+            int4 e;
+            if (last == jp) {
+                e = make_int4(S.js, __float_as_int(tj_new.hi), __float_as_int(tj_new.lo), 0);
+            } else {
+                const int src = last & 31, sl = last >> 5;
+                const int jj = __shfl_sync(FULL, sl ? A.j[1] : A.j[0], src);
+                const float hh = __shfl_sync(FULL, sl ? A.t[1].hi : A.t[0].hi, src);
+                const float ll = __shfl_sync(FULL, sl ? A.t[1].lo : A.t[0].lo, src);
+                e = make_int4(jj, __float_as_int(hh), __float_as_int(ll), 0);
+            }
+            if (lane == 1) rec[vpos] = e;
+        }
+        cnt = last;
+    }
+    if (lane == 0 && cnt != A.cnt) grec[0] = make_int4(cnt, 0, 0, 0);
+    return true;
 }
 
 // Apply step S of row i: atoms (with j* appended when it enters), dense

@@ -143,6 +143,9 @@ constexpr int kAtomRecord = 64;
 
 // Sparse-support epoch (FP32, away / pairwise steps). False if n is too large.
 bool launch_epoch_sparse(const EpochArgs<float> &args, cudaStream_t st);
+// Pipelined sparse-support epoch for pairwise steps (the next row's argmin
+// overlaps the current update). False unless BCPFW and n fits.
+bool launch_epoch_pipe(const EpochArgs<float> &args, cudaStream_t st);
 
 // Atom records of a dense plan; *overflow becomes 1 if a row has > 63 atoms.
 void launch_build_atoms(int m, int n, const float *T, int4 *rec, int *overflow, cudaStream_t st);

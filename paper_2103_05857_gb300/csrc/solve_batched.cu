@@ -264,7 +264,8 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_batched(BatchArgs B) {
                     const int js = __reduce_min_sync(FULL, e.kmin == wk ? e.jmin : 0x7FFFFFFF);
                     const float gmin_all = key2f(wk);
                     bool present = false;
-                    const float t_js = atom_weight(at_cur, js, &present);
+                    int jpos = -1;
+                    const float t_js = atom_weight(at_cur, js, &present, &jpos);
                     bool stop = false;
                     if (!isfinite(gmin_all)) {
                         if (lane == 0) sflag[0] = kInstNonFinite;
@@ -275,8 +276,13 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_batched(BatchArgs B) {
                         S = B.variant == SR_OT_BCPFW
                                 ? decide_pairwise(st, gmin_all, js, ai, rho, gmx, inv, n)
                                 : decide_atoms(st, gmin_all, js, t_js, ai, B.variant, B.step, rho, m, k);
-                    if (!stop && !apply_atoms(S, at_cur, present, t_vdf, ai, rho, T + (size_t)i * n, qh, ql,
-                                              grec + (size_t)i * kAtomRecord, lane)) {
+                    const bool applied =
+                        stop || (B.variant == SR_OT_BCPFW
+                                     ? apply_pairwise(S, at_cur, jpos, st.vpos, t_vdf, rho, T + (size_t)i * n, qh,
+                                                      ql, grec + (size_t)i * kAtomRecord, lane)
+                                     : apply_atoms(S, at_cur, present, t_vdf, ai, rho, T + (size_t)i * n, qh, ql,
+                                                   grec + (size_t)i * kAtomRecord, lane));
+                    if (!applied) {
                         if (lane == 0) sflag[0] = kInstNeedsDense;
                     }
                     if (p + 1 < m && i_next == i) {  // the same row again: reload it

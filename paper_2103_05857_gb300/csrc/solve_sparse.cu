@@ -32,6 +32,7 @@
 
 #include "atoms.cuh"
 #include "common.cuh"
+#include "cpasync.cuh"
 #include "internal.h"
 #include "step.cuh"
 
@@ -40,23 +41,6 @@ namespace srot {
 namespace {
 
 constexpr int kSmemMax = 227 * 1024;
-
-struct SpRed {
-    uint32_t kmin;
-    int jmin;
-};
-
-__device__ inline void cp16(void *smem_dst, const void *gsrc) {
-    unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc));
-}
-__device__ inline void cp4(void *smem_dst, const void *gsrc) {
-    unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc));
-}
-__device__ inline void commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ inline void wait_groups() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
 }  // namespace
 
@@ -308,7 +292,8 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_sparse(EpochArgs<float
             const int js = __reduce_min_sync(FULL, e.kmin == wk ? e.jmin : 0x7FFFFFFF);
             const float gmin_all = key2f(wk);
             bool present = false;
-            const float t_js = atom_weight(at, js, &present);
+            int jpos = -1;
+            const float t_js = atom_weight(at, js, &present, &jpos);
             bool stop = false;
             if (!isfinite(gmin_all)) {
                 if (lane == 0) {
@@ -321,8 +306,12 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_sparse(EpochArgs<float
             if (!stop)
                 S = PAIR ? decide_pairwise(st, gmin_all, js, ac, rho, gmx, inv, n)
                          : decide_atoms(st, gmin_all, js, t_js, ac, A.variant, A.step, rho, m, k);
-            if (!stop && !apply_atoms(S, at, present, t_vdf, ac, rho, A.T + (size_t)i * n, qh, ql,
-                                      grec + (size_t)i * kAtomRecord, lane)) {
+            const bool applied =
+                stop || (PAIR ? apply_pairwise(S, at, jpos, st.vpos, t_vdf, rho, A.T + (size_t)i * n, qh, ql,
+                                               grec + (size_t)i * kAtomRecord, lane)
+                              : apply_atoms(S, at, present, t_vdf, ac, rho, A.T + (size_t)i * n, qh, ql,
+                                            grec + (size_t)i * kAtomRecord, lane));
+            if (!applied) {
                 if (lane == 0) {
                     sflag[0] = 2;  // j* would be a 64th atom: the dense kernel takes over here
                     if (A.resume) *A.resume = p;

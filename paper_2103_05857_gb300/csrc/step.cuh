@@ -254,6 +254,7 @@ __device__ inline DF apply_atom(const Step<float> &S, int j, DF t, DF mv, float 
 struct AtomStats {
     float gmax, g_aw, s2, dda, t_v;
     int v, nnz;
+    int vpos;  // position of v in the atom record (-1 if none)
 };
 
 // Decision of one block update from the atom statistics (Alg. 1 / A.2 with
