@@ -11,15 +11,17 @@
 // The paper does not differentiate its solver; this is the library's backward
 // pass.
 //
-// One pass reads T once. A CTA of 256 threads owns a tile of `rh` rows x 256
-// columns (one column per thread). Per row it accumulates the column partials
-// t_ij (x_i, 1) in registers and forms the row partials t_ij (y_j, 1), which a
-// warp reduce-scatter (31 shuffles for 32 values) folds across the warp's 32
-// columns for R = 32 / P rows at a time, P = the padded width d + 1. The
-// per-warp row partials are summed in a fixed order in shared memory; column
-// partials (per row band) and row partials (per column tile) go to a
-// workspace, and two small kernels reduce them in FP64 in a fixed order, so
-// the result does not depend on scheduling.
+// One pass reads T once. A CTA of 8 warps owns a tile of `rh` rows x TW
+// columns, TW = 32 lanes x CPT columns per lane (16 bytes of T per lane per
+// row: 4 FP32 or 2 FP64 columns; one column when d + 1 > 8). Each warp takes
+// its own groups of R = 32 / P rows (P = the padded width of d + 1) over all
+// TW columns: per row it accumulates the column partials t_ij (x_i, 1) in
+// registers and the row partials sum_j t_ij (y_j, 1), which a warp
+// reduce-scatter (31 shuffles for 32 values) completes for the tile, so row
+// partials go straight to a workspace with no block barrier in the loop.
+// The 8 warps' column partials are summed in a fixed order at the end. Two
+// small kernels reduce the per-band and per-tile partials in FP64 in a fixed
+// order, so the result does not depend on scheduling.
 #include <algorithm>
 
 #include "common.cuh"
@@ -31,13 +33,6 @@ namespace {
 
 constexpr int kAdjThreads = 256;
 constexpr int kAdjWarps = kAdjThreads / kWarp;
-
-// rows staged per chunk: the per-warp row-partial buffer stays <= 32 KiB
-template <typename Real, int P>
-constexpr int adj_chunk() {
-    return (32768 / (kAdjWarps * P * (int)sizeof(Real))) < 64 ? (32768 / (kAdjWarps * P * (int)sizeof(Real)))
-                                                              : 64;
-}
 
 // Index of the last instance whose `key` prefix is <= x (instances sorted by key).
 template <typename F>
@@ -69,12 +64,27 @@ __device__ inline Real reduce_scatter32(Real (&v)[32], int lane) {
     return v[0];
 }
 
+// Columns per thread: 16 bytes of T per row while the per-column registers
+// (2 CPT P) stay small, else one.
+template <typename Real, int P>
+constexpr int adj_cpt() { return P <= 8 ? 16 / (int)sizeof(Real) : 1; }
+
+template <typename Real>
+struct Vec16;
+template <>
+struct Vec16<float> { using T = float4; };
+template <>
+struct Vec16<double> { using T = double2; };
+
 template <typename Real, int P>
 __global__ void __launch_bounds__(kAdjThreads) k_adj_tiles(AdjArgs<Real> A) {
     constexpr int R = 32 / P;
-    constexpr int CH = adj_chunk<Real, P>();
-    __shared__ __align__(16) Real xs[CH][P];
-    __shared__ __align__(16) Real rsm[CH][kAdjWarps][P];
+    constexpr int CPT = adj_cpt<Real, P>();
+    constexpr int TW = kWarp * CPT;                   // columns of a tile (one per lane x CPT)
+    constexpr bool V16 = CPT * sizeof(Real) == 16;
+    constexpr int QC = (32768 / (kAdjWarps * TW * (int)sizeof(Real))) < P
+                           ? (32768 / (kAdjWarps * TW * (int)sizeof(Real))) : P;  // components per pass
+    __shared__ __align__(16) Real csm[kAdjWarps][QC][TW];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int k = find_inst(A.ninst, (long long)blockIdx.x, [&](int q) { return (long long)A.inst[q].tile0; });
@@ -82,62 +92,98 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_tiles(AdjArgs<Real> A) {
     const int t = (int)blockIdx.x - I.tile0;
     const int band = t / I.ncol, ct = t - band * I.ncol;
     const int i0 = band * I.rh, i1 = min(I.m, i0 + I.rh);
-    const int j = ct * kAdjThreads + tid;
-    const bool jv = j < I.n;
+    const int j0 = ct * TW + lane * CPT;  // this lane's first column
     const int d = A.d;
     const Real *Tm = A.T + I.oT;
     Real *dCm = A.dC ? A.dC + I.oT : nullptr;
+    // 16-byte row accesses when every row starts on a 16-byte boundary
+    const bool vec = V16 && (I.n % CPT == 0) && ((reinterpret_cast<uintptr_t>(Tm) & 15) == 0) &&
+                     (!dCm || (reinterpret_cast<uintptr_t>(dCm) & 15) == 0);
+    const Real *Xm = A.X ? A.X + I.oX : nullptr;
 
-    Real y[P], cacc[P];
+    Real y[CPT][P], cacc[CPT][P];
 #pragma unroll
-    for (int c = 0; c < P; ++c) {
-        y[c] = (c < d && jv && A.Y) ? A.Y[I.oY + (size_t)j * d + c] : (c == d ? Real(1) : Real(0));
-        cacc[c] = Real(0);
-    }
-    const bool want_x = A.X != nullptr;
-
-    for (int c0 = i0; c0 < i1; c0 += CH) {
-        const int rows = min(CH, i1 - c0);
-        __syncthreads();  // the previous chunk's buffers are consumed
-        for (int e = tid; e < CH * P; e += kAdjThreads) {
-            const int r = e / P, c = e - r * P;
-            Real v = Real(0);
-            if (r < rows) v = c < d ? (want_x ? A.X[I.oX + (size_t)(c0 + r) * d + c] : Real(0))
-                                    : (c == d ? Real(1) : Real(0));
-            xs[r][c] = v;
+    for (int c = 0; c < CPT; ++c) {
+        const int j = j0 + c;
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            y[c][q] = (q < d && j < I.n && A.Y) ? A.Y[I.oY + (size_t)j * d + q] : (q == d ? Real(1) : Real(0));
+            cacc[c][q] = Real(0);
         }
-        __syncthreads();
-        for (int g = 0; g < rows; g += R) {
-            Real tv[R];
+    }
+
+    // Each warp takes groups of R rows (warp w: groups w, w + 8, ...) over all
+    // TW columns of the tile, so a row's partial over the tile is complete
+    // after the warp's reduce-scatter: no block barrier in this loop.
+    for (int r0 = i0 + warp * R; r0 < i1; r0 += kAdjWarps * R) {
+        // all R rows are loaded before anything is stored (dC may not be
+        // proven distinct from T), so the loads are in flight together
+        Real tv[R][CPT];
 #pragma unroll
-            for (int r = 0; r < R; ++r)
-                tv[r] = (jv && g + r < rows) ? Tm[(size_t)(c0 + g + r) * I.n + j] : Real(0);
-            Real v[32];
+        for (int r = 0; r < R; ++r) {
+            const bool rv = r0 + r < i1;
+            const size_t off = (size_t)(r0 + r) * I.n + j0;
+            if (V16 && vec) {
+                typename Vec16<Real>::T w;
+                if (rv && j0 < I.n) w = __ldg(reinterpret_cast<const typename Vec16<Real>::T *>(Tm + off));
+                else w = typename Vec16<Real>::T{};
+                const Real *pw = reinterpret_cast<const Real *>(&w);
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) tv[r][c] = pw[c];
+            } else {
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) tv[r][c] = (rv && j0 + c < I.n) ? __ldg(Tm + off + c) : Real(0);
+            }
+        }
+        if (dCm) {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                if (dCm && jv && g + r < rows) dCm[(size_t)(c0 + g + r) * I.n + j] = tv[r];
+                if (r0 + r >= i1) break;
+                const size_t off = (size_t)(r0 + r) * I.n + j0;
 #pragma unroll
-                for (int c = 0; c < P; ++c) {
-                    cacc[c] += tv[r] * xs[g + r][c];
-                    v[r * P + c] = tv[r] * y[c];
-                }
+                for (int c = 0; c < CPT; ++c)
+                    if (j0 + c < I.n) dCm[off + c] = tv[r][c];
             }
-            const Real s = reduce_scatter32(v, lane);
-            const int r = lane / P, c = lane - (lane / P) * P;
-            if (g + r < rows) rsm[g + r][warp][c] = s;
         }
-        __syncthreads();
-        for (int e = tid; e < rows * P; e += kAdjThreads) {
-            const int r = e / P, c = e - r * P;
-            Real s = Real(0);
+        Real v[32];
 #pragma unroll
-            for (int w = 0; w < kAdjWarps; ++w) s += rsm[r][w][c];
-            A.rowpart[I.orp + ((size_t)ct * I.m + (c0 + r)) * P + c] = s;
+        for (int r = 0; r < R; ++r) {
+            const bool rv = r0 + r < i1;
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                const Real xq = q < d ? ((Xm && rv) ? Xm[(size_t)(r0 + r) * d + q] : Real(0))
+                                      : (q == d ? Real(1) : Real(0));
+                Real acc = Real(0);
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) {
+                    cacc[c][q] += tv[r][c] * xq;
+                    acc += tv[r][c] * y[c][q];
+                }
+                v[r * P + q] = acc;
+            }
         }
+        const Real sres = reduce_scatter32(v, lane);
+        const int r = lane / P, q = lane - (lane / P) * P;
+        if (r0 + r < i1) A.rowpart[I.orp + ((size_t)ct * I.m + (r0 + r)) * P + q] = sres;
     }
-    if (jv) {
+
+    // column partials: sum over the 8 warps in a fixed order, QC components at a time
 #pragma unroll
-        for (int c = 0; c < P; ++c) A.colpart[I.ocp + ((size_t)band * I.n + j) * P + c] = cacc[c];
+    for (int q0 = 0; q0 < P; q0 += QC) {
+        __syncthreads();
+#pragma unroll
+        for (int qq = 0; qq < QC; ++qq)
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) csm[warp][qq][lane * CPT + c] = cacc[c][q0 + qq];
+        __syncthreads();
+        for (int e = tid; e < QC * TW; e += kAdjThreads) {
+            const int qq = e / TW, col = e - qq * TW;
+            const int j = ct * TW + col;
+            Real sum = Real(0);
+#pragma unroll
+            for (int w = 0; w < kAdjWarps; ++w) sum += csm[w][qq][col];
+            if (j < I.n) A.colpart[I.ocp + ((size_t)band * I.n + j) * P + q0 + qq] = sum;
+        }
     }
 }
 
@@ -225,10 +271,13 @@ int adj_width(int d) {
     return p;
 }
 
-AdjTotals adj_plan(int ninst, const int *m, const int *n, int d, AdjInst *out) {
+int adj_cols_per_thread(int d, int elem_bytes) { return adj_width(d) <= 8 ? 16 / elem_bytes : 1; }
+
+AdjTotals adj_plan(int ninst, const int *m, const int *n, int d, int elem_bytes, AdjInst *out) {
     const int P = adj_width(d);
+    const int TW = kWarp * adj_cols_per_thread(d, elem_bytes);  // columns per tile
     long long ncol_total = 0;
-    for (int k = 0; k < ninst; ++k) ncol_total += (n[k] + kAdjThreads - 1) / kAdjThreads;
+    for (int k = 0; k < ninst; ++k) ncol_total += (n[k] + TW - 1) / TW;
     // enough tiles to fill the GPU (152 SMs x 8 CTAs), rows per band a multiple of 64
     const long long target = 152 * 8;
     const long long f = std::max<long long>(1, (target + ncol_total - 1) / std::max<long long>(ncol_total, 1));
@@ -237,7 +286,7 @@ AdjTotals adj_plan(int ninst, const int *m, const int *n, int d, AdjInst *out) {
         AdjInst &I = out[k];
         I.m = m[k];
         I.n = n[k];
-        I.ncol = (n[k] + kAdjThreads - 1) / kAdjThreads;
+        I.ncol = (n[k] + TW - 1) / TW;
         const long long maxb = (m[k] + 63) / 64;
         const int nb0 = (int)std::min<long long>(f, maxb);
         int rh = (m[k] + nb0 - 1) / nb0;

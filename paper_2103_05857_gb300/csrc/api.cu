@@ -668,7 +668,7 @@ sr_ot_status grad_impl(sr_ot_handle h, const sr_ot_options *o, int ninst, const 
         if (oX[k] < 0 || oY[k] < 0 || ob[k] < 0 || oT[k] < 0) return fail(h, SR_OT_EINVAL, "instance %d: negative offset", k);
     }
     std::vector<AdjInst> inst(ninst);
-    const AdjTotals tot = adj_plan(ninst, m, n, d, inst.data());
+    const AdjTotals tot = adj_plan(ninst, m, n, d, (int)sizeof(Real), inst.data());
     if (tot.tiles > 0x7FFFFFFFLL) return fail(h, SR_OT_EUNSUPPORTED, "adjoint launch too large (%lld tiles)", tot.tiles);
     for (int k = 0; k < ninst; ++k) {
         inst[k].oX = oX[k];

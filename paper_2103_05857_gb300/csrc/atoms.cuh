@@ -170,18 +170,15 @@ __device__ inline bool apply_pairwise(const Step<float> &S, const LaneAtoms &A, 
     } else {
         const int last = cnt - 1;
         if (last != vpos) {
-            // move the last atom into v's place; it is j* when j* was just appended
-            int4 e;
+            // move the last atom into v's place: j* (lane 0) when j* was just
+            // appended, else the lane that holds the last atom writes it
             if (last == jp) {
-                e = make_int4(S.js, __float_as_int(tj_new.hi), __float_as_int(tj_new.lo), 0);
-            } else {
-                const int src = last & 31, sl = last >> 5;
-                const int jj = __shfl_sync(FULL, sl ? A.j[1] : A.j[0], src);
-                const float hh = __shfl_sync(FULL, sl ? A.t[1].hi : A.t[0].hi, src);
-                const float ll = __shfl_sync(FULL, sl ? A.t[1].lo : A.t[0].lo, src);
-                e = make_int4(jj, __float_as_int(hh), __float_as_int(ll), 0);
+                if (lane == 0) rec[vpos] = make_int4(S.js, __float_as_int(tj_new.hi), __float_as_int(tj_new.lo), 0);
+            } else if (lane == (last & 31)) {
+                const int sl = last >> 5;
+                rec[vpos] = make_int4(sl ? A.j[1] : A.j[0], __float_as_int(sl ? A.t[1].hi : A.t[0].hi),
+                                      __float_as_int(sl ? A.t[1].lo : A.t[0].lo), 0);
             }
-            if (lane == 1) rec[vpos] = e;
         }
         cnt = last;
     }

@@ -166,7 +166,7 @@ void set_handleless_error(const char *msg);
 struct AdjInst {
     int m, n;
     long long oX, oY, ob, oT;
-    int nbands, rh, ncol;  // row bands of rh rows; column tiles of 256
+    int nbands, rh, ncol;  // row bands of rh rows; column tiles of 256 x (16 / element size)
     int tile0;             // first tile (CTA) of this instance
     long long col0, row0;  // prefix sums of n and m over the instances
     long long ocp, orp;    // offsets of the column / row partials
@@ -190,9 +190,9 @@ struct AdjArgs {
 
 // Padded width of the per-entry partial vector (x or y, then 1): 4, 8, 16 or 32.
 int adj_width(int d);
-// Tiles and workspace of a set of instances; fills out[k] except the offsets
-// oX, oY, ob, oT.
-AdjTotals adj_plan(int ninst, const int *m, const int *n, int d, AdjInst *out);
+// Tiles and workspace of a set of instances (elem_bytes: 4 or 8); fills
+// out[k] except the offsets oX, oY, ob, oT.
+AdjTotals adj_plan(int ninst, const int *m, const int *n, int d, int elem_bytes, AdjInst *out);
 // Launch the tile pass and the two reductions; false if d is out of range.
 template <typename Real>
 bool launch_adjoint(const AdjArgs<Real> &A, cudaStream_t st);

@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_pipe(EpochArgs<float> 
         auto grad = [&](int j) -> float { return grad_at(j, 0, xc0, xc1, xc2); };
         st = atom_stats(at, grad, ac, false, &t_vdf);
         if (ac > 0.f) {
-            gmx = st.t_v / ac;
+            gmx = st.t_v * (1.f / ac);  // same rounding as the two-phase kernel
             inv = 1.f / (2.f * rho * ac);
         }
         named_sync(1, NT);
@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_pipe(EpochArgs<float> 
                 st = atom_stats(at, grad, an, false, &t_vdf);
                 gmx = inv = 0.f;
                 if (an > 0.f) {
-                    gmx = st.t_v / an;
+                    gmx = st.t_v * (1.f / an);
                     inv = 1.f / (2.f * rho * an);
                 }
                 // ---- merge the compute warps' partial argmin ---------------

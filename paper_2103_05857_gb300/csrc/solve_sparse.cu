@@ -59,6 +59,9 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_sparse(EpochArgs<float
     int4 *aring = reinterpret_cast<int4 *>(cring + (PTS ? 0 : RING * WID));
     SpRed(*red)[NWC] = reinterpret_cast<SpRed(*)[NWC]>(aring + RING * kAtomRecord);
     int *sflag = reinterpret_cast<int *>(red + 2);
+    // per ring slot, the row of that update and what the control warp needs of
+    // it, written one update ahead by compute warp 1 (off the control chain)
+    float4 *rinf = reinterpret_cast<float4 *>(sflag + 4);  // [2 * RING]
 
     const int m = A.in.m, n = A.in.n;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -114,11 +117,14 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_sparse(EpochArgs<float
         return scale_u64(sm64_draw(A.seed, 2, (uint64_t)(A.k0 + p)), m);
     };
     // control warp: atom record; compute threads: their quads of the cost row
+    // compute warp 0 streams the atom records (off the control warp's chain);
+    // it waits for them before the barrier that precedes their use
     auto fetch_async = [&](int i, int s) {
-        if (ctrl) {
+        if (warp == 0) {
             cp16(aring + (size_t)s * kAtomRecord + lane, grec + (size_t)i * kAtomRecord + lane);
             cp16(aring + (size_t)s * kAtomRecord + 32 + lane, grec + (size_t)i * kAtomRecord + 32 + lane);
-        } else if (!PTS) {
+        }
+        if (!ctrl && !PTS) {
             float *dst = cring + (size_t)s * WID;
             const float *src = A.in.C + (size_t)i * n;
 #pragma unroll
@@ -182,6 +188,18 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_sparse(EpochArgs<float
         }
         ai = A.in.a[i];
     };
+    // pairwise steps: 1 / a_i and 1 / (2 rho a_i), taken two updates ahead
+    auto recips = [&](float ai, float &ra, float &ia) {
+        ra = ai > 0.f ? 1.f / ai : 0.f;
+        ia = ai > 0.f ? 1.f / (2.f * rho * ai) : 0.f;
+    };
+    // compute warp 1, lane 0: row info of the update in ring slot s
+    auto put_info = [&](int s, int i, bool pre, float x0, float x1, float x2, float ai) {
+        float ra = 0.f, ia = 0.f;
+        if (PAIR) recips(ai, ra, ia);
+        rinf[2 * s] = make_float4(__int_as_float(i), __int_as_float(pre ? 1 : 0), x0, x1);
+        rinf[2 * s + 1] = make_float4(x2, ai, ra, ia);
+    };
 
     const bool prefetchable = (order == SR_OT_CYCLIC || order == SR_OT_PERMUTE || order == SR_OT_UNIFORM);
     // Pipelines: rq[t] = row of update p+t (t <= D+1), aq[t] = it travels by
@@ -202,29 +220,43 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_sparse(EpochArgs<float
     float xc0 = 0.f, xc1 = 0.f, xc2 = 0.f, ac = 0.f, xn0 = 0.f, xn1 = 0.f, xn2 = 0.f, an = 0.f;
     load_x(rq[0], xc0, xc1, xc2, ac);
     load_x(rq[1], xn0, xn1, xn2, an);
+    if (warp == 1 && lane == 0) put_info(0, rq[0], aq[0], xc0, xc1, xc2, ac);
     if (!ctrl) {
         if (!PTS) {
             if (aq[0]) wait_groups<D - 1>();
             else fetch_sync_costs(rq[0], 0);
+        } else if (warp == 0 && aq[0]) {
+            wait_groups<D - 1>();  // the record of row 0
         }
         load_costs(rq[0], 0, xc0, xc1, xc2);
     }
+    __syncthreads();  // records streamed by warp 0 visible to the control warp
     int i_prev = -1, par = 0;
+    int stop_l = 0;  // control warp: stop after this update
     for (int p = 0; p < m; ++p) {
         const long long k = A.k0 + p;
-        const int i = rq[0];
         const int s_cur = p % RING;
-        {
+        int i, r_far = -1;
+        float xm0 = 0.f, xm1 = 0.f, xm2 = 0.f, am = 0.f;  // row of update p+2
+        float rc = 0.f, ic = 0.f;
+        bool pre = false;
+        if (ctrl) {
+            // the row of this update and its data, from the row-info ring
+            const float4 r0 = rinf[2 * s_cur], r1 = rinf[2 * s_cur + 1];
+            i = __float_as_int(r0.x);
+            pre = __float_as_int(r0.y) != 0;
+            xc0 = r0.z; xc1 = r0.w; xc2 = r1.x; ac = r1.y; rc = r1.z; ic = r1.w;
+        } else {
+            i = rq[0];
             bool ok = prefetchable && rq[D] >= 0 && rq[D] != i_prev;
 #pragma unroll
             for (int u = 0; u < D; ++u) ok = ok && rq[D] != rq[u];
             aq[D] = ok;
             if (ok) fetch_async(rq[D], (p + D) % RING);
-            commit();
+            r_far = row_of(p + D + 2);
+            load_x(rq[2 <= D + 1 ? 2 : D + 1], xm0, xm1, xm2, am);
         }
-        const int r_far = row_of(p + D + 2);
-        float xm0 = 0.f, xm1 = 0.f, xm2 = 0.f, am = 0.f;  // row of update p+2
-        load_x(rq[2 <= D + 1 ? 2 : D + 1], xm0, xm1, xm2, am);
+        commit();
 
         // ---- phase 1: LMO argmin (compute warps) | away vertex (control) ---
         LaneAtoms at;
@@ -261,9 +293,10 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_sparse(EpochArgs<float
             const int wj = __reduce_min_sync(FULL, km == wk ? jmin : 0x7FFFFFFF);
             if (lane == 0) red[par][warp] = SpRed{wk, wj};
         } else {
-            if (aq[0]) wait_groups<D>();
-            else fetch_sync_record(i, s_cur);
-            __syncwarp();
+            if (!pre) {
+                fetch_sync_record(i, s_cur);
+                __syncwarp();
+            }
             at = load_atoms(aring + (size_t)s_cur * kAtomRecord, lane);
             auto grad = [&](int j) -> float {
                 float c;
@@ -279,8 +312,8 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_sparse(EpochArgs<float
             st = atom_stats(at, grad, ac, !PAIR, &t_vdf);
             // quantities of the pairwise step that do not depend on the LMO vertex
             if (PAIR && ac > 0.f) {
-                gmx = st.t_v / ac;                 // gamma_max = alpha_v
-                inv = 1.f / (2.f * rho * ac);      // eq. 10 with d = a_i (e_j* - e_v)
+                gmx = st.t_v * rc;  // gamma_max = alpha_v = t_v / a_i
+                inv = ic;           // eq. 10 with d = a_i (e_j* - e_v)
             }
         }
         __syncthreads();  // (A)
@@ -296,11 +329,9 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_sparse(EpochArgs<float
             const float t_js = atom_weight(at, js, &present, &jpos);
             bool stop = false;
             if (!isfinite(gmin_all)) {
-                if (lane == 0) {
-                    atomicCAS(A.status, 0, (int)kDevNonFinite);
-                    sflag[0] = 1;
-                }
+                if (lane == 0) atomicCAS(A.status, 0, (int)kDevNonFinite);
                 stop = true;
+                stop_l = 1;
             }
             Step<float> S{-1, 0.f, js, st.v, 1.f, 0.f, 0.f, false};
             if (!stop)
@@ -312,10 +343,8 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_sparse(EpochArgs<float
                               : apply_atoms(S, at, present, t_vdf, ac, rho, A.T + (size_t)i * n, qh, ql,
                                             grec + (size_t)i * kAtomRecord, lane));
             if (!applied) {
-                if (lane == 0) {
-                    sflag[0] = 2;  // j* would be a 64th atom: the dense kernel takes over here
-                    if (A.resume) *A.resume = p;
-                }
+                stop_l = 1;  // j* would be a 64th atom: the dense kernel takes over here
+                if (lane == 0 && A.resume) *A.resume = p;
             }
             if (lane == 0 && A.trace && k < A.trace_cap) {
                 A.trace[4 * k] = i;
@@ -327,20 +356,25 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_sparse(EpochArgs<float
             if (!PTS) {
                 if (aq[1]) wait_groups<D - 1>();
                 else fetch_sync_costs(rq[1], (p + 1) % RING);
+            } else if (warp == 0 && aq[1]) {
+                wait_groups<D - 1>();  // the record of the next row
             }
             load_costs(rq[1], (p + 1) % RING, xn0, xn1, xn2);
+            if (warp == 1 && lane == 0) put_info((p + 1) % RING, rq[1], aq[1], xn0, xn1, xn2, an);
         }
         par ^= 1;
-        __syncthreads();  // (B) residual, records and next costs ready
-        if (sflag[0]) break;
-        i_prev = i;
+        // (B) residual, records and next costs ready; stop if the control warp says so
+        if (__syncthreads_or(stop_l)) break;
+        if (!ctrl) {
+            i_prev = i;
 #pragma unroll
-        for (int t = 0; t < D + 1; ++t) rq[t] = rq[t + 1];
-        rq[D + 1] = r_far;
+            for (int t = 0; t < D + 1; ++t) rq[t] = rq[t + 1];
+            rq[D + 1] = r_far;
 #pragma unroll
-        for (int t = 0; t < D; ++t) aq[t] = aq[t + 1];
-        xc0 = xn0; xc1 = xn1; xc2 = xn2; ac = an;
-        xn0 = xm0; xn1 = xm1; xn2 = xm2; an = am;
+            for (int t = 0; t < D; ++t) aq[t] = aq[t + 1];
+            xc0 = xn0; xc1 = xn1; xc2 = xn2; ac = an;
+            xn0 = xm0; xn1 = xm1; xn2 = xm2; an = am;
+        }
     }
     wait_groups<0>();
     __syncthreads();
@@ -355,6 +389,7 @@ static size_t sparse_smem(int ring) {
     else b += (size_t)ring * WID * 4;           // cost-row ring
     b += (size_t)ring * kAtomRecord * 16;       // atom-record ring (1 KiB per slot)
     b += 2 * (NT / kWarp) * sizeof(SpRed) + 16; // reduction slots, flag
+    b += (size_t)ring * 32;                     // row-info ring
     return b;
 }
 
