@@ -96,10 +96,11 @@ typedef struct {
     long long trace_capacity;
     int dense_only;           /* 1: FP32 away/pairwise solves keep the dense row
                                  kernel instead of the active-set kernel          */
-    int pipeline;             /* 1: FP32 pairwise solves use the pipelined
-                                 active-set kernel (the next row's LMO overlaps
-                                 the current update); same decisions as the
-                                 default two-phase kernel                          */
+    int two_phase;            /* 1: FP32 pairwise solves use the two-phase
+                                 active-set kernel instead of the default
+                                 pipelined one (the next row's LMO and away
+                                 vertex overlap the current update); both make
+                                 the same decisions                                */
 } sr_ot_options;
 
 typedef struct {

@@ -528,7 +528,7 @@ sr_ot_status solve_impl(sr_ot_handle h, const sr_ot_options *o, int m, int n, in
                 if (use_sparse) {
                     EpochArgs<float> As = A;
                     As.resume = dstat_d + 1;
-                    if (!o->pipeline || !launch_epoch_pipe(As, h->stream)) launch_epoch_sparse(As, h->stream);
+                    if (o->two_phase || !launch_epoch_pipe(As, h->stream)) launch_epoch_sparse(As, h->stream);
                     EpochArgs<float> Ad = A;
                     Ad.resume_in = dstat_d + 1;  // finishes the epoch only after an overflow
                     launch_epoch<float>(Ad, h->stream);

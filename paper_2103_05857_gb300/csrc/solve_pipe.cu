@@ -1,33 +1,32 @@
 // solve_pipe.cu -- one epoch of BCPFW (pairwise steps, Alg. A.3, exact line
-// search eq. 10) on a single instance with the LMO of the next block taken
-// while the current block is being updated.
+// search eq. 10) on a single instance, with the work of consecutive block
+// updates overlapped.
 //
 // A pairwise step of row i changes the plan, and so the residual r, in two
-// columns only: the LMO vertex j* and the away vertex v. So the argmin of
-// row i' = the row of the next update can be split exactly:
-//   min over j not in {j*, v} of C_i'j + q_j   (q before the update: those
-//                                               columns are unchanged by it)
-//   and the two values at j*, v with the updated q.
-// The compute warps take the first part for row p+1 while the control warp
-// applies update p; the control warp then evaluates the two fresh values and
-// merges them with the compute warps' partial minimum under the same order
-// (value, then column), so the result is exactly the argmin over all
-// columns at the updated residual, as in the non-pipelined kernel.
+// columns only: the LMO vertex j* and the away vertex v. Everything the next
+// update needs can therefore be prepared while the current one is applied,
+// over the columns it leaves unchanged, and completed afterwards at the two
+// changed columns:
+//   LMO of row p+1:    min over j not in {j*_p, v_p} of C_ij + q_j (taken by
+//                      the compute warps), then the two values at j*_p, v_p
+//                      with the updated q;
+//   away vertex of p+1: max over its atoms not in {j*_p, v_p}; if an atom is
+//                      one of those two columns, recomputed in full after the
+//                      update.
+// Both merges use the order of the plain kernel (value, then column), so the
+// decisions are exactly those of the two-phase kernel (solve_sparse.cu).
 //
-// Per phase p (one full barrier each):
-//   compute warps: argmin of row p+1 over columns not in {j*_p, v_p} ->
-//                  partials -> named barrier (arrive) -> cost row of p+2;
-//   control warp:  decide and apply update p (atoms, plan, residual) ->
-//                  away statistics of row p+1 at the new residual ->
-//                  named barrier (wait) -> merge -> j*_{p+1}, exclusion set
-//                  {j*_{p+1}, v_{p+1}} for the next phase.
-// Compute warps read the residual while the control warp writes it, but only
-// in the excluded columns, whose values they ignore.
+// Two control warps alternate: in phase p the owner warp (p even: first,
+// p odd: second) decides and applies update p with the atoms of row p it
+// already holds, while the other warp loads the atoms of row p+1 and takes
+// their statistics; after one named barrier (compute warps and owner arrive)
+// it completes the LMO and the away vertex, publishes {j*_{p+1}, v_{p+1}} and
+// becomes the owner of update p+1. One full barrier per update.
 //
-// Layout, atom records (up to 63 per row, double-float weights), the
-// compensated residual pair in shared memory, the record / cost-row ring
-// (cp.async, D = RING - 2 rows ahead) and the overflow hand-off to the dense
-// kernel are those of the active-set kernel (solve_sparse.cu).
+// Layout (atom records, compensated residual pair, record / cost-row ring,
+// row-info ring written by compute warp 1, overflow hand-off) as in
+// solve_sparse.cu. A row whose record is being rewritten (it repeats the
+// previous row, uniform order) is read from global memory after the apply.
 #include <algorithm>
 #include <limits>
 
@@ -53,9 +52,9 @@ __device__ inline void named_sync(int id, int count) {
 }  // namespace
 
 template <int NTC, int G, bool PTS, int RING>
-__global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_pipe(EpochArgs<float> A) {
-    constexpr int NWC = NTC / kWarp;  // compute warps; warp NWC is the control warp
-    constexpr int NT = NTC + kWarp;
+__global__ void __launch_bounds__(NTC + 2 * kWarp, 1) k_epoch_pipe(EpochArgs<float> A) {
+    constexpr int NWC = NTC / kWarp;  // compute warps; warps NWC, NWC+1 are the control warps
+    constexpr int NT = NTC + 2 * kWarp;
     constexpr int CPT = 4 * G;
     constexpr int WID = NTC * CPT;
     constexpr int D = RING - 2;
@@ -67,11 +66,13 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_pipe(EpochArgs<float> 
     float *cring = reinterpret_cast<float *>(ys + (PTS ? WID : 0));
     int4 *aring = reinterpret_cast<int4 *>(cring + (PTS ? 0 : RING * WID));
     SpRed *red = reinterpret_cast<SpRed *>(aring + RING * kAtomRecord);
-    int *sflag = reinterpret_cast<int *>(red + NWC);  // [0] stop, [2..3] exclusion set
+    int *sflag = reinterpret_cast<int *>(red + NWC);      // [2..3]: exclusion set
+    float4 *rinf = reinterpret_cast<float4 *>(sflag + 4);  // [2 * RING] row info
 
     const int m = A.in.m, n = A.in.n;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool ctrl = warp == NWC;
+    const int cw = warp - NWC;  // 0 / 1 for the control warps
+    const bool ctrl = cw >= 0;
     const unsigned FULL = 0xffffffffu;
     const float rho = (float)A.rho;
     const int order = A.order;
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_pipe(EpochArgs<float> 
     int4 *grec = A.atoms;
     const float INF = std::numeric_limits<float>::infinity();
 
-    // ---- one-time set-up (as in the active-set kernel) --------------------
+    // ---- one-time set-up ------------------------------------------------
     for (int j = tid; j < WID; j += NT) {
         if (j < n) {
             const double qq = A.q[j];
@@ -98,7 +99,6 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_pipe(EpochArgs<float> 
             for (int s = 0; s < RING; ++s) cring[(size_t)s * WID + j] = 0.f;
     }
     if (tid == 0) {
-        sflag[0] = 0;
         sflag[2] = -1;
         sflag[3] = -1;
         if (A.resume) *A.resume = -1;
@@ -124,11 +124,13 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_pipe(EpochArgs<float> 
         if (order == SR_OT_PERMUTE) return A.perm[p];
         return scale_u64(sm64_draw(A.seed, 2, (uint64_t)(A.k0 + p)), m);
     };
+    // compute warp 0 streams atom records; all compute threads their cost quads
     auto fetch_async = [&](int i, int s) {
-        if (ctrl) {
+        if (warp == 0) {
             cp16(aring + (size_t)s * kAtomRecord + lane, grec + (size_t)i * kAtomRecord + lane);
             cp16(aring + (size_t)s * kAtomRecord + 32 + lane, grec + (size_t)i * kAtomRecord + 32 + lane);
-        } else if (!PTS) {
+        }
+        if (!ctrl && !PTS) {
             float *dst = cring + (size_t)s * WID;
             const float *src = A.in.C + (size_t)i * n;
 #pragma unroll
@@ -190,6 +192,13 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_pipe(EpochArgs<float> 
         }
         ai = A.in.a[i];
     };
+    // compute warp 1, lane 0: the row of the update in slot s and its data
+    auto put_info = [&](int s, int i, bool pre, float x0, float x1, float x2, float ai) {
+        const float ra = ai > 0.f ? 1.f / ai : 0.f;
+        const float ia = ai > 0.f ? 1.f / (2.f * rho * ai) : 0.f;
+        rinf[2 * s] = make_float4(__int_as_float(i), __int_as_float(pre ? 1 : 0), x0, x1);
+        rinf[2 * s + 1] = make_float4(x2, ai, ra, ia);
+    };
     // compute warps: partial argmin of the current cost row over the columns
     // not in {e1, e2}; ties to the smallest column
     auto partial_argmin = [&](int e1, int e2) {
@@ -227,7 +236,7 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_pipe(EpochArgs<float> 
         const int wj = __reduce_min_sync(FULL, km == wk ? qj[0] : 0x7FFFFFFF);
         if (lane == 0) red[warp] = SpRed{wk, wj};
     };
-    // control warp: gradient of row (x, cost slot s) at column j, current residual
+    // control warps: gradient of a row (x, cost slot s) at column j, current residual
     auto grad_at = [&](int j, int s, float x0, float x1, float x2) -> float {
         float c;
         if (PTS) {
@@ -241,15 +250,16 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_pipe(EpochArgs<float> 
     };
 
     const bool prefetchable = (order == SR_OT_CYCLIC || order == SR_OT_PERMUTE || order == SR_OT_UNIFORM);
-    // rq[t] = row of update p+1+t (t <= D); aq[t]: it travels by cp.async.
-    // Row p+1+D is issued at the start of phase p; a row that repeats one of
-    // the rows updated between its fetch and its use is loaded synchronously.
+    // Compute threads: rq[t] = row of update p+1+t (t <= D), aq[t]: it travels
+    // by cp.async. Row p+1+D is issued in phase p into slot (p+1+D) % RING; a
+    // row whose record changes between its fetch and its use is not issued.
     int rq[D + 1];
     bool aq[D + 1];
-    int row_cur = row_of(0);  // row of update p
-    int row_prev = -1;        // row of update p-1 (its record writes precede this phase)
-    // prologue: rows 0 .. D travel (row 0 in slot 0, ...)
-    {
+    int row_cur = row_of(0), row_prev = -1;
+    // compute threads: x, a of the row whose cost row they build next (loaded
+    // one phase before use, so no global-load latency sits in a phase)
+    float xn0 = 0.f, xn1 = 0.f, xn2 = 0.f, an = 0.f;
+    if (!ctrl) {
         int pre[D + 1];
 #pragma unroll
         for (int t = 0; t <= D; ++t) {
@@ -263,170 +273,164 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_pipe(EpochArgs<float> 
         }
         rq[D] = row_of(D + 1);
         aq[D] = false;
-        // row 0 itself: its record and costs
         const bool ok0 = prefetchable && pre[0] >= 0;
-        if (ctrl) {
-            if (ok0) wait_groups<D>();
-            else fetch_sync_record(pre[0], 0);
-        } else if (!PTS) {
-            if (ok0) wait_groups<D>();
-            else fetch_sync_costs(pre[0], 0);
-        }
+        float x0 = 0.f, x1 = 0.f, x2 = 0.f, a0 = 0.f;
+        load_x(pre[0], x0, x1, x2, a0);
+        if (ok0) wait_groups<D>();  // row 0: record (warp 0) and costs
+        else if (!PTS) fetch_sync_costs(pre[0], 0);
+        if (warp == 1 && lane == 0) put_info(0, pre[0], ok0, x0, x1, x2, a0);
+        load_x(rq[0], xn0, xn1, xn2, an);
+        load_costs(0, x0, x1, x2);  // PTS: from x; given C: slot 0 (own quads)
     }
-    // control state of the pending update (row_cur)
-    float xc0 = 0.f, xc1 = 0.f, xc2 = 0.f, ac = 0.f;
-    load_x(row_cur, xc0, xc1, xc2, ac);
+    __syncthreads();  // row 0's record, costs and info visible
+
+    // control-warp state of the update this warp owns next
     LaneAtoms at;
     AtomStats st;
-    DF t_vdf{0.f, 0.f};
-    float gmx = 0.f, inv = 0.f, gmin_cur = 0.f;
-    int js_cur = 0;
-    float xn0 = 0.f, xn1 = 0.f, xn2 = 0.f, an = 0.f;  // row of update p+1
-    load_x(rq[0], xn0, xn1, xn2, an);
+    DF tvd{0.f, 0.f};
+    float gmin = 0.f, gmx = 0.f, inv = 0.f, ai = 0.f;
+    int js = 0, row = 0;
+    int stop_l = 0;
+
+    // the statistics warp for row `pr` (slot s): atoms, away vertex over the
+    // atoms not in {e1, e2}, then (after the named barrier) the LMO merge and
+    // the completion at e1, e2; publishes the exclusion set of update pr
+    auto stats_and_merge = [&](int s, int e1, int e2, bool arrive_before) {
+        const float4 r0 = rinf[2 * s], r1 = rinf[2 * s + 1];
+        const int i1 = __float_as_int(r0.x);
+        const bool pre1 = __float_as_int(r0.y) != 0;
+        const float x0 = r0.z, x1 = r0.w, x2 = r1.x, a1 = r1.y, ra = r1.z, ia = r1.w;
+        bool full_after = !pre1;  // record read (and statistics) after the update
+        bool anyE = false;
+        if (pre1) {
+            at = load_atoms(aring + (size_t)s * kAtomRecord, lane);
+            const bool e_in = (at.j[0] >= 0 && (at.j[0] == e1 || at.j[0] == e2)) ||
+                              (at.j[1] >= 0 && (at.j[1] == e1 || at.j[1] == e2));
+            anyE = __any_sync(FULL, e_in);
+            if (!anyE) {
+                auto grad = [&](int j) -> float { return grad_at(j, s, x0, x1, x2); };
+                st = atom_stats(at, grad, a1, false, &tvd);
+            }
+        }
+        if (arrive_before) named_sync(1, NT);
+        if (full_after) {
+            fetch_sync_record(i1, s);
+            __syncwarp();
+            at = load_atoms(aring + (size_t)s * kAtomRecord, lane);
+        }
+        if (full_after || anyE) {
+            auto grad = [&](int j) -> float { return grad_at(j, s, x0, x1, x2); };
+            st = atom_stats(at, grad, a1, false, &tvd);
+        }
+        // LMO: the compute warps' partial minimum and the columns e1, e2
+        const SpRed e = lane < NWC ? red[lane] : SpRed{0xFFFFFFFFu, 0x7FFFFFFF};
+        uint32_t wk = e.kmin;
+        int wj = e.jmin;
+        const int ec = lane == NWC ? e1 : (lane == NWC + 1 ? e2 : -1);
+        if (ec >= 0) {
+            wk = f2key(grad_at(ec, s, x0, x1, x2));
+            wj = ec;
+        }
+        const uint32_t fk = __reduce_min_sync(FULL, wk);
+        js = __reduce_min_sync(FULL, wk == fk ? wj : 0x7FFFFFFF);
+        gmin = key2f(fk);
+        row = i1;
+        ai = a1;
+        gmx = inv = 0.f;
+        if (a1 > 0.f) {
+            gmx = st.t_v * ra;  // same rounding as the two-phase kernel
+            inv = ia;
+        }
+        if (!isfinite(gmin)) {
+            if (lane == 0) atomicCAS(A.status, 0, (int)kDevNonFinite);
+            stop_l = 1;
+        }
+        if (lane == 0) {
+            sflag[2] = js;
+            sflag[3] = (st.v >= 0 && st.v < n) ? st.v : -1;
+        }
+    };
 
     // ---- prologue phase: LMO and away vertex of row 0 ---------------------
-    __syncthreads();  // synchronous loads of row 0 visible
     if (!ctrl) {
-        load_costs(0, xc0, xc1, xc2);
         partial_argmin(-1, -1);
         named_arrive(1, NT);
         if (m > 1) {
-            if (!PTS) {
-                if (aq[0]) wait_groups<D - 1>();
-                else fetch_sync_costs(rq[0], 1 % RING);
-            }
+            if (aq[0]) wait_groups<D - 1>();  // row 1: record and costs
+            else if (!PTS) fetch_sync_costs(rq[0], 1 % RING);
             load_costs(1 % RING, xn0, xn1, xn2);
+            if (warp == 1 && lane == 0) put_info(1 % RING, rq[0], aq[0], xn0, xn1, xn2, an);
+            load_x(row_of(2), xn0, xn1, xn2, an);  // row 2, used in phase 0
         }
+    } else if (cw == 0) {
+        stats_and_merge(0, -1, -1, true);
     } else {
-        at = load_atoms(aring, lane);
-        auto grad = [&](int j) -> float { return grad_at(j, 0, xc0, xc1, xc2); };
-        st = atom_stats(at, grad, ac, false, &t_vdf);
-        if (ac > 0.f) {
-            gmx = st.t_v * (1.f / ac);  // same rounding as the two-phase kernel
-            inv = 1.f / (2.f * rho * ac);
-        }
-        named_sync(1, NT);
-        const SpRed e = lane < NWC ? red[lane] : SpRed{0xFFFFFFFFu, 0x7FFFFFFF};
-        const uint32_t wk = __reduce_min_sync(FULL, e.kmin);
-        js_cur = __reduce_min_sync(FULL, e.kmin == wk ? e.jmin : 0x7FFFFFFF);
-        gmin_cur = key2f(wk);
-        if (lane == 0) {
-            if (!isfinite(gmin_cur)) {
-                atomicCAS(A.status, 0, (int)kDevNonFinite);
-                sflag[0] = 1;
-            }
-            sflag[2] = js_cur;
-            sflag[3] = (st.v >= 0 && st.v < n) ? st.v : -1;
-        }
+        named_arrive(1, NT);
     }
-    __syncthreads();
+    if (__syncthreads_or(stop_l)) {
+        wait_groups<0>();
+        __syncthreads();
+        for (int j = tid; j < n; j += NT) A.q[j] = (double)qh[j] - (double)ql[j];
+        return;
+    }
 
-    for (int p = 0; p < m && !sflag[0]; ++p) {
+    for (int p = 0; p < m; ++p) {
         const long long k = A.k0 + p;
         const bool more = p + 1 < m;
-        const int row_p = row_cur;
-        // issue row p+1+D (not if its record changes before it is used)
-        {
+        const int e1 = sflag[2], e2 = sflag[3];  // columns update p changes
+        if (!ctrl) {
+            // issue row p+1+D (not if its record changes before it is used)
             const int rnew = row_of(p + 1 + D);
             bool ok = prefetchable && rnew >= 0 && rnew != row_cur && rnew != row_prev;
 #pragma unroll
             for (int u = 0; u < D; ++u) ok = ok && rnew != rq[u];
             if (ok) fetch_async(rnew, (p + 1 + D) % RING);
-            commit();
             rq[D] = rnew;
             aq[D] = ok;
         }
-        const int e1 = sflag[2], e2 = sflag[3];  // columns update p changes
+        commit();
         if (!ctrl) {
             if (more) {
-                partial_argmin(e1, e2);
+                partial_argmin(e1, e2);  // row p+1
                 named_arrive(1, NT);
                 if (p + 2 < m) {
-                    float xm0 = 0.f, xm1 = 0.f, xm2 = 0.f, am = 0.f;
-                    load_x(rq[1], xm0, xm1, xm2, am);
-                    if (!PTS) {
-                        if (aq[1]) wait_groups<D - 1>();
-                        else fetch_sync_costs(rq[1], (p + 2) % RING);
-                    }
-                    load_costs((p + 2) % RING, xm0, xm1, xm2);
+                    if (aq[1]) wait_groups<D - 1>();  // row p+2: record and costs
+                    else if (!PTS) fetch_sync_costs(rq[1], (p + 2) % RING);
+                    load_costs((p + 2) % RING, xn0, xn1, xn2);  // x of row p+2, loaded last phase
+                    if (warp == 1 && lane == 0) put_info((p + 2) % RING, rq[1], aq[1], xn0, xn1, xn2, an);
+                    load_x(row_of(p + 3), xn0, xn1, xn2, an);    // for the next phase
                 }
             }
-        } else {
-            // ---- update p -------------------------------------------------
-            const int i = row_cur;
+        } else if (cw == (p & 1)) {
+            // ---- owner: update p ------------------------------------------
             bool present = false;
             int jpos = -1;
-            atom_weight(at, js_cur, &present, &jpos);
-            const Step<float> S = decide_pairwise(st, gmin_cur, js_cur, ac, rho, gmx, inv, n);
-            bool ok = apply_pairwise(S, at, jpos, st.vpos, t_vdf, rho, A.T + (size_t)i * n, qh, ql,
-                                     grec + (size_t)i * kAtomRecord, lane);
+            atom_weight(at, js, &present, &jpos);
+            const Step<float> S = decide_pairwise(st, gmin, js, ai, rho, gmx, inv, n);
+            const bool ok = apply_pairwise(S, at, jpos, st.vpos, tvd, rho, A.T + (size_t)row * n, qh, ql,
+                                           grec + (size_t)row * kAtomRecord, lane);
             if (lane == 0 && A.trace && k < A.trace_cap) {
-                A.trace[4 * k] = i;
-                A.trace[4 * k + 1] = js_cur;
+                A.trace[4 * k] = row;
+                A.trace[4 * k + 1] = js;
                 A.trace[4 * k + 2] = (st.v >= 0 && st.v < n) ? st.v : -1;
                 A.trace[4 * k + 3] = __float_as_int(S.gamma);
             }
-            if (!ok && lane == 0) {
-                sflag[0] = 2;  // j* would be a 64th atom: the dense kernel takes over at p
-                if (A.resume) *A.resume = p;
+            if (!ok) {
+                stop_l = 1;  // j* would be a 64th atom: the dense kernel takes over at p
+                if (lane == 0 && A.resume) *A.resume = p;
             }
-            if (more) {
-                // ---- row p+1: record, away vertex at the new residual ------
-                const int i1 = rq[0];
-                const int s1 = (p + 1) % RING;
-                if (aq[0]) {
-                    wait_groups<D>();
-                } else {
-                    __syncwarp();  // this warp's record writes of update p
-                    fetch_sync_record(i1, s1);
-                }
-                __syncwarp();
-                at = load_atoms(aring + (size_t)s1 * kAtomRecord, lane);
-                auto grad = [&](int j) -> float { return grad_at(j, s1, xn0, xn1, xn2); };
-                st = atom_stats(at, grad, an, false, &t_vdf);
-                gmx = inv = 0.f;
-                if (an > 0.f) {
-                    gmx = st.t_v * (1.f / an);
-                    inv = 1.f / (2.f * rho * an);
-                }
-                // ---- merge the compute warps' partial argmin ---------------
-                named_sync(1, NT);
-                const SpRed e = lane < NWC ? red[lane] : SpRed{0xFFFFFFFFu, 0x7FFFFFFF};
-                uint32_t wk = __reduce_min_sync(FULL, e.kmin);
-                int wj = __reduce_min_sync(FULL, e.kmin == wk ? e.jmin : 0x7FFFFFFF);
-                // the columns update p changed, at the updated residual
-                uint32_t kx = 0xFFFFFFFFu;
-                int jx = 0x7FFFFFFF;
-                const int ec = lane == 0 ? e1 : (lane == 1 ? e2 : -1);
-                if (ec >= 0) {
-                    kx = f2key(grad_at(ec, s1, xn0, xn1, xn2));
-                    jx = ec;
-                }
-                if (kx < wk || (kx == wk && jx < wj)) { wk = kx; wj = jx; }
-                const uint32_t fk = __reduce_min_sync(FULL, wk);
-                js_cur = __reduce_min_sync(FULL, wk == fk ? wj : 0x7FFFFFFF);
-                gmin_cur = key2f(fk);
-                if (lane == 0) {
-                    if (!isfinite(gmin_cur)) {
-                        atomicCAS(A.status, 0, (int)kDevNonFinite);
-                        sflag[0] = 1;
-                    }
-                    sflag[2] = js_cur;
-                    sflag[3] = (st.v >= 0 && st.v < n) ? st.v : -1;
-                }
-                xc0 = xn0; xc1 = xn1; xc2 = xn2; ac = an;
-            }
+            if (more) named_arrive(1, NT);
+        } else if (more) {
+            // ---- statistics warp: row p+1 ---------------------------------
+            stats_and_merge((p + 1) % RING, e1, e2, true);
         }
-        __syncthreads();  // residual, records, partials, exclusion set and costs ready
-        if (sflag[0]) break;
-        // advance the row pipeline (all threads)
-        row_prev = row_p;
-        row_cur = rq[0];
+        if (__syncthreads_or(stop_l)) break;
+        if (!ctrl) {
+            row_prev = row_cur;
+            row_cur = rq[0];
 #pragma unroll
-        for (int t = 0; t < D; ++t) { rq[t] = rq[t + 1]; aq[t] = aq[t + 1]; }
-        float t0 = 0.f, t1 = 0.f, t2 = 0.f, ta = 0.f;
-        load_x(rq[0], t0, t1, t2, ta);
-        xn0 = t0; xn1 = t1; xn2 = t2; an = ta;
+            for (int t = 0; t < D; ++t) { rq[t] = rq[t + 1]; aq[t] = aq[t + 1]; }
+        }
     }
     wait_groups<0>();
     __syncthreads();
@@ -441,6 +445,7 @@ static size_t pipe_smem(int ring) {
     else b += (size_t)ring * WID * 4;
     b += (size_t)ring * kAtomRecord * 16;
     b += (NT / kWarp) * sizeof(SpRed) + 16;
+    b += (size_t)ring * 32;  // row-info ring
     return b;
 }
 
@@ -452,7 +457,7 @@ static void launch_pipe_ring(const EpochArgs<float> &A, cudaStream_t st) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
         attr_set = true;
     }
-    kern<<<1, NT + kWarp, pipe_smem<NT, G, PTS>(RING), st>>>(A);
+    kern<<<1, NT + 2 * kWarp, pipe_smem<NT, G, PTS>(RING), st>>>(A);
 }
 
 template <int NT, int G>

@@ -20,8 +20,11 @@
 // ahead (cp.async) by a control warp, which alone applies the update. The
 // dense plan T is kept exact by storing the changed entries.
 //
-// Per update: argmin pass (all threads) -> barrier -> warp 0: global argmin,
-// away vertex, decision, atom / T / q updates -> barrier.
+// Per update: argmin pass (compute warps) | away vertex (control warp) ->
+// barrier -> control warp: global argmin, decision, atom / T / q updates |
+// compute warps: next cost row -> barrier. (For pairwise steps the
+// pipelined kernel of solve_pipe.cu is the default; this one is kept for
+// away steps and as its reference.)
 //
 // If a row would need more than 63 atoms, the kernel stops before changing
 // it and records the update index in *resume; the dense kernel then finishes

@@ -34,7 +34,7 @@ class Options(ct.Structure):
         ("rho", ct.c_double), ("tol_rel_gap", ct.c_double), ("max_epochs", ct.c_longlong),
         ("gap_every", ct.c_int), ("refresh_every", ct.c_int), ("ga_M", ct.c_int),
         ("ga_global_only", ct.c_int), ("seed", ct.c_ulonglong), ("trace", ct.c_void_p),
-        ("trace_capacity", ct.c_longlong), ("dense_only", ct.c_int), ("pipeline", ct.c_int),
+        ("trace_capacity", ct.c_longlong), ("dense_only", ct.c_int), ("two_phase", ct.c_int),
     ]
 
 

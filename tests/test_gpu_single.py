@@ -521,21 +521,22 @@ def test_fp32_dense_steps_conserve_row_mass(S, h, oracle_mod, variant, order):
                                                ("PERMUTE", 200, 1500, 15, "pts"), ("CYCLIC", 190, 600, 20, "cost"),
                                                ("CYCLIC", 1024, 4096, 3, "pts")])
 def test_pipelined_pairwise_kernel_matches_two_phase(S, h, oracle_mod, order, m, n, ep, mode):
-    """The pipelined BCPFW kernel takes the next row's argmin over the
-    columns the current update leaves unchanged and merges the two changed
-    ones afterwards: every decision (block, LMO vertex, away vertex, step)
-    and the final plan equal the two-phase active-set kernel's bit for bit."""
+    """The pipelined BCPFW kernel (the default) takes the next row's LMO and
+    away vertex over the columns the current update leaves unchanged and
+    completes them at the two changed columns afterwards: every decision
+    (block, LMO vertex, away vertex, step) and the final plan equal the
+    two-phase active-set kernel's bit for bit."""
     inst = W.colour_instance(17 + m, m, n, rho=10.0, b_dirichlet=True).rounded()
     C = dev(oracle_mod.cost(inst.X, inst.Y), torch.float32) if mode == "cost" else None
     out = []
-    for pipe in (1, 0):
+    for two in (0, 1):
         cap = ep * m
         tr = torch.full((4 * cap,), -1, dtype=torch.int32, device="cuda")
         T = torch.zeros((m, n), dtype=torch.float32, device="cuda")
         kw = dict(C=C) if C is not None else dict(X=dev(inst.X, torch.float32), Y=dev(inst.Y, torch.float32))
         res = h.solve(dev(inst.a, torch.float32), dev(inst.b, torch.float32), T, precision=S.FP32,
                       variant=S.BCPFW, step=S.ELS, order=getattr(S, order), seed=11, rho=inst.rho,
-                      max_epochs=ep, trace=tr, trace_capacity=cap, pipeline=pipe, **kw)
+                      max_epochs=ep, trace=tr, trace_capacity=cap, two_phase=two, **kw)
         out.append((tr.cpu().numpy(), T.cpu().numpy(), res))
     np.testing.assert_array_equal(out[0][0], out[1][0])
     np.testing.assert_array_equal(out[0][1], out[1][1])
