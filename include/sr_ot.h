@@ -161,6 +161,9 @@ sr_ot_status sr_ot_solve(sr_ot_handle h, const sr_ot_options *opts, int m, int n
 /*
  * Solve `batch` independent instances in one persistent launch (captured in a
  * CUDA graph and replayed for a repeated shape set). Points mode with d = 3.
+ * Each instance checks its certificate every gap_every epochs, or 2, 4 or 8
+ * times less often while its last relative gap was more than 10, 100 or 1000
+ * times tol_rel_gap (a certificate reads the instance's whole plan).
  * m[k], n[k]: HOST arrays of per-instance sizes. off_X, off_Y, off_a, off_b,
  * off_T: HOST arrays of per-instance ELEMENT offsets into the packed device
  * buffers X, Y, a, b, T. Each instance starts from T0 = (a_i e_0).

@@ -37,6 +37,30 @@ __device__ inline LaneAtoms load_atoms(const int4 *rec, int lane) {
     return A;
 }
 
+// A row's record as raw entries (count, this lane's two atoms): loads that
+// can be issued an update ahead and decoded with decode_atoms when used.
+struct RawAtoms {
+    int4 head, e0, e1;
+};
+__device__ inline RawAtoms fetch_atoms(const int4 *rec, int lane) {
+    RawAtoms R;
+    R.head = rec[0];
+    R.e0 = rec[1 + lane];
+    R.e1 = rec[1 + (lane + 32 < kAtomsMax ? lane + 32 : 0)];
+    return R;
+}
+__device__ inline LaneAtoms decode_atoms(const RawAtoms &R, int lane) {
+    LaneAtoms A;
+    A.cnt = R.head.x;
+    const bool h0 = lane < A.cnt, h1 = lane + 32 < A.cnt;
+    A.j[0] = h0 ? R.e0.x : -1;
+    A.t[0] = h0 ? DF{__int_as_float(R.e0.y), __int_as_float(R.e0.z)} : DF{0.f, 0.f};
+    A.j[1] = h1 ? R.e1.x : -1;
+    A.t[1] = h1 ? DF{__int_as_float(R.e1.y), __int_as_float(R.e1.z)} : DF{0.f, 0.f};
+    A.g[0] = A.g[1] = 0.f;
+    return A;
+}
+
 // Gradient statistics over the atoms (see AtomStats). grad(j) evaluates the
 // row gradient of column j; ai is the row weight.
 template <typename GradF>

@@ -23,6 +23,7 @@
 #include "atoms.cuh"
 #include "batched.h"
 #include "common.cuh"
+#include "cpasync.cuh"
 #include "internal.h"
 #include "step.cuh"
 
@@ -32,6 +33,7 @@ namespace {
 
 constexpr int kSmemMax = 227 * 1024;
 constexpr int kPermMax = 2048;  // PERMUTE order: rows sorted in shared memory
+constexpr int kRowMax = 2048;   // rows whose a_i and reciprocals are staged in shared memory
 
 struct BRed {
     uint32_t kmin;
@@ -58,6 +60,8 @@ size_t batched_smem() {
     b += (size_t)kPermMax * (8 + 4);                 // permutation keys and rows
     b += 2 * ((NTC / kWarp) + 1) * sizeof(BRed);     // reduction slots
     b += 64 * sizeof(double) + 64;                   // certificate partials, flags
+    b += (size_t)kRowMax * 16;                       // per-row a, 1/a, 1/(2 rho a)
+    b += 2 * (size_t)kAtomRecord * 16;               // two-slot atom-record ring
     return b;
 }
 
@@ -77,6 +81,11 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_batched(BatchArgs B) {
     BRed(*red)[NW] = reinterpret_cast<BRed(*)[NW]>(prow + kPermMax);
     double *cacc = reinterpret_cast<double *>(red + 2);  // certificate partials [NW][3]
     int *sflag = reinterpret_cast<int *>(cacc + 64);
+    // per row {a_i, 1 / a_i, 1 / (2 rho a_i)}: the control warp reads them
+    // from shared memory instead of loading and dividing on its chain
+    float4 *arow = reinterpret_cast<float4 *>(sflag + 16);
+    // atom records of the current and next row, streamed by compute warp 0
+    int4 *aring = reinterpret_cast<int4 *>(arow + kRowMax);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool ctrl = warp == NWC;
@@ -106,8 +115,11 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_batched(BatchArgs B) {
             T[e] = j == 0 ? a[i] : 0.f;
         }
         for (int i = tid; i < m; i += NT) {
-            grec[(size_t)i * kAtomRecord] = make_int4(a[i] > 0.f ? 1 : 0, 0, 0, 0);
-            grec[(size_t)i * kAtomRecord + 1] = make_int4(0, __float_as_int(a[i]), 0, 0);
+            const float ai = a[i];
+            grec[(size_t)i * kAtomRecord] = make_int4(ai > 0.f ? 1 : 0, 0, 0, 0);
+            grec[(size_t)i * kAtomRecord + 1] = make_int4(0, __float_as_int(ai), 0, 0);
+            if (i < kRowMax)
+                arow[i] = make_float4(ai, ai > 0.f ? 1.f / ai : 0.f, ai > 0.f ? 1.f / (2.f * rho * ai) : 0.f, 0.f);
         }
         // s_0 = sum_i a_i in ascending order (one thread), r = s - b
         if (tid == 0) {
@@ -117,6 +129,13 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_batched(BatchArgs B) {
             sflag[0] = 0;
         }
         __syncthreads();
+        // fixed-point exponent for the certificate's column sums (see there)
+        int fx_exp;
+        {
+            int e2 = 0;
+            frexp(cacc[0] > 1.0 ? cacc[0] : 1.0, &e2);  // total mass < 2^e2
+            fx_exp = 61 - e2;
+        }
         for (int j = tid; j < WID; j += NT) {
             if (j < n) {
                 const double qq = rho64 * ((j == 0 ? cacc[0] : 0.0) - (double)b[j]);
@@ -147,6 +166,7 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_batched(BatchArgs B) {
 
         double f = 0.0, gap = 0.0, feas_err = 0.0;
         long long ep = 0, updates = 0;
+        long long next_cert = 0;  // epoch count at which the next certificate is due
         int status = kInstOk;
         int par = 0;
         for (ep = 0; ep < B.max_epochs; ++ep) {
@@ -189,14 +209,29 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_batched(BatchArgs B) {
             // ---- m block updates ---------------------------------------------
             float cst[CPT];
             int i_next = row_of(0);
-            // control warp: lane l holds atoms l and 32+l of the current row,
-            // and the next row's atoms are loaded one update ahead
-            LaneAtoms at_cur{}, at_nxt{};
-            if (ctrl) at_cur = load_atoms(grec + (size_t)i_next * kAtomRecord, lane);
+            // atom records: row of update p in ring slot p & 1; compute warp 0
+            // streams the next row's record during update p (not when that
+            // record is being rewritten: the row of update p or p-1)
+            if (warp == 0) {
+                cp16(aring + lane, grec + (size_t)i_next * kAtomRecord + lane);
+                cp16(aring + 32 + lane, grec + (size_t)i_next * kAtomRecord + 32 + lane);
+                commit();
+                wait_groups<0>();
+            }
+            bool pre_cur = true;  // the current row's record is in its slot
+            int i_prev = -1;
             float xn0 = 0.f, xn1 = 0.f, xn2 = 0.f;
             xn0 = X[(size_t)i_next * 3];
             xn1 = X[(size_t)i_next * 3 + 1];
             xn2 = X[(size_t)i_next * 3 + 2];
+            // x of the row two updates ahead, loaded an update before its use
+            int i_far = m > 1 ? row_of(1) : -1;
+            float xf0 = 0.f, xf1 = 0.f, xf2 = 0.f;
+            if (i_far >= 0) {
+                xf0 = X[(size_t)i_far * 3];
+                xf1 = X[(size_t)i_far * 3 + 1];
+                xf2 = X[(size_t)i_far * 3 + 2];
+            }
             if (!ctrl) {
                 const float2 X0 = make_float2(xn0, xn0), X1 = make_float2(xn1, xn1), X2 = make_float2(xn2, xn2);
 #pragma unroll
@@ -209,19 +244,36 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_batched(BatchArgs B) {
                     cst[2 * hh + 1] = c.y;
                 }
             }
+            __syncthreads();  // row 0's record visible
             for (int p = 0; p < m; ++p) {
                 const long long k = k0 + p;
                 const int i = i_next;
                 const float x0 = xn0, x1 = xn1, x2 = xn2;
+                const int slot = p & 1;
                 if (p + 1 < m) {
-                    i_next = row_of(p + 1);
-                    xn0 = X[(size_t)i_next * 3];
-                    xn1 = X[(size_t)i_next * 3 + 1];
-                    xn2 = X[(size_t)i_next * 3 + 2];
+                    i_next = i_far;
+                    xn0 = xf0;
+                    xn1 = xf1;
+                    xn2 = xf2;
+                    i_far = p + 2 < m ? row_of(p + 2) : -1;
+                    if (i_far >= 0) {
+                        xf0 = X[(size_t)i_far * 3];
+                        xf1 = X[(size_t)i_far * 3 + 1];
+                        xf2 = X[(size_t)i_far * 3 + 2];
+                    }
                 }
                 AtomStats st{};
                 DF t_vdf{0.f, 0.f};
                 float ai = 0.f, gmx = 0.f, inv = 0.f;
+                LaneAtoms at_cur;
+                // the next row's record travels unless it is being rewritten
+                const bool pre_next = p + 1 < m && i_next != i && i_next != i_prev;
+                if (warp == 0 && pre_next) {
+                    int4 *dst = aring + (size_t)(slot ^ 1) * kAtomRecord;
+                    cp16(dst + lane, grec + (size_t)i_next * kAtomRecord + lane);
+                    cp16(dst + 32 + lane, grec + (size_t)i_next * kAtomRecord + 32 + lane);
+                    commit();
+                }
                 if (!ctrl) {
                     float qv[G];
                     int qj[G];
@@ -248,13 +300,29 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_batched(BatchArgs B) {
                     const int wj = __reduce_min_sync(FULL, km == wk ? qj[0] : 0x7FFFFFFF);
                     if (lane == 0) red[par][warp] = BRed{wk, wj};
                 } else {
-                    if (p + 1 < m && i_next != i) at_nxt = load_atoms(grec + (size_t)i_next * kAtomRecord, lane);
-                    ai = a[i];
+                    int4 *rec = aring + (size_t)slot * kAtomRecord;
+                    if (!pre_cur) {
+                        rec[lane] = grec[(size_t)i * kAtomRecord + lane];
+                        rec[32 + lane] = grec[(size_t)i * kAtomRecord + 32 + lane];
+                        __syncwarp();
+                    }
+                    at_cur = load_atoms(rec, lane);
+                    float ra, ia;
+                    if (m <= kRowMax) {
+                        const float4 ar = arow[i];
+                        ai = ar.x;
+                        ra = ar.y;
+                        ia = ar.z;
+                    } else {
+                        ai = a[i];
+                        ra = ai > 0.f ? 1.f / ai : 0.f;
+                        ia = ai > 0.f ? 1.f / (2.f * rho * ai) : 0.f;
+                    }
                     auto grad = [&](int j) -> float { return cost3f(x0, x1, x2, ys[j]) + qh[j]; };
                     st = atom_stats(at_cur, grad, ai, B.variant != SR_OT_BCPFW, &t_vdf);
                     if (B.variant == SR_OT_BCPFW && ai > 0.f) {
-                        gmx = st.t_v / ai;             // gamma_max = alpha_v
-                        inv = 1.f / (2.f * rho * ai);  // eq. 10 with d = a_i (e_j* - e_v)
+                        gmx = st.t_v * ra;  // gamma_max = alpha_v = t_v / a_i
+                        inv = ia;           // eq. 10 with d = a_i (e_j* - e_v)
                     }
                 }
                 __syncthreads();  // (A)
@@ -285,11 +353,7 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_batched(BatchArgs B) {
                     if (!applied) {
                         if (lane == 0) sflag[0] = kInstNeedsDense;
                     }
-                    if (p + 1 < m && i_next == i) {  // the same row again: reload it
-                        __syncwarp();
-                        at_nxt = load_atoms(grec + (size_t)i * kAtomRecord, lane);
-                    }
-                    at_cur = at_nxt;
+
                 } else if (p + 1 < m) {
                     const float2 X0 = make_float2(xn0, xn0), X1 = make_float2(xn1, xn1), X2 = make_float2(xn2, xn2);
 #pragma unroll
@@ -302,35 +366,107 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_batched(BatchArgs B) {
                         cst[2 * hh + 1] = c.y;
                     }
                 }
+                if (warp == 0 && pre_next) wait_groups<0>();  // the next row's record
                 par ^= 1;
                 __syncthreads();  // (B)
                 if (sflag[0]) break;
                 ++updates;
+                pre_cur = pre_next;
+                i_prev = i;
             }
             if (sflag[0]) { status = sflag[0]; break; }
 
-            // ---- certificate (Thm 2) every gap_every epochs and at the end ---
+            // ---- certificate (Thm 2) ------------------------------------------
+            // every gap_every epochs and at the end; while the last relative gap
+            // was far above the tolerance the next one is taken later (each
+            // costs two passes over the plan at one SM's share of bandwidth)
             const bool last = ep + 1 == B.max_epochs;
             if (!((ep + 1) % B.gap_every == 0 || last)) continue;
-            // exact column sums s_j (compensated, rows in ascending order)
-            for (int j = tid; j < n; j += NT) {
-                float sh = 0.f, sl = 0.f;
-                for (int i = 0; i < m; ++i) {
-                    const float t = T[(size_t)i * n + j];
-                    const float y = __fsub_rn(t, sl);
-                    const float tt = __fadd_rn(sh, y);
-                    sl = __fsub_rn(__fsub_rn(tt, sh), y);
-                    sh = tt;
+            if (!last && ep + 1 < next_cert) continue;
+            // exact column sums s_j from the atom records (the plan's nonzeros,
+            // with their double-float weights) as 64-bit fixed-point integers:
+            // integer addition is exact, so the order in which threads add does
+            // not change the result. Scale: 2^fx_exp with every column sum below
+            // the total mass sum_i a_i < 2^(62 - fx_exp).
+            {
+                unsigned long long *csum = reinterpret_cast<unsigned long long *>(pkey);  // n <= kPermMax
+                for (int j = tid; j < n; j += NT) csum[j] = 0ull;
+                __syncthreads();
+                // one row per thread: many records in flight at once
+                for (int i = tid; i < m; i += NT) {
+                    const int4 *g = grec + (size_t)i * kAtomRecord;
+                    const int4 h0 = g[0], e0 = g[1];
+                    const int c = h0.x;
+                    for (int kk = 0; kk < c; ++kk) {
+                        const int4 at = kk == 0 ? e0 : g[1 + kk];
+                        const double t = (double)__int_as_float(at.y) + (double)__int_as_float(at.z);
+                        if (t > 0.0)
+                            atomicAdd(&csum[at.x], (unsigned long long)__double2ll_rn(ldexp(t, fx_exp)));
+                    }
                 }
-                const double s = (double)sh - (double)sl;
-                const double qq = rho64 * (s - (double)b[j]);
-                const float h = (float)qq;
-                qh[j] = h;  // refresh of the running residual
-                ql[j] = (float)((double)h - qq);
+                __syncthreads();
+                for (int j = tid; j < n; j += NT) {
+                    const double sj = ldexp((double)(long long)csum[j], -fx_exp);
+                    const double qq = rho64 * (sj - (double)b[j]);
+                    const float h = (float)qq;
+                    qh[j] = h;  // refresh of the running residual
+                    ql[j] = (float)((double)h - qq);
+                }
             }
             __syncthreads();
             // per row: LMO vertex over all columns, <t_i, c_i>, <t_i, q>
             double lin = 0.0, tq = 0.0, amin = 0.0, feas = 0.0;
+            if (m <= kRowMax) {
+                // (a) the LMO: one warp per row over the columns (x of the
+                // warp's next row loaded while this one is processed)
+                int i = warp;
+                float xi0 = 0.f, xi1 = 0.f, xi2 = 0.f;
+                if (i < m) { xi0 = X[(size_t)i * 3]; xi1 = X[(size_t)i * 3 + 1]; xi2 = X[(size_t)i * 3 + 2]; }
+                for (; i < m; i += NW) {
+                    const int inx = i + NW;
+                    float nx0 = 0.f, nx1 = 0.f, nx2 = 0.f;
+                    if (inx < m) { nx0 = X[(size_t)inx * 3]; nx1 = X[(size_t)inx * 3 + 1]; nx2 = X[(size_t)inx * 3 + 2]; }
+                    float gb = std::numeric_limits<float>::infinity();
+                    int jb = 0x7FFFFFFF;
+                    for (int j = lane; j < n; j += kWarp) {
+                        const float gr = cost3f(xi0, xi1, xi2, ys[j]) + qh[j];
+                        if (gr < gb || jb == 0x7FFFFFFF) { gb = gr; jb = j; }
+                    }
+                    const uint32_t kb = f2key(gb);
+                    const uint32_t wk = __reduce_min_sync(FULL, kb);
+                    const int jm = __reduce_min_sync(FULL, kb == wk ? jb : 0x7FFFFFFF);
+                    if (lane == 0) arow[i].w = __int_as_float(jm);
+                    xi0 = nx0; xi1 = nx1; xi2 = nx2;
+                }
+                __syncthreads();
+                // (b) per row, one row per thread: a_i min_j grad_ij at the LMO
+                // vertex, and the atom sums <t_i, c_i>, <t_i, q>, sum_j t_ij
+                for (int r = tid; r < m; r += NT) {
+                    const float y0 = X[(size_t)r * 3], y1 = X[(size_t)r * 3 + 1], y2 = X[(size_t)r * 3 + 2];
+                    const int jm = __float_as_int(arow[r].w);
+                    const int4 *g = grec + (size_t)r * kAtomRecord;
+                    const int c = g[0].x;
+                    double l1 = 0.0, l2 = 0.0, l3 = 0.0;
+                    for (int kk = 0; kk < c; ++kk) {
+                        const int4 at = g[1 + kk];
+                        const double t = (double)__int_as_float(at.y) + (double)__int_as_float(at.z);
+                        l1 += t * (double)cost3f(y0, y1, y2, ys[at.x]);
+                        l2 += t * ((double)qh[at.x] - (double)ql[at.x]);
+                        l3 += t;
+                    }
+                    const double gmin = (double)cost3f(y0, y1, y2, ys[jm]) + ((double)qh[jm] - (double)ql[jm]);
+                    const double ai = (double)arow[r].x;
+                    lin += l1;
+                    tq += l2;
+                    amin += ai * gmin;
+                    feas = fmax(feas, fabs(l3 - ai) / (ai > 0.0 ? ai : 1e-300));
+                }
+                lin = warp_sum(lin);
+                tq = warp_sum(tq);
+                amin = warp_sum(amin);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) feas = fmax(feas, __shfl_xor_sync(FULL, feas, o));
+            } else
             for (int i = warp; i < m; i += NW) {
                 const float xi0 = X[(size_t)i * 3], xi1 = X[(size_t)i * 3 + 1], xi2 = X[(size_t)i * 3 + 2];
                 float gb = std::numeric_limits<float>::infinity();
@@ -400,6 +536,11 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_batched(BatchArgs B) {
             gap = cacc[61];
             feas_err = cacc[62];
             if (B.tol > 0.0 && gap <= B.tol * f && feas_err <= kFeasTol) { ++ep; break; }
+            if (B.tol > 0.0) {
+                const double rel = f > 0.0 ? gap / f : 0.0;
+                const long long skip = rel > 1000.0 * B.tol ? 8 : (rel > 100.0 * B.tol ? 4 : (rel > 10.0 * B.tol ? 2 : 1));
+                next_cert = ep + 1 + skip * B.gap_every;
+            }
         }
         if (status == kInstOk && B.tol > 0.0 && !(gap <= B.tol * f && feas_err <= kFeasTol))
             status = kInstNotConverged;
