@@ -47,31 +47,33 @@ FLOPS_PER_GRAD = 8        # d = 3 cost (3 sub, 3 mul/fma) + residual add + compa
 BATCH_WORKLOADS = ("colour_batch512", "colour_batch64_2048")
 
 # DRAM bytes (read + write) per launch of a workload's dominant kernel from one
-# ncu capture (summaries in profiles/), valid only while the kernel sources
-# are the ones captured: the digest of csrc/ at capture time must match.
+# ncu capture (summaries in profiles/), valid only while the sources that kernel
+# is built from are the ones captured: their digest at capture time must match.
 CAPTURED_TRAFFIC = {
-    ("colour4096_fp32", "roofline"): {"bytes": 4376320, "digest": "90dea680f85438af"},
-    ("feature8192_d128", "roofline_cost"): {"bytes": 4291840 + 207535104, "digest": "90dea680f85438af"},
-    ("colour_batch64_2048", "roofline_adjoint"): {"bytes": 1077010000 + 23416576, "digest": "90dea680f85438af"},
+    ("colour4096_fp32", "roofline"): {
+        "bytes": 4401920, "files": ("solve_pipe.cu", "atoms.cuh", "step.cuh", "reduce.cuh", "cpasync.cuh",
+                                    "common.cuh"), "digest": "8dde81f29623e7cf"},
+    ("feature8192_d128", "roofline_cost"): {
+        "bytes": 4291840 + 207535104, "files": ("cost_bf16.cu", "common.cuh"), "digest": "11122f5d38d60dc1"},
+    ("colour_batch64_2048", "roofline_adjoint"): {
+        "bytes": 1077048576 + 37675264, "files": ("adjoint.cu", "common.cuh"), "digest": "950e1f34bd429fa7"},
 }
 
 
-def kernel_digest():
+def kernel_digest(files):
     import hashlib
-    import glob
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2103_05857_gb300", "csrc", "*"))):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(os.path.basename(f).encode())
-            with open(f, "rb") as fh:
-                h.update(fh.read())
+    for f in files:
+        h.update(f.encode())
+        with open(os.path.join(ROOT, "paper_2103_05857_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def captured_traffic(workload, key):
-    """Bytes per launch from the ncu capture, or None if the kernels changed since."""
+    """Bytes per launch from the ncu capture, or None if the kernel changed since."""
     e = CAPTURED_TRAFFIC.get((workload, key))
-    if e is None or e["digest"] != kernel_digest():
+    if e is None or e["digest"] != kernel_digest(e["files"]):
         return None
     return e["bytes"]
 
@@ -89,6 +91,8 @@ def parse():
     ap.add_argument("--max-epochs", type=int, default=None)
     ap.add_argument("--cpu-epochs", type=int, default=None, help="oracle sample size (epochs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--instances", type=int, default=None,
+                    help="batched workloads: use only the first K instances (small profiling cases)")
     return ap.parse_args()
 
 
@@ -423,8 +427,9 @@ def bench_single(args, s, ws, rank, local):
     supp = float((T > 0).sum().item()) / m
     extra = {"launches": ep_n, "chain_ns_per_update": 1e6 * avg / m, "cert_avg_ms": ce_ms / max(ce_n, 1),
              "hbm_bytes_per_update": 8 * supp, "mean_support": supp}
-    kname = ("k_epoch_sparse (one CTA, m block updates; active-set, pairwise)" if s["variant"] != "BCFW"
-             else "k_epoch (one CTA, m block updates; dense rows)")
+    kname = {"BCPFW": "k_epoch_pipe (one CTA, m block updates; active-set, pairwise, two control warps)",
+             "BCAFW": "k_epoch_sparse (one CTA, m block updates; active-set, away steps)",
+             "BCFW": "k_epoch (one CTA, m block updates; dense rows)"}[s["variant"]]
     roof = alu_roofline(FLOPS_PER_GRAD * n * m, avg, peaks, peak_src, kname, extra)
     cfg = config_for(args, s, inst, ws)
     line = {"metric": metric_for(s),
@@ -457,6 +462,8 @@ def bench_batch(args, s, ws, rank, local):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     allinst = load(args.workload)
+    if args.instances:
+        allinst = allinst[: args.instances]
     share = lpt_partition([i.m * i.n for i in allinst], ws)[rank]
     insts = [allinst[k] for k in share]
     stream = torch.cuda.current_stream(dev)
@@ -510,6 +517,33 @@ def bench_batch(args, s, ws, rank, local):
             "epochs_max": max(r["epochs"] for r in res0), "epochs_median": float(np.median([r["epochs"] for r in res0])),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "roofline": roof, "clocks": clk}
+    # the same instances solved one after another on the single-instance path
+    # (sr_ot_solve, same rule and tolerance): 32 evenly spaced instances,
+    # extrapolated to the whole share by their block updates
+    if not backward:
+        sample = list(range(0, len(insts), max(1, len(insts) // 32)))[:32]
+        seq_upd, seq_ms = 0, 0.0
+        for k in sample:
+            inst = insts[k]
+            Xs, Ys = (torch.as_tensor(np.ascontiguousarray(v), dtype=torch.float32, device=dev) for v in (inst.X, inst.Y))
+            as_, bs = (torch.as_tensor(np.ascontiguousarray(v), dtype=torch.float32, device=dev) for v in (inst.a, inst.b))
+            Ts = torch.zeros((inst.m, inst.n), dtype=torch.float32, device=dev)
+            h.solve(as_, bs, Ts, X=Xs, Y=Ys, precision=S.FP32, max_epochs=1, **{kk: vv for kk, vv in kw.items() if kk != "max_epochs"})
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = h.solve(as_, bs, Ts, X=Xs, Y=Ys, precision=S.FP32, **kw)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            seq_ms += e0.elapsed_time(e1)
+            seq_upd += r["block_updates"]
+        seq_rate = seq_upd / (seq_ms / 1e3)
+        line["sequential_baseline"] = {
+            "value": seq_rate, "unit": UNIT,
+            "sample": f"{len(sample)} of {len(insts)} instances solved one after another with sr_ot_solve "
+                      f"({s['variant']}-{s['step']}, same tolerance), {seq_ms / 1e3:.2f} s for {seq_upd} block updates",
+            "extrapolated_s": (updates / len(out)) / seq_rate,
+            "batched_speedup": value / seq_rate}
     g_ms, g_n = prof[S.PROF_GRAD]
     if g_n:
         tbytes = 4.0 * pb.total_T + 4.0 * sum(3 * (i.m + i.n) * 2 + i.n * 2 for i in insts)
