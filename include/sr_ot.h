@@ -75,6 +75,16 @@ typedef enum { SR_OT_DEC = 0, SR_OT_ELS = 1 } sr_ot_step;
  * accumulation and FP32 norms (points mode, d a multiple of 64). */
 typedef enum { SR_OT_FP64 = 0, SR_OT_FP32 = 1, SR_OT_FP32_BF16COST = 2 } sr_ot_precision;
 
+/* Active-set epoch kernels for FP32 pairwise solves (sr_ot_options.epoch_kernel). */
+typedef enum {
+    SR_OT_EPOCH_AUTO = 0,
+    SR_OT_EPOCH_TWO_PHASE = 1,    /* the next row's LMO waits for the current update   */
+    SR_OT_EPOCH_PIPELINED = 2,    /* the next row's LMO and away vertex overlap the
+                                     current update (two alternating control warps)    */
+    SR_OT_EPOCH_SPECULATIVE = 3   /* LMOs of the next rows taken ahead against an older
+                                     residual and repaired at the changed columns      */
+} sr_ot_epoch_kernel;
+
 typedef struct {
     int variant;              /* sr_ot_variant                                     */
     int order;                /* sr_ot_order (ignored by SR_OT_FW)                 */
@@ -96,11 +106,14 @@ typedef struct {
     long long trace_capacity;
     int dense_only;           /* 1: FP32 away/pairwise solves keep the dense row
                                  kernel instead of the active-set kernel          */
-    int two_phase;            /* 1: FP32 pairwise solves use the two-phase
-                                 active-set kernel instead of the default
-                                 pipelined one (the next row's LMO and away
-                                 vertex overlap the current update); both make
-                                 the same decisions                                */
+    int epoch_kernel;         /* FP32 pairwise (BCPFW) solves, one of
+                                 sr_ot_epoch_kernel: which active-set kernel
+                                 runs an epoch. All make the same decisions bit
+                                 for bit; AUTO takes the first that applies of
+                                 SPECULATIVE (d = 3 points, cyclic or permuted
+                                 order, n <= 4096), PIPELINED (n <= 8192),
+                                 TWO_PHASE. A kernel that does not apply falls
+                                 back the same way.                            */
 } sr_ot_options;
 
 typedef struct {

@@ -242,6 +242,8 @@ sr_ot_status check_opts(sr_ot_handle h, const sr_ot_options *o) {
     if ((o->variant == SR_OT_BCAFW || o->variant == SR_OT_BCPFW) && o->step != SR_OT_ELS)
         return fail(h, SR_OT_EINVAL, "away and pairwise steps need the exact line search (SR_OT_ELS)");
     if (o->trace && o->trace_capacity < 0) return fail(h, SR_OT_EINVAL, "trace_capacity must be >= 0");
+    if (o->epoch_kernel < SR_OT_EPOCH_AUTO || o->epoch_kernel > SR_OT_EPOCH_SPECULATIVE)
+        return fail(h, SR_OT_EINVAL, "unknown epoch_kernel %d", o->epoch_kernel);
     return SR_OT_OK;
 }
 
@@ -528,7 +530,11 @@ sr_ot_status solve_impl(sr_ot_handle h, const sr_ot_options *o, int m, int n, in
                 if (use_sparse) {
                     EpochArgs<float> As = A;
                     As.resume = dstat_d + 1;
-                    if (o->two_phase || !launch_epoch_pipe(As, h->stream)) launch_epoch_sparse(As, h->stream);
+                    const int ek = o->epoch_kernel;
+                    bool ran = false;
+                    if (ek == SR_OT_EPOCH_AUTO || ek == SR_OT_EPOCH_SPECULATIVE) ran = launch_epoch_spec(As, h->stream);
+                    if (!ran && ek != SR_OT_EPOCH_TWO_PHASE) ran = launch_epoch_pipe(As, h->stream);
+                    if (!ran) launch_epoch_sparse(As, h->stream);
                     EpochArgs<float> Ad = A;
                     Ad.resume_in = dstat_d + 1;  // finishes the epoch only after an overflow
                     launch_epoch<float>(Ad, h->stream);

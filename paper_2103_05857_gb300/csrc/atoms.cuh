@@ -150,11 +150,18 @@ __device__ inline float atom_weight(const LaneAtoms &A, int js, bool *present, i
 // carries no meaning: every reduction over it is by column). Plan entries
 // and the residual pair change exactly as in apply_atoms. jpos, vpos: the
 // record positions of j* (-1 if absent) and v. Returns false (and changes
-// nothing) if j* would be atom 64.
+// nothing) if j* would be atom 64. mid() runs (on every lane, in every case
+// that returns true) after the residual pair has changed and before the plan
+// entries and the record are stored.
+template <typename Mid>
 __device__ inline bool apply_pairwise(const Step<float> &S, const LaneAtoms &A, int jpos, int vpos, DF t_v,
-                                      float rho, float *trow, float *qh, float *ql, int4 *grec, int lane) {
+                                      float rho, float *trow, float *qh, float *ql, int4 *grec, int lane,
+                                      Mid &&mid) {
     const unsigned FULL = 0xffffffffu;
-    if (S.kind != 2 || S.v == S.js || vpos < 0) return true;
+    if (S.kind != 2 || S.v == S.js || vpos < 0) {
+        mid();
+        return true;
+    }
     const bool grows = S.add_js > 0.f;
     const bool append = grows && jpos < 0;
     if (append && A.cnt >= kAtomsMax) return false;
@@ -166,21 +173,21 @@ __device__ inline bool apply_pairwise(const Step<float> &S, const LaneAtoms &A, 
     const DF tj_old = jpos >= 0 ? DF{jh, jl} : DF{0.f, 0.f};
     const DF tj_new = grows ? df_add(tj_old, mv) : tj_old;
     const DF tv_new = S.drop ? DF{0.f, 0.f} : df_add(t_v, DF{-mv.hi, -mv.lo});
-    // plan entries and residual: lane 0 takes j*, lane 1 takes v
-    if (lane < 2) {
-        const int col = lane == 0 ? S.js : S.v;
-        const DF told = lane == 0 ? tj_old : t_v;
-        const DF tn = lane == 0 ? tj_new : tv_new;
-        if (tn.hi != told.hi || tn.lo != told.lo) {
-            trow[col] = tn.hi;
-            const float dlt = __fadd_rn(__fsub_rn(tn.hi, told.hi), __fsub_rn(tn.lo, told.lo));
-            const float d = rho * dlt;
-            const float y = __fsub_rn(d, ql[col]);
-            const float tt = __fadd_rn(qh[col], y);
-            ql[col] = __fsub_rn(__fsub_rn(tt, qh[col]), y);
-            qh[col] = tt;
-        }
+    // residual, then plan entries: lane 0 takes j*, lane 1 takes v
+    const int col = lane == 0 ? S.js : S.v;
+    const DF told = lane == 0 ? tj_old : t_v;
+    const DF tn = lane == 0 ? tj_new : tv_new;
+    const bool chg = lane < 2 && (tn.hi != told.hi || tn.lo != told.lo);
+    if (chg) {
+        const float dlt = __fadd_rn(__fsub_rn(tn.hi, told.hi), __fsub_rn(tn.lo, told.lo));
+        const float d = rho * dlt;
+        const float y = __fsub_rn(d, ql[col]);
+        const float tt = __fadd_rn(qh[col], y);
+        ql[col] = __fsub_rn(__fsub_rn(tt, qh[col]), y);
+        qh[col] = tt;
     }
+    mid();
+    if (chg) trow[col] = tn.hi;
     // record: positions of j* and v after the step
     int cnt = A.cnt;
     const int jp = append ? cnt : jpos;
@@ -208,6 +215,11 @@ __device__ inline bool apply_pairwise(const Step<float> &S, const LaneAtoms &A, 
     }
     if (lane == 0 && cnt != A.cnt) grec[0] = make_int4(cnt, 0, 0, 0);
     return true;
+}
+
+__device__ inline bool apply_pairwise(const Step<float> &S, const LaneAtoms &A, int jpos, int vpos, DF t_v,
+                                      float rho, float *trow, float *qh, float *ql, int4 *grec, int lane) {
+    return apply_pairwise(S, A, jpos, vpos, t_v, rho, trow, qh, ql, grec, lane, [] {});
 }
 
 // Apply step S of row i: atoms (with j* appended when it enters), dense

@@ -146,6 +146,10 @@ bool launch_epoch_sparse(const EpochArgs<float> &args, cudaStream_t st);
 // Pipelined sparse-support epoch for pairwise steps (the next row's argmin
 // overlaps the current update). False unless BCPFW and n fits.
 bool launch_epoch_pipe(const EpochArgs<float> &args, cudaStream_t st);
+// Speculative pairwise epoch: the LMOs of the next rows are taken ahead
+// against an older residual and repaired at the columns changed since. False
+// unless BCPFW, d = 3 points, cyclic or permuted order and n <= 4096.
+bool launch_epoch_spec(const EpochArgs<float> &args, cudaStream_t st);
 
 // Atom records of a dense plan; *overflow becomes 1 if a row has > 63 atoms.
 void launch_build_atoms(int m, int n, const float *T, int4 *rec, int *overflow, cudaStream_t st);

@@ -1,0 +1,438 @@
+// solve_spec.cu -- one epoch of BCPFW (pairwise steps, Alg. A.3, exact line
+// search eq. 10) on a single instance with d = 3 points, cyclic or permuted
+// block order, the heavy per-row work of the next updates done ahead of the
+// update chain.
+//
+// A pairwise step of row i changes the residual in two columns only (the LMO
+// vertex j* and the away vertex v). So the statistics of a later row can be
+// taken against an older residual and repaired: for update u, producer warps
+// take the minimum of C_ij + q_j over their own segment of columns, and the
+// atom warp the away vertex (maximum of the gradient over the row's atoms),
+// each with the residual as it stood after `ver` updates, ver >= u - kSpecLag.
+// When the chain warp reaches update u it knows which columns changed since
+// (a per-column index of the last update that changed it, and the columns of
+// the last kSpecLag updates in registers):
+//   - a segment minimum whose column has not changed since ver is exact for
+//     every unchanged column of its segment;
+//   - every column changed in the last kSpecLag updates is evaluated with the
+//     current residual (one per lane);
+//   - a segment whose minimum sits on a changed column is recomputed in full,
+//     and so are the away statistics if one of the row's atoms changed (both
+//     rare).
+// The minimum over these, ties to the smallest column, is the exact LMO. All
+// decisions equal those of the two-phase kernel (solve_sparse.cu) bit for bit.
+//
+// Warps 0..NWP-1 produce segment minima (their columns: quads tid + NTC g),
+// warp NWP (the atom warp) streams the atom records, takes the away
+// statistics and publishes the row's data, warp NWP+1 is the chain. With
+// NWP = 4 the chain shares its scheduler with one producer only. They
+// synchronise through mbarriers only (no polling): per slot a "full" barrier
+// on which the producers and the atom warp arrive (release) once their words
+// for update u are stored and on which the chain waits (acquire), and per
+// update a "done" barrier on which the chain arrives once the residual of
+// update u is in shared memory (before the update's global stores, so the
+// release never waits on them) and on which producers wait before reading
+// the residual for update u + kSpecLag + 1. Every wait is bounded.
+#include <algorithm>
+#include <climits>
+#include <limits>
+
+#include "atoms.cuh"
+#include "common.cuh"
+#include "cpasync.cuh"
+#include "internal.h"
+#include "step.cuh"
+
+namespace srot {
+
+namespace {
+
+constexpr int kSmemMax = 227 * 1024;
+constexpr int kSpecLag = 4;        // producers run at most this many updates ahead of the chain
+constexpr int kSpecSlots = 8;      // candidate / atom-warp slots (> kSpecLag)
+constexpr int kSpecRecAhead = 2;   // atom records are fetched this many updates early
+constexpr int kSpecRecSlots = 8;   // record slots (> kSpecLag + kSpecRecAhead)
+constexpr long long kSpecSpin = 1ll << 26;  // polls before a wait gives up
+static_assert(kSpecSlots > kSpecLag && kSpecRecSlots > kSpecLag + kSpecRecAhead, "slot rings too small");
+
+__device__ inline unsigned saddr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ inline int vload(const int *p) { return *reinterpret_cast<const volatile int *>(p); }
+__device__ inline void vstore(int *p, int v) { *reinterpret_cast<volatile int *>(p) = v; }
+__device__ inline void mbar_init(uint64_t *b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(saddr(b)), "r"(count) : "memory");
+}
+__device__ inline void mbar_arrive(uint64_t *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(saddr(b)) : "memory");
+}
+// One bounded probe of phase `parity` (the hardware may suspend the warp
+// for a while before it answers false).
+__device__ inline bool mbar_try(uint64_t *b, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(saddr(b)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+constexpr int kAtomWords = 3;  // atom warp output per update: int4 words
+
+}  // namespace
+
+template <int NWP, int G>
+__global__ void __launch_bounds__(NWP * kWarp + 2 * kWarp, 1) k_epoch_spec(EpochArgs<float> A) {
+    constexpr int NTC = NWP * kWarp;  // producer threads
+    constexpr int AW = NWP;  // the atom warp; warp NWP + 1 is the chain
+    constexpr int NT = NTC + 2 * kWarp;
+    constexpr int WID = NTC * 4 * G;
+    static_assert(WID <= 8192, "column index must fit 13 bits");
+    static_assert(NWP + 2 * kSpecLag <= kWarp, "candidates and changed columns must fit one warp");
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *qh = reinterpret_cast<float *>(smem);
+    float *ql = qh + WID;
+    float4 *ys = reinterpret_cast<float4 *>(ql + WID);
+    int *lastmod = reinterpret_cast<int *>(ys + WID);            // last update that changed column j
+    int4 *aring = reinterpret_cast<int4 *>(lastmod + WID);       // kSpecRecSlots atom records
+    int4 *aw = aring + (size_t)kSpecRecSlots * kAtomRecord;       // kSpecSlots x kAtomWords
+    unsigned long long *cand = reinterpret_cast<unsigned long long *>(aw + kSpecSlots * kAtomWords);  // kSpecSlots x NWP
+    uint64_t *full = reinterpret_cast<uint64_t *>(cand + kSpecSlots * NWP);  // kSpecSlots
+    uint64_t *done = full + kSpecSlots;                                      // kSpecSlots
+    int *ctl = reinterpret_cast<int *>(done + kSpecSlots);                   // [0] stop
+
+    const int m = A.in.m, n = A.in.n;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned FULL = 0xffffffffu;
+    const float rho = (float)A.rho;
+    const int order = A.order;
+    int4 *grec = A.atoms;
+    const float INF = std::numeric_limits<float>::infinity();
+
+    // ---- one-time set-up ------------------------------------------------
+    for (int j = tid; j < WID; j += NT) {
+        if (j < n) {
+            const double qq = A.q[j];
+            const float h = (float)qq;
+            qh[j] = h;
+            ql[j] = (float)((double)h - qq);
+            ys[j] = make_float4(A.in.Y[(size_t)j * 3], A.in.Y[(size_t)j * 3 + 1], A.in.Y[(size_t)j * 3 + 2], 0.f);
+        } else {
+            qh[j] = 1e30f;
+            ql[j] = 0.f;
+            ys[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        lastmod[j] = -1;
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kSpecSlots; ++s) {
+            mbar_init(full + s, NWP + 1);
+            mbar_init(done + s, 1);
+        }
+        ctl[0] = 0;
+        if (A.resume) *A.resume = -1;
+    }
+    __syncthreads();
+
+    auto row_of = [&](int u) -> int { return order == SR_OT_PERMUTE ? A.perm[u] : u; };
+    // gradient of row x at column j with the residual as it is now
+    auto grad_at = [&](int j, float x0, float x1, float x2) -> float {
+        const float4 y = ys[j];
+        const float d0 = x0 - y.x, d1 = x1 - y.y, d2 = x2 - y.z;
+        return fmaf(d2, d2, fmaf(d1, d1, __fmul_rn(d0, d0))) + qh[j];
+    };
+    // producers and the atom warp: wait until the chain has applied update
+    // u - kSpecLag - 1 (its residual is then visible); false to stop
+    auto gate = [&](int u) -> bool {
+        const int p = u - kSpecLag - 1;
+        if (p < 0) return true;
+        long long it = 0;
+        while (!mbar_try(done + p % kSpecSlots, (unsigned)(p / kSpecSlots) & 1u)) {
+            if (vload(ctl)) return false;
+            if (++it > kSpecSpin) {
+                if (lane == 0) {
+                    atomicCAS(A.status, 0, (int)kDevTimeout);
+                    vstore(ctl, 1);
+                }
+                return false;
+            }
+        }
+        return true;
+    };
+    // x and a of the rows of updates u and u + 1 (loaded two updates early)
+    float xa[2][4];
+    auto load_xa = [&](int s, int u) {
+        xa[s][0] = xa[s][1] = xa[s][2] = xa[s][3] = 0.f;
+        if (u < m) {
+            const int i = row_of(u);
+            xa[s][0] = A.in.X[(size_t)i * 3];
+            xa[s][1] = A.in.X[(size_t)i * 3 + 1];
+            xa[s][2] = A.in.X[(size_t)i * 3 + 2];
+            xa[s][3] = A.in.a[i];
+        }
+    };
+    auto shift_xa = [&] {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) xa[0][e] = xa[1][e];
+    };
+
+    if (warp < NWP) {
+        // ================= producers: segment minima =====================
+        float2 ny0[2 * G], ny1[2 * G], ny2[2 * G];
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = 4 * (tid + NTC * g) + 2 * h;
+                const float4 ya = ys[j], yb = ys[j + 1];
+                ny0[2 * g + h] = make_float2(-ya.x, -yb.x);
+                ny1[2 * g + h] = make_float2(-ya.y, -yb.y);
+                ny2[2 * g + h] = make_float2(-ya.z, -yb.z);
+            }
+        load_xa(0, 0);
+        load_xa(1, 1);
+        for (int u = 0; u < m; ++u) {
+            if (!gate(u)) break;
+            const float2 X0 = make_float2(xa[0][0], xa[0][0]), X1 = make_float2(xa[0][1], xa[0][1]),
+                         X2 = make_float2(xa[0][2], xa[0][2]);
+            float qv[G];
+            int qj[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const int j0 = 4 * (tid + NTC * g);
+                const float4 q4 = *reinterpret_cast<const float4 *>(qh + j0);
+                float2 c[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float2 d0 = __fadd2_rn(X0, ny0[2 * g + h]), d1 = __fadd2_rn(X1, ny1[2 * g + h]),
+                                 d2 = __fadd2_rn(X2, ny2[2 * g + h]);
+                    float2 cc = __fmul2_rn(d0, d0);
+                    cc = __ffma2_rn(d1, d1, cc);
+                    c[h] = __ffma2_rn(d2, d2, cc);
+                }
+                const float2 ga = __fadd2_rn(c[0], make_float2(q4.x, q4.y));
+                const float2 gb = __fadd2_rn(c[1], make_float2(q4.z, q4.w));
+                const bool ta = ga.y < ga.x, tb = gb.y < gb.x;
+                const float va = ta ? ga.y : ga.x, vb = tb ? gb.y : gb.x;
+                const int ia = j0 + (ta ? 1 : 0), ib = j0 + (tb ? 3 : 2);
+                const bool tq = vb < va;
+                qv[g] = tq ? vb : va;
+                qj[g] = tq ? ib : ia;
+            }
+#pragma unroll
+            for (int w = 1; w < G; w <<= 1)
+#pragma unroll
+                for (int g = 0; g + w < G; g += 2 * w)
+                    if (qv[g + w] < qv[g]) { qv[g] = qv[g + w]; qj[g] = qj[g + w]; }
+            const uint32_t km = f2key(qv[0]);
+            const uint32_t wk = __reduce_min_sync(FULL, km);
+            const int wj = __reduce_min_sync(FULL, km == wk ? qj[0] : 0x7FFFFFFF);
+            if (lane == 0) {
+                cand[(u % kSpecSlots) * NWP + warp] = (unsigned long long)wk | ((unsigned long long)wj << 32);
+                mbar_arrive(full + u % kSpecSlots);
+            }
+            shift_xa();
+            load_xa(1, u + 2);
+        }
+    } else if (warp == AW) {
+        // ================= atom warp: records, away statistics, row data ==
+        auto fetch_record = [&](int t) {
+            if (t < m) {
+                const int i = row_of(t);
+                int4 *dst = aring + (size_t)(t % kSpecRecSlots) * kAtomRecord;
+                cp16(dst + lane, grec + (size_t)i * kAtomRecord + lane);
+                cp16(dst + 32 + lane, grec + (size_t)i * kAtomRecord + 32 + lane);
+            }
+            commit();
+        };
+        for (int t = 0; t < kSpecRecAhead; ++t) fetch_record(t);
+        load_xa(0, 0);
+        load_xa(1, 1);
+        for (int u = 0; u < m; ++u) {
+            if (!gate(u)) break;
+            wait_groups<kSpecRecAhead - 1>();  // the record of update u has landed
+            __syncwarp();
+            const float x0 = xa[0][0], x1 = xa[0][1], x2 = xa[0][2], au = xa[0][3];
+            LaneAtoms at = load_atoms(aring + (size_t)(u % kSpecRecSlots) * kAtomRecord, lane);
+            DF tvd{0.f, 0.f};
+            auto grad = [&](int j) -> float { return grad_at(j, x0, x1, x2); };
+            const AtomStats st = atom_stats(at, grad, au, false, &tvd);
+            if (lane == 0) {
+                const float ra = au > 0.f ? 1.f / au : 0.f;
+                const float ia = au > 0.f ? 1.f / (2.f * rho * au) : 0.f;
+                const int vv = (st.v >= 0 && st.v < n) ? st.v : 0x1FFF;
+                int4 *o = aw + (u % kSpecSlots) * kAtomWords;
+                o[0] = make_int4(__float_as_int(st.gmax), __float_as_int(tvd.hi), __float_as_int(tvd.lo),
+                                 vv | ((st.vpos + 1) << 13));
+                o[1] = make_int4(__float_as_int(x0), __float_as_int(x1), __float_as_int(x2), __float_as_int(au));
+                o[2] = make_int4(__float_as_int(ra), __float_as_int(ia), row_of(u), 0);
+                mbar_arrive(full + u % kSpecSlots);
+            }
+            fetch_record(u + kSpecRecAhead);
+            shift_xa();
+            load_xa(1, u + 2);
+        }
+        wait_groups<0>();
+    } else {
+        // ================= the update chain ==============================
+        // lane NWP + 2t + s holds column s (0: j*, 1: v) changed by update u-1-t
+        int hcol = -1;
+        for (int u = 0; u < m; ++u) {
+            const long long k = A.k0 + u;
+            const int slot = u % kSpecSlots;
+            bool quit = false;
+            {
+                long long it = 0;
+                while (!mbar_try(full + slot, (unsigned)(u / kSpecSlots) & 1u)) {
+                    if (vload(ctl)) { quit = true; break; }
+                    if (++it > kSpecSpin) {
+                        if (lane == 0) atomicCAS(A.status, 0, (int)kDevTimeout);
+                        quit = true;
+                        break;
+                    }
+                }
+            }
+            if (quit) break;
+            const unsigned long long cw = lane < NWP ? cand[slot * NWP + lane] : 0ull;
+            const int4 w0 = aw[slot * kAtomWords], w1 = aw[slot * kAtomWords + 1], w2 = aw[slot * kAtomWords + 2];
+            const int row = w2.z;
+            const int ver = u > kSpecLag ? u - kSpecLag : 0;  // residual age of every word of update u
+            const float x0 = __int_as_float(w1.x), x1 = __int_as_float(w1.y), x2 = __int_as_float(w1.z);
+            const float ai = __int_as_float(w1.w), ra = __int_as_float(w2.x), ia = __int_as_float(w2.y);
+            // the atom warp's copy of the record (ordered by the full barrier)
+            LaneAtoms at = load_atoms(aring + (size_t)(u % kSpecRecSlots) * kAtomRecord, lane);
+            auto grad = [&](int j) -> float { return grad_at(j, x0, x1, x2); };
+            // LMO: clean segment minima, the recently changed columns, recomputed segments
+            uint32_t key = 0xFFFFFFFFu;
+            int col = 0x7FFFFFFF;
+            bool stale = false;
+            if (lane < NWP) {
+                const int cj = (int)(cw >> 32);
+                stale = lastmod[cj] >= ver;
+                if (!stale) {
+                    key = (uint32_t)cw;
+                    col = cj;
+                }
+            } else if (hcol >= 0) {
+                key = f2key(grad(hcol));
+                col = hcol;
+            }
+            // away statistics: the atom warp's unless an atom's column changed since
+            const bool adirty = (at.j[0] >= 0 && lastmod[at.j[0]] >= ver) ||
+                                (at.cnt > 32 && at.j[1] >= 0 && lastmod[at.j[1]] >= ver);
+            unsigned fb = __ballot_sync(FULL, stale);
+            while (fb) {
+                const int w = __ffs(fb) - 1;
+                fb &= fb - 1;
+                float bv = INF;
+                int bj = 0x7FFFFFFF;
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    const int j0 = 4 * (kWarp * w + lane + NTC * g);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float gv = grad(j0 + e);
+                        if (gv < bv) { bv = gv; bj = j0 + e; }
+                    }
+                }
+                const uint32_t kb = f2key(bv);
+                const uint32_t wk = __reduce_min_sync(FULL, kb);
+                const int wj = __reduce_min_sync(FULL, kb == wk ? bj : 0x7FFFFFFF);
+                if (lane == w) { key = wk; col = wj; }
+            }
+            const uint32_t fk = __reduce_min_sync(FULL, key);
+            const int js = __reduce_min_sync(FULL, key == fk ? col : 0x7FFFFFFF);
+            const float gmin = key2f(fk);
+            DF tvd{__int_as_float(w0.y), __int_as_float(w0.z)};
+            AtomStats st;
+            if (__any_sync(FULL, adirty)) {
+                st = atom_stats(at, grad, ai, false, &tvd);
+            } else {
+                const int v13 = w0.w & 0x1FFF;
+                st.v = v13 == 0x1FFF ? 0x7FFFFFFF : v13;
+                st.vpos = (w0.w >> 13) - 1;
+                st.gmax = __int_as_float(w0.x);
+                st.t_v = tvd.hi;
+                st.nnz = at.cnt;
+                st.g_aw = st.s2 = st.dda = 0.f;
+            }
+            if (!isfinite(gmin)) {
+                if (lane == 0) atomicCAS(A.status, 0, (int)kDevNonFinite);
+                break;
+            }
+            float gmx = 0.f, inv = 0.f;
+            if (ai > 0.f) {
+                gmx = st.t_v * ra;  // same rounding as the two-phase kernel
+                inv = ia;
+            }
+            bool present = false;
+            int jpos = -1;
+            atom_weight(at, js, &present, &jpos);
+            const Step<float> S = decide_pairwise(st, gmin, js, ai, rho, gmx, inv, n);
+            // after the residual has changed: bookkeeping and the release of
+            // update u, before the plan entries and the record are stored
+            auto publish = [&] {
+                const bool moved = S.kind == 2 && S.v != S.js && st.vpos >= 0;
+                if (lane == 0 && moved) {
+                    lastmod[S.js] = u;
+                    lastmod[S.v] = u;
+                }
+                const int up = __shfl_up_sync(FULL, hcol, 2);
+                const int hl = lane - NWP;
+                hcol = hl < 0 || hl >= 2 * kSpecLag ? -1 : (hl < 2 ? (moved ? (hl == 0 ? S.js : S.v) : -1) : up);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(done + u % kSpecSlots);
+            };
+            const bool ok = apply_pairwise(S, at, jpos, st.vpos, tvd, rho, A.T + (size_t)row * n, qh, ql,
+                                           grec + (size_t)row * kAtomRecord, lane, publish);
+            if (!ok) {  // j* would be a 64th atom: the dense kernel takes over at u
+                if (lane == 0 && A.resume) *A.resume = u;
+                break;
+            }
+            if (lane == 0 && A.trace && k < A.trace_cap) {
+                A.trace[4 * k] = row;
+                A.trace[4 * k + 1] = js;
+                A.trace[4 * k + 2] = (st.v >= 0 && st.v < n) ? st.v : -1;
+                A.trace[4 * k + 3] = __float_as_int(S.gamma);
+            }
+        }
+        if (lane == 0) vstore(ctl, 1);  // releases producers still waiting
+    }
+    __syncthreads();
+    for (int j = tid; j < n; j += NT) A.q[j] = (double)qh[j] - (double)ql[j];
+}
+
+template <int NWP, int G>
+static size_t spec_smem() {
+    constexpr int WID = NWP * kWarp * 4 * G;
+    size_t b = (size_t)WID * (4 + 4 + 16 + 4);
+    b += (size_t)kSpecRecSlots * kAtomRecord * 16;
+    b += (size_t)kSpecSlots * (kAtomWords * 16 + NWP * 8 + 16);
+    b += 16;
+    return b;
+}
+
+template <int NWP, int G>
+static void launch_spec(const EpochArgs<float> &A, cudaStream_t st) {
+    auto kern = k_epoch_spec<NWP, G>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
+        attr_set = true;
+    }
+    kern<<<1, NWP * kWarp + 2 * kWarp, spec_smem<NWP, G>(), st>>>(A);
+}
+
+bool launch_epoch_spec(const EpochArgs<float> &A, cudaStream_t st) {
+    if (A.variant != SR_OT_BCPFW || A.in.cost_mode != kCostPts3) return false;
+    if (A.order != SR_OT_CYCLIC && A.order != SR_OT_PERMUTE) return false;
+    const int n = A.in.n;
+    if (n <= 128 * 4) launch_spec<4, 1>(A, st);
+    else if (n <= 128 * 8) launch_spec<4, 2>(A, st);
+    else if (n <= 128 * 16) launch_spec<4, 4>(A, st);
+    else if (n <= 128 * 32) launch_spec<4, 8>(A, st);
+    else return false;
+    return true;
+}
+
+}  // namespace srot

@@ -519,25 +519,30 @@ def test_fp32_dense_steps_conserve_row_mass(S, h, oracle_mod, variant, order):
 
 @pytest.mark.parametrize("order,m,n,ep,mode", [("CYCLIC", 300, 700, 30, "pts"), ("UNIFORM", 257, 515, 20, "pts"),
                                                ("PERMUTE", 200, 1500, 15, "pts"), ("CYCLIC", 190, 600, 20, "cost"),
-                                               ("CYCLIC", 1024, 4096, 3, "pts")])
-def test_pipelined_pairwise_kernel_matches_two_phase(S, h, oracle_mod, order, m, n, ep, mode):
-    """The pipelined BCPFW kernel (the default) takes the next row's LMO and
-    away vertex over the columns the current update leaves unchanged and
-    completes them at the two changed columns afterwards: every decision
-    (block, LMO vertex, away vertex, step) and the final plan equal the
-    two-phase active-set kernel's bit for bit."""
+                                               ("CYCLIC", 1024, 4096, 3, "pts"), ("PERMUTE", 2048, 3000, 4, "pts"),
+                                               ("CYCLIC", 3, 40, 200, "pts"), ("CYCLIC", 5000, 1025, 2, "pts")])
+def test_pairwise_kernels_match_two_phase(S, h, oracle_mod, order, m, n, ep, mode):
+    """The pipelined BCPFW kernel takes the next row's LMO and away vertex over
+    the columns the current update leaves unchanged and completes them at the
+    two changed columns afterwards; the speculative kernel takes the LMOs of
+    the next rows against an older residual and repairs them at every column
+    changed since. Every decision (block, LMO vertex, away vertex, step) and
+    the final plan equal the two-phase active-set kernel's bit for bit (where
+    a kernel does not apply, the fallback runs and must match as well)."""
     inst = W.colour_instance(17 + m, m, n, rho=10.0, b_dirichlet=True).rounded()
     C = dev(oracle_mod.cost(inst.X, inst.Y), torch.float32) if mode == "cost" else None
     out = []
-    for two in (0, 1):
+    for ek in (S.EPOCH_TWO_PHASE, S.EPOCH_PIPELINED, S.EPOCH_SPECULATIVE):
         cap = ep * m
         tr = torch.full((4 * cap,), -1, dtype=torch.int32, device="cuda")
         T = torch.zeros((m, n), dtype=torch.float32, device="cuda")
         kw = dict(C=C) if C is not None else dict(X=dev(inst.X, torch.float32), Y=dev(inst.Y, torch.float32))
         res = h.solve(dev(inst.a, torch.float32), dev(inst.b, torch.float32), T, precision=S.FP32,
                       variant=S.BCPFW, step=S.ELS, order=getattr(S, order), seed=11, rho=inst.rho,
-                      max_epochs=ep, trace=tr, trace_capacity=cap, two_phase=two, **kw)
+                      max_epochs=ep, trace=tr, trace_capacity=cap, epoch_kernel=ek, **kw)
+        assert res["status"] in (S.OK, S.NOT_CONVERGED), res
         out.append((tr.cpu().numpy(), T.cpu().numpy(), res))
-    np.testing.assert_array_equal(out[0][0], out[1][0])
-    np.testing.assert_array_equal(out[0][1], out[1][1])
-    assert out[0][2]["objective"] == out[1][2]["objective"]
+    for k in (1, 2):
+        np.testing.assert_array_equal(out[0][0], out[k][0])
+        np.testing.assert_array_equal(out[0][1], out[k][1])
+        assert out[0][2]["objective"] == out[k][2]["objective"]
