@@ -82,10 +82,10 @@ constexpr int kAtomWords = 3;  // atom warp output per update: int4 words
 }  // namespace
 
 template <int NWP, int G>
-__global__ void __launch_bounds__(NWP * kWarp + 2 * kWarp, 1) k_epoch_spec(EpochArgs<float> A) {
+__global__ void __launch_bounds__(NWP * kWarp + 3 * kWarp, 1) k_epoch_spec(EpochArgs<float> A) {
     constexpr int NTC = NWP * kWarp;  // producer threads
-    constexpr int AW = NWP;  // the atom warp; warp NWP + 1 is the chain
-    constexpr int NT = NTC + 2 * kWarp;
+    constexpr int AW = NWP;  // the atom warp; warps NWP + 1, NWP + 2 are the chain
+    constexpr int NT = NTC + 3 * kWarp;
     constexpr int WID = NTC * 4 * G;
     static_assert(WID <= 8192, "column index must fit 13 bits");
     static_assert(NWP + 2 * kSpecLag <= kWarp, "candidates and changed columns must fit one warp");
@@ -99,7 +99,9 @@ __global__ void __launch_bounds__(NWP * kWarp + 2 * kWarp, 1) k_epoch_spec(Epoch
     unsigned long long *cand = reinterpret_cast<unsigned long long *>(aw + kSpecSlots * kAtomWords);  // kSpecSlots x NWP
     uint64_t *full = reinterpret_cast<uint64_t *>(cand + kSpecSlots * NWP);  // kSpecSlots
     uint64_t *done = full + kSpecSlots;                                      // kSpecSlots
-    int *ctl = reinterpret_cast<int *>(done + kSpecSlots);                   // [0] stop
+    uint64_t *decided = done + kSpecSlots;                                   // kSpecSlots
+    int2 *dec = reinterpret_cast<int2 *>(decided + kSpecSlots);              // columns update u changes
+    int *ctl = reinterpret_cast<int *>(dec + kSpecSlots);                    // [0] stop
 
     const int m = A.in.m, n = A.in.n;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -128,6 +130,8 @@ __global__ void __launch_bounds__(NWP * kWarp + 2 * kWarp, 1) k_epoch_spec(Epoch
         for (int s = 0; s < kSpecSlots; ++s) {
             mbar_init(full + s, NWP + 1);
             mbar_init(done + s, 1);
+            mbar_init(decided + s, 1);
+            dec[s] = make_int2(-1, -1);
         }
         ctl[0] = 0;
         if (A.resume) *A.resume = -1;
@@ -274,25 +278,35 @@ __global__ void __launch_bounds__(NWP * kWarp + 2 * kWarp, 1) k_epoch_spec(Epoch
         }
         wait_groups<0>();
     } else {
-        // ================= the update chain ==============================
-        // lane NWP + 2t + s holds column s (0: j*, 1: v) changed by update u-1-t
-        int hcol = -1;
-        for (int u = 0; u < m; ++u) {
-            const long long k = A.k0 + u;
-            const int slot = u % kSpecSlots;
-            bool quit = false;
-            {
-                long long it = 0;
-                while (!mbar_try(full + slot, (unsigned)(u / kSpecSlots) & 1u)) {
-                    if (vload(ctl)) { quit = true; break; }
-                    if (++it > kSpecSpin) {
-                        if (lane == 0) atomicCAS(A.status, 0, (int)kDevTimeout);
-                        quit = true;
-                        break;
+        // ================= two chain warps: even and odd updates =========
+        // Warp NWP + 1 + (u & 1) takes update u. It prepares u (segment
+        // minima, the columns changed by updates ver..u-2, the away
+        // statistics) while the other warp decides and applies u - 1; then
+        // it takes the two columns e1, e2 that u - 1 changes, waits until
+        // their residual is stored, evaluates them and decides.
+        const int cwi = warp - (NWP + 1);
+        bool aborted = false;
+        auto wait_bar = [&](uint64_t *b, unsigned parity) -> bool {
+            long long it = 0;
+            while (!mbar_try(b, parity)) {
+                if (vload(ctl)) return false;
+                if (++it > kSpecSpin) {
+                    if (lane == 0) {
+                        atomicCAS(A.status, 0, (int)kDevTimeout);
+                        vstore(ctl, 1);
                     }
+                    return false;
                 }
             }
-            if (quit) break;
+            return true;
+        };
+        for (int u = cwi; u < m; u += 2) {
+            const long long k = A.k0 + u;
+            const int slot = u % kSpecSlots;
+            const int ps = (u + kSpecSlots - 1) % kSpecSlots;  // slot of update u - 1
+            const unsigned pp = u >= 1 ? (unsigned)((u - 1) / kSpecSlots) & 1u : 0u;
+            // ---- prepare ------------------------------------------------
+            if (!wait_bar(full + slot, (unsigned)(u / kSpecSlots) & 1u)) { aborted = true; break; }
             const unsigned long long cw = lane < NWP ? cand[slot * NWP + lane] : 0ull;
             const int4 w0 = aw[slot * kAtomWords], w1 = aw[slot * kAtomWords + 1], w2 = aw[slot * kAtomWords + 2];
             const int row = w2.z;
@@ -302,7 +316,7 @@ __global__ void __launch_bounds__(NWP * kWarp + 2 * kWarp, 1) k_epoch_spec(Epoch
             // the atom warp's copy of the record (ordered by the full barrier)
             LaneAtoms at = load_atoms(aring + (size_t)(u % kSpecRecSlots) * kAtomRecord, lane);
             auto grad = [&](int j) -> float { return grad_at(j, x0, x1, x2); };
-            // LMO: clean segment minima, the recently changed columns, recomputed segments
+            // clean segment minima and the columns changed by updates ver..u-2
             uint32_t key = 0xFFFFFFFFu;
             int col = 0x7FFFFFFF;
             bool stale = false;
@@ -313,13 +327,17 @@ __global__ void __launch_bounds__(NWP * kWarp + 2 * kWarp, 1) k_epoch_spec(Epoch
                     key = (uint32_t)cw;
                     col = cj;
                 }
-            } else if (hcol >= 0) {
-                key = f2key(grad(hcol));
-                col = hcol;
+            } else if (lane < NWP + 2 * (kSpecLag - 1)) {
+                const int w = u - 2 - ((lane - NWP) >> 1);
+                if (w >= ver && w >= 0) {
+                    const int2 d = dec[w % kSpecSlots];
+                    const int c = ((lane - NWP) & 1) ? d.y : d.x;
+                    if (c >= 0) {
+                        key = f2key(grad(c));
+                        col = c;
+                    }
+                }
             }
-            // away statistics: the atom warp's unless an atom's column changed since
-            const bool adirty = (at.j[0] >= 0 && lastmod[at.j[0]] >= ver) ||
-                                (at.cnt > 32 && at.j[1] >= 0 && lastmod[at.j[1]] >= ver);
             unsigned fb = __ballot_sync(FULL, stale);
             while (fb) {
                 const int w = __ffs(fb) - 1;
@@ -340,12 +358,49 @@ __global__ void __launch_bounds__(NWP * kWarp + 2 * kWarp, 1) k_epoch_spec(Epoch
                 const int wj = __reduce_min_sync(FULL, kb == wk ? bj : 0x7FFFFFFF);
                 if (lane == w) { key = wk; col = wj; }
             }
-            const uint32_t fk = __reduce_min_sync(FULL, key);
-            const int js = __reduce_min_sync(FULL, key == fk ? col : 0x7FFFFFFF);
+            const uint32_t pk = __reduce_min_sync(FULL, key);
+            const int pj = __reduce_min_sync(FULL, key == pk ? col : 0x7FFFFFFF);
+            const bool olddirty = (at.j[0] >= 0 && lastmod[at.j[0]] >= ver) ||
+                                  (at.cnt > 32 && at.j[1] >= 0 && lastmod[at.j[1]] >= ver);
+            // ---- hand-over: the columns update u-1 changes, then their residual
+            int e1 = -1, e2 = -1;
+            if (u >= 1) {
+                if (!wait_bar(decided + ps, pp)) { aborted = true; break; }
+                const int2 d = dec[ps];
+                e1 = d.x;
+                e2 = d.y;
+            }
+            auto hit = [&](int c) { return c >= 0 && (c == e1 || c == e2); };
+            const bool redo_atoms = __any_sync(FULL, olddirty || hit(at.j[0]) || (at.cnt > 32 && hit(at.j[1])));
+            const bool redo_lmo = hit(pj);
+            if (u >= 1 && !wait_bar(done + ps, pp)) { aborted = true; break; }
+            uint32_t fk = pk;
+            int js = pj;
+            if (redo_lmo) {
+                // the prepared minimum sits on a column u - 1 changed: full LMO
+                float bv = INF;
+                int bj = 0x7FFFFFFF;
+                for (int q = lane; q < WID / 4; q += kWarp) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float gv = grad(4 * q + e);
+                        if (gv < bv) { bv = gv; bj = 4 * q + e; }
+                    }
+                }
+                const uint32_t kb = f2key(bv);
+                fk = __reduce_min_sync(FULL, kb);
+                js = __reduce_min_sync(FULL, kb == fk ? bj : 0x7FFFFFFF);
+            } else {
+                const int ec = lane == 0 ? e1 : e2;
+                const uint32_t ke = (lane < 2 && ec >= 0) ? f2key(grad(ec)) : 0xFFFFFFFFu;
+                const uint32_t k1 = __shfl_sync(FULL, ke, 0), k2 = __shfl_sync(FULL, ke, 1);
+                if (e1 >= 0 && (k1 < fk || (k1 == fk && e1 < js))) { fk = k1; js = e1; }
+                if (e2 >= 0 && (k2 < fk || (k2 == fk && e2 < js))) { fk = k2; js = e2; }
+            }
             const float gmin = key2f(fk);
             DF tvd{__int_as_float(w0.y), __int_as_float(w0.z)};
             AtomStats st;
-            if (__any_sync(FULL, adirty)) {
+            if (redo_atoms) {
                 st = atom_stats(at, grad, ai, false, &tvd);
             } else {
                 const int v13 = w0.w & 0x1FFF;
@@ -358,6 +413,7 @@ __global__ void __launch_bounds__(NWP * kWarp + 2 * kWarp, 1) k_epoch_spec(Epoch
             }
             if (!isfinite(gmin)) {
                 if (lane == 0) atomicCAS(A.status, 0, (int)kDevNonFinite);
+                aborted = true;
                 break;
             }
             float gmx = 0.f, inv = 0.f;
@@ -369,24 +425,26 @@ __global__ void __launch_bounds__(NWP * kWarp + 2 * kWarp, 1) k_epoch_spec(Epoch
             int jpos = -1;
             atom_weight(at, js, &present, &jpos);
             const Step<float> S = decide_pairwise(st, gmin, js, ai, rho, gmx, inv, n);
-            // after the residual has changed: bookkeeping and the release of
-            // update u, before the plan entries and the record are stored
+            // ---- decision of u: the columns it changes, for the other warp
+            const bool moved = S.kind == 2 && S.v != S.js && st.vpos >= 0;
+            if (lane == 0) dec[slot] = moved ? make_int2(S.js, S.v) : make_int2(-1, -1);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(decided + slot);
+            // after the residual has changed: release of update u, before the
+            // plan entries and the record are stored
             auto publish = [&] {
-                const bool moved = S.kind == 2 && S.v != S.js && st.vpos >= 0;
                 if (lane == 0 && moved) {
                     lastmod[S.js] = u;
                     lastmod[S.v] = u;
                 }
-                const int up = __shfl_up_sync(FULL, hcol, 2);
-                const int hl = lane - NWP;
-                hcol = hl < 0 || hl >= 2 * kSpecLag ? -1 : (hl < 2 ? (moved ? (hl == 0 ? S.js : S.v) : -1) : up);
                 __syncwarp();
-                if (lane == 0) mbar_arrive(done + u % kSpecSlots);
+                if (lane == 0) mbar_arrive(done + slot);
             };
             const bool ok = apply_pairwise(S, at, jpos, st.vpos, tvd, rho, A.T + (size_t)row * n, qh, ql,
                                            grec + (size_t)row * kAtomRecord, lane, publish);
             if (!ok) {  // j* would be a 64th atom: the dense kernel takes over at u
                 if (lane == 0 && A.resume) *A.resume = u;
+                aborted = true;
                 break;
             }
             if (lane == 0 && A.trace && k < A.trace_cap) {
@@ -396,7 +454,7 @@ __global__ void __launch_bounds__(NWP * kWarp + 2 * kWarp, 1) k_epoch_spec(Epoch
                 A.trace[4 * k + 3] = __float_as_int(S.gamma);
             }
         }
-        if (lane == 0) vstore(ctl, 1);  // releases producers still waiting
+        if (aborted && lane == 0) vstore(ctl, 1);  // releases every other warp still waiting
     }
     __syncthreads();
     for (int j = tid; j < n; j += NT) A.q[j] = (double)qh[j] - (double)ql[j];
@@ -407,7 +465,7 @@ static size_t spec_smem() {
     constexpr int WID = NWP * kWarp * 4 * G;
     size_t b = (size_t)WID * (4 + 4 + 16 + 4);
     b += (size_t)kSpecRecSlots * kAtomRecord * 16;
-    b += (size_t)kSpecSlots * (kAtomWords * 16 + NWP * 8 + 16);
+    b += (size_t)kSpecSlots * (kAtomWords * 16 + NWP * 8 + 3 * 8 + 8);
     b += 16;
     return b;
 }
@@ -420,7 +478,7 @@ static void launch_spec(const EpochArgs<float> &A, cudaStream_t st) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
         attr_set = true;
     }
-    kern<<<1, NWP * kWarp + 2 * kWarp, spec_smem<NWP, G>(), st>>>(A);
+    kern<<<1, NWP * kWarp + 3 * kWarp, spec_smem<NWP, G>(), st>>>(A);
 }
 
 bool launch_epoch_spec(const EpochArgs<float> &A, cudaStream_t st) {
