@@ -23,9 +23,10 @@
 // decisions equal those of the two-phase kernel (solve_sparse.cu) bit for bit.
 //
 // Warps 0..NWP-1 produce segment minima (their columns: quads tid + NTC g),
-// warp NWP (the atom warp) streams the atom records, takes the away
-// statistics and publishes the row's data, warp NWP+1 is the chain. With
-// NWP = 4 the chain shares its scheduler with one producer only. They
+// warps NWP, NWP+1 (atom warps, even and odd updates) stream the atom
+// records, take the away statistics and publish the row's data, warps
+// NWP+2, NWP+3 are the chain (even and odd updates). With NWP = 4 each
+// chain warp shares its scheduler with one producer only. They
 // synchronise through mbarriers only (no polling): per slot a "full" barrier
 // on which the producers and the atom warp arrive (release) once their words
 // for update u are stored and on which the chain waits (acquire), and per
@@ -50,8 +51,8 @@ namespace {
 constexpr int kSmemMax = 227 * 1024;
 constexpr int kSpecLag = 4;        // producers run at most this many updates ahead of the chain
 constexpr int kSpecSlots = 8;      // candidate / atom-warp slots (> kSpecLag)
-constexpr int kSpecRecAhead = 2;   // atom records are fetched this many updates early
-constexpr int kSpecRecSlots = 8;   // record slots (> kSpecLag + kSpecRecAhead)
+constexpr int kSpecRecAhead = 4;   // atom records are fetched this many updates early
+constexpr int kSpecRecSlots = 16;  // record slots (> kSpecLag + kSpecRecAhead)
 constexpr long long kSpecSpin = 1ll << 26;  // polls before a wait gives up
 static_assert(kSpecSlots > kSpecLag && kSpecRecSlots > kSpecLag + kSpecRecAhead, "slot rings too small");
 
@@ -82,10 +83,10 @@ constexpr int kAtomWords = 3;  // atom warp output per update: int4 words
 }  // namespace
 
 template <int NWP, int G>
-__global__ void __launch_bounds__(NWP * kWarp + 3 * kWarp, 1) k_epoch_spec(EpochArgs<float> A) {
+__global__ void __launch_bounds__(NWP * kWarp + 4 * kWarp, 1) k_epoch_spec(EpochArgs<float> A) {
     constexpr int NTC = NWP * kWarp;  // producer threads
-    constexpr int AW = NWP;  // the atom warp; warps NWP + 1, NWP + 2 are the chain
-    constexpr int NT = NTC + 3 * kWarp;
+    constexpr int AW = NWP;  // atom warps NWP, NWP + 1; chain warps NWP + 2, NWP + 3
+    constexpr int NT = NTC + 4 * kWarp;
     constexpr int WID = NTC * 4 * G;
     static_assert(WID <= 8192, "column index must fit 13 bits");
     static_assert(NWP + 2 * kSpecLag <= kWarp, "candidates and changed columns must fit one warp");
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(NWP * kWarp + 3 * kWarp, 1) k_epoch_spec(Epoch
         }
         return true;
     };
-    // x and a of the rows of updates u and u + 1 (loaded two updates early)
+    // x and a of the rows of this warp's next two updates (loaded early)
     float xa[2][4];
     auto load_xa = [&](int s, int u) {
         xa[s][0] = xa[s][1] = xa[s][2] = xa[s][3] = 0.f;
@@ -238,8 +239,10 @@ __global__ void __launch_bounds__(NWP * kWarp + 3 * kWarp, 1) k_epoch_spec(Epoch
             shift_xa();
             load_xa(1, u + 2);
         }
-    } else if (warp == AW) {
-        // ================= atom warp: records, away statistics, row data ==
+    } else if (warp < AW + 2) {
+        // ============ two atom warps (even, odd updates): records, away
+        // ============ statistics, row data
+        const int aw0 = warp - AW;
         auto fetch_record = [&](int t) {
             if (t < m) {
                 const int i = row_of(t);
@@ -249,12 +252,13 @@ __global__ void __launch_bounds__(NWP * kWarp + 3 * kWarp, 1) k_epoch_spec(Epoch
             }
             commit();
         };
-        for (int t = 0; t < kSpecRecAhead; ++t) fetch_record(t);
-        load_xa(0, 0);
-        load_xa(1, 1);
-        for (int u = 0; u < m; ++u) {
+        fetch_record(aw0);
+        fetch_record(aw0 + 2);
+        load_xa(0, aw0);
+        load_xa(1, aw0 + 2);
+        for (int u = aw0; u < m; u += 2) {
             if (!gate(u)) break;
-            wait_groups<kSpecRecAhead - 1>();  // the record of update u has landed
+            wait_groups<1>();  // the record of update u has landed (u + 2 may be in flight)
             __syncwarp();
             const float x0 = xa[0][0], x1 = xa[0][1], x2 = xa[0][2], au = xa[0][3];
             LaneAtoms at = load_atoms(aring + (size_t)(u % kSpecRecSlots) * kAtomRecord, lane);
@@ -274,17 +278,17 @@ __global__ void __launch_bounds__(NWP * kWarp + 3 * kWarp, 1) k_epoch_spec(Epoch
             }
             fetch_record(u + kSpecRecAhead);
             shift_xa();
-            load_xa(1, u + 2);
+            load_xa(1, u + 4);
         }
         wait_groups<0>();
     } else {
         // ================= two chain warps: even and odd updates =========
-        // Warp NWP + 1 + (u & 1) takes update u. It prepares u (segment
+        // Warp NWP + 2 + (u & 1) takes update u. It prepares u (segment
         // minima, the columns changed by updates ver..u-2, the away
         // statistics) while the other warp decides and applies u - 1; then
         // it takes the two columns e1, e2 that u - 1 changes, waits until
         // their residual is stored, evaluates them and decides.
-        const int cwi = warp - (NWP + 1);
+        const int cwi = warp - (NWP + 2);
         bool aborted = false;
         auto wait_bar = [&](uint64_t *b, unsigned parity) -> bool {
             long long it = 0;
@@ -373,6 +377,18 @@ __global__ void __launch_bounds__(NWP * kWarp + 3 * kWarp, 1) k_epoch_spec(Epoch
             auto hit = [&](int c) { return c >= 0 && (c == e1 || c == e2); };
             const bool redo_atoms = __any_sync(FULL, olddirty || hit(at.j[0]) || (at.cnt > 32 && hit(at.j[1])));
             const bool redo_lmo = hit(pj);
+            // what does not depend on the residual of u - 1: the cost of the
+            // row at e1, e2 and the record position of the likely vertex pj
+            const int ec = lane == 0 ? e1 : e2;
+            float ce = 0.f;
+            if (lane < 2 && ec >= 0) {
+                const float4 y = ys[ec];
+                const float d0 = x0 - y.x, d1 = x1 - y.y, d2 = x2 - y.z;
+                ce = fmaf(d2, d2, fmaf(d1, d1, __fmul_rn(d0, d0)));
+            }
+            bool present = false;
+            int jpos = -1;
+            atom_weight(at, pj, &present, &jpos);
             if (u >= 1 && !wait_bar(done + ps, pp)) { aborted = true; break; }
             uint32_t fk = pk;
             int js = pj;
@@ -391,8 +407,7 @@ __global__ void __launch_bounds__(NWP * kWarp + 3 * kWarp, 1) k_epoch_spec(Epoch
                 fk = __reduce_min_sync(FULL, kb);
                 js = __reduce_min_sync(FULL, kb == fk ? bj : 0x7FFFFFFF);
             } else {
-                const int ec = lane == 0 ? e1 : e2;
-                const uint32_t ke = (lane < 2 && ec >= 0) ? f2key(grad(ec)) : 0xFFFFFFFFu;
+                const uint32_t ke = (lane < 2 && ec >= 0) ? f2key(ce + qh[ec]) : 0xFFFFFFFFu;
                 const uint32_t k1 = __shfl_sync(FULL, ke, 0), k2 = __shfl_sync(FULL, ke, 1);
                 if (e1 >= 0 && (k1 < fk || (k1 == fk && e1 < js))) { fk = k1; js = e1; }
                 if (e2 >= 0 && (k2 < fk || (k2 == fk && e2 < js))) { fk = k2; js = e2; }
@@ -421,9 +436,7 @@ __global__ void __launch_bounds__(NWP * kWarp + 3 * kWarp, 1) k_epoch_spec(Epoch
                 gmx = st.t_v * ra;  // same rounding as the two-phase kernel
                 inv = ia;
             }
-            bool present = false;
-            int jpos = -1;
-            atom_weight(at, js, &present, &jpos);
+            if (js != pj) atom_weight(at, js, &present, &jpos);
             const Step<float> S = decide_pairwise(st, gmin, js, ai, rho, gmx, inv, n);
             // ---- decision of u: the columns it changes, for the other warp
             const bool moved = S.kind == 2 && S.v != S.js && st.vpos >= 0;
@@ -478,7 +491,7 @@ static void launch_spec(const EpochArgs<float> &A, cudaStream_t st) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
         attr_set = true;
     }
-    kern<<<1, NWP * kWarp + 3 * kWarp, spec_smem<NWP, G>(), st>>>(A);
+    kern<<<1, NWP * kWarp + 4 * kWarp, spec_smem<NWP, G>(), st>>>(A);
 }
 
 bool launch_epoch_spec(const EpochArgs<float> &A, cudaStream_t st) {
