@@ -51,8 +51,8 @@ BATCH_WORKLOADS = ("colour_batch512", "colour_batch64_2048")
 # is built from are the ones captured: their digest at capture time must match.
 CAPTURED_TRAFFIC = {
     ("colour4096_fp32", "roofline"): {
-        "bytes": 4401920, "files": ("solve_pipe.cu", "atoms.cuh", "step.cuh", "reduce.cuh", "cpasync.cuh",
-                                    "common.cuh"), "digest": "8dde81f29623e7cf"},
+        "bytes": 4398848, "files": ("solve_spec.cu", "atoms.cuh", "step.cuh", "cpasync.cuh", "common.cuh"),
+        "digest": "b92b9df6ebe2dd2d"},
     ("feature8192_d128", "roofline_cost"): {
         "bytes": 4291840 + 207535104, "files": ("cost_bf16.cu", "common.cuh"), "digest": "11122f5d38d60dc1"},
     ("colour_batch64_2048", "roofline_adjoint"): {
@@ -215,6 +215,22 @@ def settings(args):
     if args.cpu_epochs is not None:
         s["cpu_epochs"] = args.cpu_epochs
     return s
+
+
+def epoch_kernel_name(s, n):
+    """The epoch kernel the library runs for these settings (its own dispatch:
+    speculative for pairwise steps on d = 3 points with n <= 4096, pipelined up
+    to n = 8192, else two-phase; FP64 and BCFW keep the dense-row kernel)."""
+    if s["precision"] == "FP64" or s["variant"] == "BCFW":
+        return "k_epoch (one CTA, m block updates; dense rows)"
+    if s["variant"] == "BCAFW":
+        return "k_epoch_sparse (one CTA, m block updates; active-set, away steps)"
+    if s["precision"] != "FP32_BF16COST" and n <= 4096:
+        return ("k_epoch_spec (one CTA, m block updates; pairwise; segment minima and away statistics taken "
+                "ahead by producer warps, two alternating chain warps)")
+    if n <= 8192:
+        return "k_epoch_pipe (one CTA, m block updates; active-set, pairwise, two control warps)"
+    return "k_epoch_sparse (one CTA, m block updates; active-set, pairwise)"
 
 
 def load(name):
@@ -427,9 +443,7 @@ def bench_single(args, s, ws, rank, local):
     supp = float((T > 0).sum().item()) / m
     extra = {"launches": ep_n, "chain_ns_per_update": 1e6 * avg / m, "cert_avg_ms": ce_ms / max(ce_n, 1),
              "hbm_bytes_per_update": 8 * supp, "mean_support": supp}
-    kname = {"BCPFW": "k_epoch_pipe (one CTA, m block updates; active-set, pairwise, two control warps)",
-             "BCAFW": "k_epoch_sparse (one CTA, m block updates; active-set, away steps)",
-             "BCFW": "k_epoch (one CTA, m block updates; dense rows)"}[s["variant"]]
+    kname = epoch_kernel_name(s, n)
     roof = alu_roofline(FLOPS_PER_GRAD * n * m, avg, peaks, peak_src, kname, extra)
     cfg = config_for(args, s, inst, ws)
     line = {"metric": metric_for(s),

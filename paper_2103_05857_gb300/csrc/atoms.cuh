@@ -148,72 +148,121 @@ __device__ inline float atom_weight(const LaneAtoms &A, int js, bool *present, i
 // double-float arithmetic as in apply_atoms; an atom whose weight reaches 0
 // is removed by moving the last atom into its place (the record's order
 // carries no meaning: every reduction over it is by column). Plan entries
-// and the residual pair change exactly as in apply_atoms. jpos, vpos: the
-// record positions of j* (-1 if absent) and v. Returns false (and changes
-// nothing) if j* would be atom 64. mid() runs (on every lane, in every case
-// that returns true) after the residual pair has changed and before the plan
-// entries and the record are stored.
-template <typename Mid>
-__device__ inline bool apply_pairwise(const Step<float> &S, const LaneAtoms &A, int jpos, int vpos, DF t_v,
-                                      float rho, float *trow, float *qh, float *ql, int4 *grec, int lane,
-                                      Mid &&mid) {
+// and the residual pair change exactly as in apply_atoms.
+//
+// In three parts, for kernels that hand the new residual to another warp
+// before they store it: pairwise_plan (new weights; 0: nothing changes, 1: a
+// step, -1: j* would be atom 64 and nothing may change), pairwise_residual
+// (lane 0: column j*, lane 1: column v; the new compensated residual pair
+// from the current one), pairwise_store (plan entries and record).
+struct PairStep {
+    DF tj_old, tj_new, tv_new;
+    int jpos, vpos;  // record positions of j* (-1 if absent) and v
+    bool grows, append;
+};
+__device__ inline int pairwise_plan(const Step<float> &S, const LaneAtoms &A, int jpos, int vpos, DF t_v,
+                                    PairStep *P) {
     const unsigned FULL = 0xffffffffu;
-    if (S.kind != 2 || S.v == S.js || vpos < 0) {
-        mid();
-        return true;
-    }
-    const bool grows = S.add_js > 0.f;
-    const bool append = grows && jpos < 0;
-    if (append && A.cnt >= kAtomsMax) return false;
+    if (S.kind != 2 || S.v == S.js || vpos < 0) return 0;
+    P->jpos = jpos;
+    P->vpos = vpos;
+    P->grows = S.add_js > 0.f;
+    P->append = P->grows && jpos < 0;
+    if (P->append && A.cnt >= kAtomsMax) return -1;
     const DF mv = S.drop ? t_v : DF{S.add_js, 0.f};
-    // old weights of j* and v, from the lanes holding them
+    // old weight of j*, from the lane holding it
     const int jsrc = jpos >= 0 ? (jpos & 31) : 0;
     const float jh = __shfl_sync(FULL, (jpos >> 5) > 0 ? A.t[1].hi : A.t[0].hi, jsrc);
     const float jl = __shfl_sync(FULL, (jpos >> 5) > 0 ? A.t[1].lo : A.t[0].lo, jsrc);
-    const DF tj_old = jpos >= 0 ? DF{jh, jl} : DF{0.f, 0.f};
-    const DF tj_new = grows ? df_add(tj_old, mv) : tj_old;
-    const DF tv_new = S.drop ? DF{0.f, 0.f} : df_add(t_v, DF{-mv.hi, -mv.lo});
-    // residual, then plan entries: lane 0 takes j*, lane 1 takes v
-    const int col = lane == 0 ? S.js : S.v;
-    const DF told = lane == 0 ? tj_old : t_v;
-    const DF tn = lane == 0 ? tj_new : tv_new;
-    const bool chg = lane < 2 && (tn.hi != told.hi || tn.lo != told.lo);
-    if (chg) {
+    P->tj_old = jpos >= 0 ? DF{jh, jl} : DF{0.f, 0.f};
+    P->tj_new = P->grows ? df_add(P->tj_old, mv) : P->tj_old;
+    P->tv_new = S.drop ? DF{0.f, 0.f} : df_add(t_v, DF{-mv.hi, -mv.lo});
+    return 1;
+}
+// Lanes 0 and 1 (others: *chg = false): the lane's column, whether its plan
+// entry changes, and the residual pair after the step from the current pair
+// (qc, lc) of that column.
+__device__ inline void pairwise_residual(const PairStep &P, const Step<float> &S, DF t_v, float rho, int lane,
+                                         float qc, float lc, int *col, bool *chg, float *qn, float *ln) {
+    *col = lane == 0 ? S.js : S.v;
+    const DF told = lane == 0 ? P.tj_old : t_v;
+    const DF tn = lane == 0 ? P.tj_new : P.tv_new;
+    *chg = lane < 2 && (tn.hi != told.hi || tn.lo != told.lo);
+    *qn = qc;
+    *ln = lc;
+    if (*chg) {
         const float dlt = __fadd_rn(__fsub_rn(tn.hi, told.hi), __fsub_rn(tn.lo, told.lo));
         const float d = rho * dlt;
-        const float y = __fsub_rn(d, ql[col]);
-        const float tt = __fadd_rn(qh[col], y);
-        ql[col] = __fsub_rn(__fsub_rn(tt, qh[col]), y);
-        qh[col] = tt;
+        const float y = __fsub_rn(d, lc);
+        const float tt = __fadd_rn(qc, y);
+        *ln = __fsub_rn(__fsub_rn(tt, qc), y);
+        *qn = tt;
     }
-    mid();
-    if (chg) trow[col] = tn.hi;
+}
+__device__ inline void pairwise_store(const PairStep &P, const Step<float> &S, const LaneAtoms &A, DF t_v,
+                                      float *trow, int4 *grec, int lane) {
+    // plan entries: lane 0 takes j*, lane 1 takes v
+    if (lane < 2) {
+        const DF told = lane == 0 ? P.tj_old : t_v;
+        const DF tn = lane == 0 ? P.tj_new : P.tv_new;
+        if (tn.hi != told.hi || tn.lo != told.lo) trow[lane == 0 ? S.js : S.v] = tn.hi;
+    }
     // record: positions of j* and v after the step
     int cnt = A.cnt;
-    const int jp = append ? cnt : jpos;
-    if (append) ++cnt;
-    const bool vgone = !(tv_new.hi > 0.f);
+    const int jp = P.append ? cnt : P.jpos;
+    if (P.append) ++cnt;
+    const bool vgone = !(P.tv_new.hi > 0.f);
     int4 *rec = grec + 1;
-    if (lane == 0 && jp >= 0 && (grows || append))
-        rec[jp] = make_int4(S.js, __float_as_int(tj_new.hi), __float_as_int(tj_new.lo), 0);
+    if (lane == 0 && jp >= 0 && (P.grows || P.append))
+        rec[jp] = make_int4(S.js, __float_as_int(P.tj_new.hi), __float_as_int(P.tj_new.lo), 0);
     if (!vgone) {
-        if (lane == 1) rec[vpos] = make_int4(S.v, __float_as_int(tv_new.hi), __float_as_int(tv_new.lo), 0);
+        if (lane == 1) rec[P.vpos] = make_int4(S.v, __float_as_int(P.tv_new.hi), __float_as_int(P.tv_new.lo), 0);
     } else {
         const int last = cnt - 1;
-        if (last != vpos) {
+        if (last != P.vpos) {
             // move the last atom into v's place: j* (lane 0) when j* was just
             // appended, else the lane that holds the last atom writes it
             if (last == jp) {
-                if (lane == 0) rec[vpos] = make_int4(S.js, __float_as_int(tj_new.hi), __float_as_int(tj_new.lo), 0);
+                if (lane == 0)
+                    rec[P.vpos] = make_int4(S.js, __float_as_int(P.tj_new.hi), __float_as_int(P.tj_new.lo), 0);
             } else if (lane == (last & 31)) {
                 const int sl = last >> 5;
-                rec[vpos] = make_int4(sl ? A.j[1] : A.j[0], __float_as_int(sl ? A.t[1].hi : A.t[0].hi),
-                                      __float_as_int(sl ? A.t[1].lo : A.t[0].lo), 0);
+                rec[P.vpos] = make_int4(sl ? A.j[1] : A.j[0], __float_as_int(sl ? A.t[1].hi : A.t[0].hi),
+                                        __float_as_int(sl ? A.t[1].lo : A.t[0].lo), 0);
             }
         }
         cnt = last;
     }
     if (lane == 0 && cnt != A.cnt) grec[0] = make_int4(cnt, 0, 0, 0);
+}
+
+// The whole step: jpos, vpos are the record positions of j* (-1 if absent)
+// and v. Returns false (and changes nothing) if j* would be atom 64. mid()
+// runs (on every lane, in every case that returns true) after the residual
+// pair has changed and before the plan entries and the record are stored.
+template <typename Mid>
+__device__ inline bool apply_pairwise(const Step<float> &S, const LaneAtoms &A, int jpos, int vpos, DF t_v,
+                                      float rho, float *trow, float *qh, float *ql, int4 *grec, int lane,
+                                      Mid &&mid) {
+    PairStep P;
+    const int r = pairwise_plan(S, A, jpos, vpos, t_v, &P);
+    if (r < 0) return false;
+    if (r == 0) {
+        mid();
+        return true;
+    }
+    int col;
+    bool chg;
+    float qn, ln;
+    const float qc = lane < 2 ? qh[lane == 0 ? S.js : S.v] : 0.f;
+    const float lc = lane < 2 ? ql[lane == 0 ? S.js : S.v] : 0.f;
+    pairwise_residual(P, S, t_v, rho, lane, qc, lc, &col, &chg, &qn, &ln);
+    if (chg) {
+        ql[col] = ln;
+        qh[col] = qn;
+    }
+    mid();
+    pairwise_store(P, S, A, t_v, trow, grec, lane);
     return true;
 }
 
