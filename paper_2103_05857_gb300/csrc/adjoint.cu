@@ -19,9 +19,9 @@
 // registers and the row partials sum_j t_ij (y_j, 1), which a warp
 // reduce-scatter (31 shuffles for 32 values) completes for the tile, so row
 // partials go straight to a workspace with no block barrier in the loop.
-// The 8 warps' column partials are summed in a fixed order at the end. Two
-// small kernels reduce the per-band and per-tile partials in FP64 in a fixed
-// order, so the result does not depend on scheduling.
+// The 8 warps' column partials are summed in a fixed order at the end. A
+// small finishing kernel reduces the per-band and per-tile partials in FP64
+// in a fixed order, so the result does not depend on scheduling.
 #include <algorithm>
 
 #include "common.cuh"
@@ -33,6 +33,7 @@ namespace {
 
 constexpr int kAdjThreads = 256;
 constexpr int kAdjWarps = kAdjThreads / kWarp;
+constexpr int kFinThreads = 256;
 
 // Index of the last instance whose `key` prefix is <= x (instances sorted by key).
 template <typename F>
@@ -187,23 +188,72 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_tiles(AdjArgs<Real> A) {
     }
 }
 
-// dY and db from the column partials (sum over row bands, ascending).
+// acc[c] = sum of p[k * stride + c] over k = 0 .. count-1 in ascending k;
+// the loads of up to kBatch partials are issued before any is added. FP32
+// partials are summed with compensation (Kahan) in FP32 and handed over in
+// double (GB300's FP64 rate is a small fraction of its FP32 rate; the
+// compensated sum is accurate to about one FP32 rounding of the total).
 template <typename Real, int P>
-__global__ void k_adj_cols(AdjArgs<Real> A) {
+__device__ inline void sum_partials(const Real *p, size_t stride, int count, double (&acc)[P]) {
+    constexpr int kBatch = P <= 4 ? 8 : (P <= 8 ? 4 : 1);
+    constexpr bool kF32 = sizeof(Real) == 4;
+    Kahan32 ks[kF32 ? P : 1];
+    for (int k0 = 0; k0 < count; k0 += kBatch) {
+        Real buf[kBatch][P];
+#pragma unroll
+        for (int b = 0; b < kBatch; ++b)
+#pragma unroll
+            for (int c = 0; c < P; ++c) buf[b][c] = k0 + b < count ? __ldg(p + (size_t)(k0 + b) * stride + c) : Real(0);
+#pragma unroll
+        for (int b = 0; b < kBatch; ++b)
+            if (k0 + b < count) {
+#pragma unroll
+                for (int c = 0; c < P; ++c) {
+                    if constexpr (kF32) ks[c].add((float)buf[b][c]);
+                    else acc[c] += (double)buf[b][c];
+                }
+            }
+    }
+    if constexpr (kF32) {
+#pragma unroll
+        for (int c = 0; c < P; ++c) acc[c] = ks[c].value();
+    }
+}
+
+// Finishing pass: each instance owns ceil(m / 256) row blocks (dX from the
+// row partials, summed over column tiles in ascending order) followed by
+// ceil(n / 256) column blocks (dY, db from the column partials, summed over
+// row bands in ascending order); a block never spans two instances.
+template <typename Real, int P>
+__global__ void __launch_bounds__(kFinThreads) k_adj_finish(AdjArgs<Real> A) {
+    __shared__ int sk;
+    if (threadIdx.x == 0) sk = find_inst(A.ninst, (long long)blockIdx.x, [&](int q) { return (long long)A.inst[q].fin0; });
+    __syncthreads();
+    const AdjInst I = A.inst[sk];
     const int d = A.d;
-    for (long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x; gi < A.total_cols;
-         gi += (long long)gridDim.x * blockDim.x) {
-        const int k = find_inst(A.ninst, gi, [&](int q) { return A.inst[q].col0; });
-        const AdjInst I = A.inst[k];
-        const int j = (int)(gi - I.col0);
-        double acc[P];
+    const int rblocks = (I.m + kFinThreads - 1) / kFinThreads;
+    const int lb = (int)blockIdx.x - I.fin0;
+    double acc[P];
 #pragma unroll
-        for (int c = 0; c < P; ++c) acc[c] = 0.0;
-        for (int band = 0; band < I.nbands; ++band) {
-            const Real *p = A.colpart + I.ocp + ((size_t)band * I.n + j) * P;
+    for (int c = 0; c < P; ++c) acc[c] = 0.0;
+    if (lb < rblocks) {
+        const int i = lb * kFinThreads + (int)threadIdx.x;
+        if (i >= I.m || !A.dX) return;
+        sum_partials<Real, P>(A.rowpart + I.orp + (size_t)i * P, (size_t)I.m * P, I.ncol, acc);
+        double rs = 0.0;
 #pragma unroll
-            for (int c = 0; c < P; ++c) acc[c] += (double)p[c];
-        }
+        for (int c = 0; c < P; ++c)
+            if (c == d) rs = acc[c];
+#pragma unroll
+        for (int c = 0; c < P; ++c)
+            if (c < d) {
+                const double xv = (double)A.X[I.oX + (size_t)i * d + c];
+                A.dX[I.oX + (size_t)i * d + c] = (Real)(2.0 * (rs * xv - acc[c]));
+            }
+    } else {
+        const int j = (lb - rblocks) * kFinThreads + (int)threadIdx.x;
+        if (j >= I.n || !(A.dY || A.db)) return;
+        sum_partials<Real, P>(A.colpart + I.ocp + (size_t)j * P, (size_t)I.n * P, I.nbands, acc);
         double s = 0.0;
 #pragma unroll
         for (int c = 0; c < P; ++c)
@@ -220,47 +270,10 @@ __global__ void k_adj_cols(AdjArgs<Real> A) {
     }
 }
 
-// dX from the row partials (sum over column tiles, ascending).
-template <typename Real, int P>
-__global__ void k_adj_rows(AdjArgs<Real> A) {
-    const int d = A.d;
-    for (long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x; gi < A.total_rows;
-         gi += (long long)gridDim.x * blockDim.x) {
-        const int k = find_inst(A.ninst, gi, [&](int q) { return A.inst[q].row0; });
-        const AdjInst I = A.inst[k];
-        const int i = (int)(gi - I.row0);
-        double acc[P];
-#pragma unroll
-        for (int c = 0; c < P; ++c) acc[c] = 0.0;
-        for (int ct = 0; ct < I.ncol; ++ct) {
-            const Real *p = A.rowpart + I.orp + ((size_t)ct * I.m + i) * P;
-#pragma unroll
-            for (int c = 0; c < P; ++c) acc[c] += (double)p[c];
-        }
-        double rs = 0.0;
-#pragma unroll
-        for (int c = 0; c < P; ++c)
-            if (c == d) rs = acc[c];
-#pragma unroll
-        for (int c = 0; c < P; ++c)
-            if (c < d) {
-                const double xv = (double)A.X[I.oX + (size_t)i * d + c];
-                A.dX[I.oX + (size_t)i * d + c] = (Real)(2.0 * (rs * xv - acc[c]));
-            }
-    }
-}
-
 template <typename Real, int P>
 void launch_p(const AdjArgs<Real> &A, cudaStream_t st) {
     k_adj_tiles<Real, P><<<A.total_tiles, kAdjThreads, 0, st>>>(A);
-    if (A.dY || A.db) {
-        const int blocks = (int)std::min<long long>((A.total_cols + 255) / 256, 152 * 8);
-        k_adj_cols<Real, P><<<std::max(blocks, 1), 256, 0, st>>>(A);
-    }
-    if (A.dX) {
-        const int blocks = (int)std::min<long long>((A.total_rows + 255) / 256, 152 * 8);
-        k_adj_rows<Real, P><<<std::max(blocks, 1), 256, 0, st>>>(A);
-    }
+    if (A.dX || A.dY || A.db) k_adj_finish<Real, P><<<A.total_fin, kFinThreads, 0, st>>>(A);
 }
 
 }  // namespace
@@ -281,7 +294,7 @@ AdjTotals adj_plan(int ninst, const int *m, const int *n, int d, int elem_bytes,
     // enough tiles to fill the GPU (152 SMs x 8 CTAs), rows per band a multiple of 64
     const long long target = 152 * 8;
     const long long f = std::max<long long>(1, (target + ncol_total - 1) / std::max<long long>(ncol_total, 1));
-    AdjTotals tot{0, 0, 0, 0, 0};
+    AdjTotals tot{0, 0, 0, 0, 0, 0};
     for (int k = 0; k < ninst; ++k) {
         AdjInst &I = out[k];
         I.m = m[k];
@@ -303,6 +316,8 @@ AdjTotals adj_plan(int ninst, const int *m, const int *n, int d, int elem_bytes,
         tot.rows += m[k];
         tot.colpart += (long long)I.nbands * n[k] * P;
         tot.rowpart += (long long)I.ncol * m[k] * P;
+        I.fin0 = (int)tot.fin_blocks;
+        tot.fin_blocks += (m[k] + kFinThreads - 1) / kFinThreads + (n[k] + kFinThreads - 1) / kFinThreads;
     }
     return tot;
 }

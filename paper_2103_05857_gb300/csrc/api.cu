@@ -707,6 +707,7 @@ sr_ot_status grad_impl(sr_ot_handle h, const sr_ot_options *o, int ninst, const 
     A.total_tiles = (int)tot.tiles;
     A.total_cols = tot.cols;
     A.total_rows = tot.rows;
+    A.total_fin = (int)tot.fin_blocks;
     {
         ProfScope ps(h, SR_OT_PROF_GRAD);
         if (!launch_adjoint<Real>(A, h->stream)) return fail(h, SR_OT_EUNSUPPORTED, "d = %d out of range", d);

@@ -174,10 +174,11 @@ struct AdjInst {
     int tile0;             // first tile (CTA) of this instance
     long long col0, row0;  // prefix sums of n and m over the instances
     long long ocp, orp;    // offsets of the column / row partials
+    int fin0;              // first block of this instance in the finishing pass
 };
 
 struct AdjTotals {
-    long long tiles, cols, rows, colpart, rowpart;
+    long long tiles, cols, rows, colpart, rowpart, fin_blocks;
 };
 
 template <typename Real>
@@ -190,6 +191,7 @@ struct AdjArgs {
     Real *colpart, *rowpart;  // workspace from adj_plan's totals
     int total_tiles;
     long long total_cols, total_rows;
+    int total_fin;  // blocks of the finishing pass
 };
 
 // Padded width of the per-entry partial vector (x or y, then 1): 4, 8, 16 or 32.
@@ -197,7 +199,7 @@ int adj_width(int d);
 // Tiles and workspace of a set of instances (elem_bytes: 4 or 8); fills
 // out[k] except the offsets oX, oY, ob, oT.
 AdjTotals adj_plan(int ninst, const int *m, const int *n, int d, int elem_bytes, AdjInst *out);
-// Launch the tile pass and the two reductions; false if d is out of range.
+// Launch the tile pass and the finishing pass; false if d is out of range.
 template <typename Real>
 bool launch_adjoint(const AdjArgs<Real> &A, cudaStream_t st);
 
