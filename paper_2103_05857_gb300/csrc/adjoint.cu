@@ -23,6 +23,7 @@
 // small finishing kernel reduces the per-band and per-tile partials in FP64
 // in a fixed order, so the result does not depend on scheduling.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -34,6 +35,7 @@ namespace {
 constexpr int kAdjThreads = 256;
 constexpr int kAdjWarps = kAdjThreads / kWarp;
 constexpr int kFinThreads = 256;
+constexpr int kAdjBandMax = 1024;  // rows of a band (adj_plan keeps rh <= this for the FP32 d <= 3 path)
 
 // Index of the last instance whose `key` prefix is <= x (instances sorted by key).
 template <typename F>
@@ -102,89 +104,173 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_tiles(AdjArgs<Real> A) {
                      (!dCm || (reinterpret_cast<uintptr_t>(dCm) & 15) == 0);
     const Real *Xm = A.X ? A.X + I.oX : nullptr;
 
-    Real y[CPT][P], cacc[CPT][P];
+    // column partials: sum over the 8 warps in a fixed order, QC components at a time
+    auto column_partials = [&](Real (&cacc)[CPT][P]) {
 #pragma unroll
-    for (int c = 0; c < CPT; ++c) {
-        const int j = j0 + c;
+        for (int q0 = 0; q0 < P; q0 += QC) {
+            __syncthreads();
 #pragma unroll
-        for (int q = 0; q < P; ++q) {
-            y[c][q] = (q < d && j < I.n && A.Y) ? A.Y[I.oY + (size_t)j * d + q] : (q == d ? Real(1) : Real(0));
-            cacc[c][q] = Real(0);
-        }
-    }
-
-    // Each warp takes groups of R rows (warp w: groups w, w + 8, ...) over all
-    // TW columns of the tile, so a row's partial over the tile is complete
-    // after the warp's reduce-scatter: no block barrier in this loop.
-    for (int r0 = i0 + warp * R; r0 < i1; r0 += kAdjWarps * R) {
-        // all R rows are loaded before anything is stored (dC may not be
-        // proven distinct from T), so the loads are in flight together
-        Real tv[R][CPT];
+            for (int qq = 0; qq < QC; ++qq)
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const bool rv = r0 + r < i1;
-            const size_t off = (size_t)(r0 + r) * I.n + j0;
-            if (V16 && vec) {
-                typename Vec16<Real>::T w;
-                if (rv && j0 < I.n) w = __ldg(reinterpret_cast<const typename Vec16<Real>::T *>(Tm + off));
-                else w = typename Vec16<Real>::T{};
-                const Real *pw = reinterpret_cast<const Real *>(&w);
+                for (int c = 0; c < CPT; ++c) csm[warp][qq][lane * CPT + c] = cacc[c][q0 + qq];
+            __syncthreads();
+            for (int e = tid; e < QC * TW; e += kAdjThreads) {
+                const int qq = e / TW, col = e - qq * TW;
+                const int j = ct * TW + col;
+                Real sum = Real(0);
 #pragma unroll
-                for (int c = 0; c < CPT; ++c) tv[r][c] = pw[c];
-            } else {
-#pragma unroll
-                for (int c = 0; c < CPT; ++c) tv[r][c] = (rv && j0 + c < I.n) ? __ldg(Tm + off + c) : Real(0);
+                for (int w = 0; w < kAdjWarps; ++w) sum += csm[w][qq][col];
+                if (j < I.n) A.colpart[I.ocp + ((size_t)band * I.n + j) * P + q0 + qq] = sum;
             }
         }
-        if (dCm) {
+    };
+    if constexpr (std::is_same<Real, float>::value && P == 4 && CPT == 4) {
+        // FP32, d <= 3: column pairs as packed FP32x2 (two columns per
+        // instruction), the band's (x_i, 1) staged once in shared memory
+        __shared__ float4 xs[kAdjBandMax];
+        for (int i = i0 + tid; i < i1; i += kAdjThreads) {
+            float e[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) e[q] = q < d ? (Xm ? Xm[(size_t)i * d + q] : 0.f) : (q == d ? 1.f : 0.f);
+            xs[i - i0] = make_float4(e[0], e[1], e[2], e[3]);
+        }
+        __syncthreads();
+        float2 y2[2][4], ca2[2][4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float yy[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int j = j0 + 2 * h + e;
+                    yy[e] = (q < d && j < I.n && A.Y) ? A.Y[I.oY + (size_t)j * d + q] : (q == d ? 1.f : 0.f);
+                }
+                y2[h][q] = make_float2(yy[0], yy[1]);
+                ca2[h][q] = make_float2(0.f, 0.f);
+            }
+        for (int r0 = i0 + warp * R; r0 < i1; r0 += kAdjWarps * R) {
+            float4 tv[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                if (r0 + r >= i1) break;
                 const size_t off = (size_t)(r0 + r) * I.n + j0;
+                if (vec) {
+                    tv[r] = (r0 + r < i1 && j0 < I.n) ? __ldg(reinterpret_cast<const float4 *>(Tm + off))
+                                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+                } else {
+                    float e[4];
 #pragma unroll
-                for (int c = 0; c < CPT; ++c)
-                    if (j0 + c < I.n) dCm[off + c] = tv[r][c];
+                    for (int c = 0; c < 4; ++c) e[c] = (r0 + r < i1 && j0 + c < I.n) ? __ldg(Tm + off + c) : 0.f;
+                    tv[r] = make_float4(e[0], e[1], e[2], e[3]);
+                }
             }
-        }
-        Real v[32];
+            if (dCm) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const bool rv = r0 + r < i1;
+                for (int r = 0; r < R; ++r) {
+                    if (r0 + r >= i1) break;
+                    const size_t off = (size_t)(r0 + r) * I.n + j0;
+                    const float e[4] = {tv[r].x, tv[r].y, tv[r].z, tv[r].w};
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (j0 + c < I.n) dCm[off + c] = e[c];
+                }
+            }
+            float v[32];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float2 ta = make_float2(tv[r].x, tv[r].y), tb = make_float2(tv[r].z, tv[r].w);
+                const float4 x4 = r0 + r < i1 ? xs[r0 + r - i0] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float xq[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float2 x2 = make_float2(xq[q], xq[q]);
+                    ca2[0][q] = __ffma2_rn(ta, x2, ca2[0][q]);
+                    ca2[1][q] = __ffma2_rn(tb, x2, ca2[1][q]);
+                    const float2 a2 = __ffma2_rn(tb, y2[1][q], __fmul2_rn(ta, y2[0][q]));
+                    v[r * 4 + q] = a2.x + a2.y;
+                }
+            }
+            const float sres = reduce_scatter32(v, lane);
+            const int r = lane / P, q = lane - (lane / P) * P;
+            if (r0 + r < i1) A.rowpart[I.orp + ((size_t)ct * I.m + (r0 + r)) * P + q] = sres;
+        }
+        Real cacc[CPT][P];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            cacc[0][q] = ca2[0][q].x;
+            cacc[1][q] = ca2[0][q].y;
+            cacc[2][q] = ca2[1][q].x;
+            cacc[3][q] = ca2[1][q].y;
+        }
+        column_partials(cacc);
+    } else {
+        Real y[CPT][P], cacc[CPT][P];
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+            const int j = j0 + c;
 #pragma unroll
             for (int q = 0; q < P; ++q) {
-                const Real xq = q < d ? ((Xm && rv) ? Xm[(size_t)(r0 + r) * d + q] : Real(0))
-                                      : (q == d ? Real(1) : Real(0));
-                Real acc = Real(0);
-#pragma unroll
-                for (int c = 0; c < CPT; ++c) {
-                    cacc[c][q] += tv[r][c] * xq;
-                    acc += tv[r][c] * y[c][q];
-                }
-                v[r * P + q] = acc;
+                y[c][q] = (q < d && j < I.n && A.Y) ? A.Y[I.oY + (size_t)j * d + q] : (q == d ? Real(1) : Real(0));
+                cacc[c][q] = Real(0);
             }
         }
-        const Real sres = reduce_scatter32(v, lane);
-        const int r = lane / P, q = lane - (lane / P) * P;
-        if (r0 + r < i1) A.rowpart[I.orp + ((size_t)ct * I.m + (r0 + r)) * P + q] = sres;
-    }
 
-    // column partials: sum over the 8 warps in a fixed order, QC components at a time
+        // Each warp takes groups of R rows (warp w: groups w, w + 8, ...) over all
+        // TW columns of the tile, so a row's partial over the tile is complete
+        // after the warp's reduce-scatter: no block barrier in this loop.
+        for (int r0 = i0 + warp * R; r0 < i1; r0 += kAdjWarps * R) {
+            // all R rows are loaded before anything is stored (dC may not be
+            // proven distinct from T), so the loads are in flight together
+            Real tv[R][CPT];
 #pragma unroll
-    for (int q0 = 0; q0 < P; q0 += QC) {
-        __syncthreads();
+            for (int r = 0; r < R; ++r) {
+                const bool rv = r0 + r < i1;
+                const size_t off = (size_t)(r0 + r) * I.n + j0;
+                if (V16 && vec) {
+                    typename Vec16<Real>::T w;
+                    if (rv && j0 < I.n) w = __ldg(reinterpret_cast<const typename Vec16<Real>::T *>(Tm + off));
+                    else w = typename Vec16<Real>::T{};
+                    const Real *pw = reinterpret_cast<const Real *>(&w);
 #pragma unroll
-        for (int qq = 0; qq < QC; ++qq)
+                    for (int c = 0; c < CPT; ++c) tv[r][c] = pw[c];
+                } else {
 #pragma unroll
-            for (int c = 0; c < CPT; ++c) csm[warp][qq][lane * CPT + c] = cacc[c][q0 + qq];
-        __syncthreads();
-        for (int e = tid; e < QC * TW; e += kAdjThreads) {
-            const int qq = e / TW, col = e - qq * TW;
-            const int j = ct * TW + col;
-            Real sum = Real(0);
+                    for (int c = 0; c < CPT; ++c) tv[r][c] = (rv && j0 + c < I.n) ? __ldg(Tm + off + c) : Real(0);
+                }
+            }
+            if (dCm) {
 #pragma unroll
-            for (int w = 0; w < kAdjWarps; ++w) sum += csm[w][qq][col];
-            if (j < I.n) A.colpart[I.ocp + ((size_t)band * I.n + j) * P + q0 + qq] = sum;
+                for (int r = 0; r < R; ++r) {
+                    if (r0 + r >= i1) break;
+                    const size_t off = (size_t)(r0 + r) * I.n + j0;
+#pragma unroll
+                    for (int c = 0; c < CPT; ++c)
+                        if (j0 + c < I.n) dCm[off + c] = tv[r][c];
+                }
+            }
+            Real v[32];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const bool rv = r0 + r < i1;
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    const Real xq = q < d ? ((Xm && rv) ? Xm[(size_t)(r0 + r) * d + q] : Real(0))
+                                          : (q == d ? Real(1) : Real(0));
+                    Real acc = Real(0);
+#pragma unroll
+                    for (int c = 0; c < CPT; ++c) {
+                        cacc[c][q] += tv[r][c] * xq;
+                        acc += tv[r][c] * y[c][q];
+                    }
+                    v[r * P + q] = acc;
+                }
+            }
+            const Real sres = reduce_scatter32(v, lane);
+            const int r = lane / P, q = lane - (lane / P) * P;
+            if (r0 + r < i1) A.rowpart[I.orp + ((size_t)ct * I.m + (r0 + r)) * P + q] = sres;
         }
+
+        column_partials(cacc);
     }
 }
 
@@ -303,7 +389,7 @@ AdjTotals adj_plan(int ninst, const int *m, const int *n, int d, int elem_bytes,
         const long long maxb = (m[k] + 63) / 64;
         const int nb0 = (int)std::min<long long>(f, maxb);
         int rh = (m[k] + nb0 - 1) / nb0;
-        rh = ((rh + 63) / 64) * 64;
+        rh = std::min(((rh + 63) / 64) * 64, kAdjBandMax);
         I.rh = rh;
         I.nbands = (m[k] + rh - 1) / rh;
         I.tile0 = (int)tot.tiles;
