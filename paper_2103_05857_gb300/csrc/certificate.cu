@@ -155,17 +155,49 @@ k_gap_rows(Inst<Real> in, const Real *__restrict__ T, double rho, const double *
             float tc_err = 0.f;
             uint32_t kb = 0xFFFFFFFFu;
             jb = 0x7FFFFFFF;
-            for (int j = lane; j < n; j += kWarp) {
-                float t = __ldg(ti + j);
-                float c = cost_at<float>(in, i, j);
-                uint32_t k = f2key(c + __ldg(rq32 + j));
-                if (k < kb || jb == 0x7FFFFFFF) { kb = k; jb = j; }
-                if (t != 0.f) {
-                    rs.add(t);
-                    float p = __fmul_rn(t, c);
-                    tc_err += fmaf(t, c, -p);  // exact rounding error of p (TwoProduct)
-                    tc.add(p);
-                    tr.add(__fmul_rn(t, (float)__ldg(r64 + j)));
+            if (in.cost_mode == kCostGiven) {
+                // given C: kU columns per lane per step, their loads issued
+                // before any is used (the columns are still visited in
+                // ascending order); on-the-fly costs measured faster unbatched
+                constexpr int kU = 4;
+                for (int jb0 = 0; jb0 < n; jb0 += kU * kWarp) {
+                    float tv[kU], cv[kU], qv[kU];
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) {
+                        const int j = jb0 + u * kWarp + lane;
+                        const bool ok = j < n;
+                        tv[u] = ok ? __ldg(ti + j) : 0.f;
+                        cv[u] = ok ? cost_at<float>(in, i, j) : 0.f;
+                        qv[u] = ok ? __ldg(rq32 + j) : 0.f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) {
+                        const int j = jb0 + u * kWarp + lane;
+                        const float t = tv[u], c = cv[u];
+                        uint32_t k = f2key(c + qv[u]);
+                        if (j < n && (k < kb || jb == 0x7FFFFFFF)) { kb = k; jb = j; }
+                        if (t != 0.f) {
+                            rs.add(t);
+                            float p = __fmul_rn(t, c);
+                            tc_err += fmaf(t, c, -p);  // exact rounding error of p (TwoProduct)
+                            tc.add(p);
+                            tr.add(__fmul_rn(t, (float)__ldg(r64 + j)));
+                        }
+                    }
+                }
+            } else {
+                for (int j = lane; j < n; j += kWarp) {
+                    float t = __ldg(ti + j);
+                    float c = cost_at<float>(in, i, j);
+                    uint32_t k = f2key(c + __ldg(rq32 + j));
+                    if (k < kb || jb == 0x7FFFFFFF) { kb = k; jb = j; }
+                    if (t != 0.f) {
+                        rs.add(t);
+                        float p = __fmul_rn(t, c);
+                        tc_err += fmaf(t, c, -p);  // exact rounding error of p (TwoProduct)
+                        tc.add(p);
+                        tr.add(__fmul_rn(t, (float)__ldg(r64 + j)));
+                    }
                 }
             }
             uint32_t wk = __reduce_min_sync(0xffffffffu, kb);
