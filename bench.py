@@ -459,7 +459,7 @@ def bench_single(args, s, ws, rank, local):
     if co_n:
         co_avg = co_ms / co_n
         line["roofline_cost"] = hbm_roofline(4.0 * m * n + 4.0 * (m + n) * d + 2.0 * (m + n) * d, co_avg,
-                                             peaks, peak_src, "k_round_bf16 x2 + k_cost_umma (tcgen05)",
+                                             peaks, peak_src, "k_round_bf16 + k_cost_umma (tcgen05)",
                                              {"tflops_bf16": 2.0 * m * n * d / (co_avg / 1e3) / 1e12})
     h.close()
     return line, inst

@@ -1167,7 +1167,7 @@ sr_ot_status sr_ot_cost_bf16(sr_ot_handle h, int m, int n, int d, const float *X
         msg = launch_cost_bf16(m, n, d, X, Y, C, ws, err, h->stream);
     }
     if (msg) return fail(h, SR_OT_EUNSUPPORTED, "BF16 cost: %s", msg);
-    h->launches += 3;
+    h->launches += 2;  // rounding, GEMM
     CKL(h);
     CK(h, cudaMemcpyAsync(h->h_status, err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));

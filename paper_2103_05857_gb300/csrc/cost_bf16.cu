@@ -248,7 +248,9 @@ __global__ void __launch_bounds__(kThreads) k_cost_umma(const __grid_constant__ 
                 asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
             }
         }
-        if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+        // the staging buffer may be released once the stores have read it;
+        // their global writes complete with the grid
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
@@ -258,22 +260,28 @@ __global__ void __launch_bounds__(kThreads) k_cost_umma(const __grid_constant__ 
     }
 }
 
-// Round to BF16 and FP32 norms of the rounded rows; one warp per row.
-__global__ void k_round_bf16(int rows, int d, const float *__restrict__ X, __nv_bfloat16 *__restrict__ Xb,
-                             float *__restrict__ nrm) {
+// Round to BF16 and FP32 norms of the rounded rows, X's m rows then Y's n
+// rows in one launch; one warp per row.
+__global__ void k_round_bf16(int m, int n, int d, const float *__restrict__ X, __nv_bfloat16 *__restrict__ Xb,
+                             float *__restrict__ nx, const float *__restrict__ Y, __nv_bfloat16 *__restrict__ Yb,
+                             float *__restrict__ ny) {
     const int lane = threadIdx.x & 31;
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int i = w; i < rows; i += nw) {
+    for (int r = w; r < m + n; r += nw) {
+        const bool isx = r < m;
+        const int i = isx ? r : r - m;
+        const float *src = isx ? X : Y;
+        __nv_bfloat16 *dst = isx ? Xb : Yb;
         float s = 0.f;
         for (int k = lane; k < d; k += kWarp) {
-            const __nv_bfloat16 v = __float2bfloat16_rn(X[(size_t)i * d + k]);
-            Xb[(size_t)i * d + k] = v;
+            const __nv_bfloat16 v = __float2bfloat16_rn(src[(size_t)i * d + k]);
+            dst[(size_t)i * d + k] = v;
             const float f = __bfloat162float(v);
             s = fmaf(f, f, s);
         }
         s = warp_sum(s);
-        if (lane == 0) nrm[i] = s;
+        if (lane == 0) (isx ? nx : ny)[i] = s;
     }
 }
 
@@ -324,8 +332,7 @@ const char *launch_cost_bf16(int m, int n, int d, const float *X, const float *Y
     p += r((size_t)m * 4);
     float *ny = reinterpret_cast<float *>(p);
 
-    k_round_bf16<<<std::min((m + 7) / 8, 152 * 8), 256, 0, st>>>(m, d, X, Xb, nx);
-    k_round_bf16<<<std::min((n + 7) / 8, 152 * 8), 256, 0, st>>>(n, d, Y, Yb, ny);
+    k_round_bf16<<<std::min((m + n + 7) / 8, 152 * 8), 256, 0, st>>>(m, n, d, X, Xb, nx, Y, Yb, ny);
 
     CUtensorMap tA, tB, tC;
     if (!encode_2d(&tA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, Xb, d, m, (uint64_t)d * 2, kBK, kBM) ||
