@@ -9,17 +9,19 @@
 // colour centroids (Sec. 5.1); this GEMM form is the library's route for the
 // squared cost of high-dimensional features.
 //
-// Kernel: one CTA of 4 warps per 128 x 128 tile of C. With d <= 256 the whole
-// reduction dimension fits in shared memory at once, so a tile is: TMA loads
-// of the A (x~) and B (y~) tiles in 128-byte-swizzled K-major layout (boxes of
-// 64 BF16 along K), d/16 tcgen05.mma (M = 128, N = 128, K = 16) issued by one
-// thread into a 128-column FP32 accumulator in tensor memory, a commit to an
-// mbarrier, then the epilogue: each warp reads its 32 accumulator lanes
-// (tcgen05.ld 32x32b) in chunks of 32 columns, adds the norms, writes the
-// chunk into the (now unused) operand buffers in the 128-byte-swizzled layout
-// and stores it with a TMA tensor store. Several CTAs per SM overlap one
-// tile's epilogue (the HBM store of 64 KiB) with other tiles' loads and MMAs;
-// the store of C bounds the kernel.
+// Kernel: persistent, one CTA per SM looping over 128 x 128 tiles of C, warp
+// specialised. Warp 0 (one thread) streams the operands with TMA into a ring
+// of four stages, each one 64-wide K block of the A (x~) and B (y~) tiles in
+// the 128-byte-swizzled K-major layout. Warp 1 allocates tensor memory and
+// (one thread) issues the tcgen05.mma (M = 128, N = 128, K = 16) of a tile
+// into one of two 128-column FP32 accumulators, releasing each stage and
+// then the accumulator through tcgen05.commit. Warps 2..9 are the epilogue,
+// two per 32-lane quadrant of the accumulator, each taking half of the
+// tile's columns: it reads its 32 lanes (tcgen05.ld 32x32b) in chunks of 32
+// columns, hands the accumulator back, adds the norms, writes the chunk into
+// one of two 128-byte-swizzled staging buffers and stores it with a TMA
+// tensor store. So the next tile's loads and MMAs run under this tile's
+// stores, and the store of C (the bound) streams without gaps.
 //
 // Every wait on an mbarrier is bounded; a wait that gives up sets an error
 // flag the host reads, and the CTA still frees its tensor memory.
@@ -43,9 +45,13 @@ constexpr int kBM = 128;             // rows of a tile (accumulator lanes)
 constexpr int kBN = 128;             // columns of a tile (accumulator columns)
 constexpr int kBK = 64;              // BF16 elements per 128-byte swizzle row
 constexpr int kBoxBytes = kBM * 128; // one 128 x 64 BF16 box = 16 KiB
-constexpr int kThreads = 128;
-constexpr uint32_t kTmemCols = 128;
-constexpr int kStageBytes = 4 * 4 * 4096;  // 4 warps x 4 chunks of 32 x 32 floats
+constexpr int kStages = 4;                 // operand ring: one K block per stage
+constexpr int kStageOps = 2 * kBoxBytes;   // A and B boxes of one K block: 32 KiB
+constexpr int kEpiWarps = 8;                 // two per accumulator lane quadrant
+constexpr int kThreads = (2 + kEpiWarps) * 32;  // producer, MMA, epilogue warps
+constexpr uint32_t kTmemCols = 2 * kBN;    // two accumulators
+constexpr int kChunkBytes = 32 * 128;      // 32 rows x 32 FP32, one TMA store
+constexpr size_t kSmemBytes = (size_t)kStages * kStageOps + (size_t)kEpiWarps * 2 * kChunkBytes + 1024;
 constexpr long long kSpinLimit = 1ll << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -54,6 +60,10 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
@@ -153,108 +163,146 @@ struct CostArgs {
     int *err;         // set to 1 when a bounded wait gave up
 };
 
-__global__ void __launch_bounds__(kThreads) k_cost_umma(const __grid_constant__ CUtensorMap tA,
-                                                        const __grid_constant__ CUtensorMap tB,
-                                                        const __grid_constant__ CUtensorMap tC, CostArgs P) {
+__global__ void __launch_bounds__(kThreads, 1) k_cost_umma(const __grid_constant__ CUtensorMap tA,
+                                                           const __grid_constant__ CUtensorMap tB,
+                                                           const __grid_constant__ CUtensorMap tC, CostArgs P) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    unsigned char *sA = smem;
-    unsigned char *sB = smem + P.kb * kBoxBytes;
-    __shared__ uint64_t bar_tma, bar_mma;
+    unsigned char *ops = smem;                              // kStages x {A box, B box}
+    unsigned char *stg = smem + (size_t)kStages * kStageOps;  // epilogue warp e: 2 chunks
+    __shared__ uint64_t full[kStages], empty[kStages], tfull[2], tempty[2];
     __shared__ uint32_t tmem_base_sh;
-    __shared__ int ok_sh;
-    __shared__ __align__(16) float ny_s[kBN];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
+    const unsigned FULL = 0xffffffffu;
+    const int ntn = (P.n + kBN - 1) / kBN;
+    const int ntiles = ((P.m + kBM - 1) / kBM) * ntn;
 
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                          smem_u32(&tmem_base_sh)),
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
-    if (tid == 32) {
-        mbar_init(&bar_tma, 1);
-        mbar_init(&bar_mma, 1);
+    if (tid == 0) {
+        for (int q = 0; q < kStages; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], 1);
+        }
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&tfull[q], 1);
+            mbar_init(&tempty[q], kEpiWarps);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    }
-    {
-        const int j = n0 + tid;
-        ny_s[tid] = j < P.n ? P.ny[j] : 0.f;
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base_sh;
+    bool fail = false;
 
-    if (tid == 0) {
-        int ok = 1;
-        mbar_expect_tx(&bar_tma, (uint32_t)(2 * P.kb * kBoxBytes));
-        for (int kb = 0; kb < P.kb; ++kb) {
-            tma_load_2d(sA + kb * kBoxBytes, &tA, kb * kBK, m0, &bar_tma);
-            tma_load_2d(sB + kb * kBoxBytes, &tB, kb * kBK, n0, &bar_tma);
+    if (warp == 0) {
+        // ---- TMA producer: K blocks of this CTA's tiles into the ring
+        if (lane == 0) {
+            int kk = 0;
+            for (int t = blockIdx.x; t < ntiles && !fail; t += gridDim.x) {
+                const int m0 = (t / ntn) * kBM, n0 = (t % ntn) * kBN;
+                for (int kbi = 0; kbi < P.kb; ++kbi, ++kk) {
+                    const int q = kk % kStages;
+                    const uint32_t ph = (uint32_t)(kk / kStages) & 1u;
+                    if (!mbar_wait(&empty[q], ph ^ 1u)) { fail = true; break; }
+                    unsigned char *sA = ops + (size_t)q * kStageOps;
+                    mbar_expect_tx(&full[q], (uint32_t)kStageOps);
+                    tma_load_2d(sA, &tA, kbi * kBK, m0, &full[q]);
+                    tma_load_2d(sA + kBoxBytes, &tB, kbi * kBK, n0, &full[q]);
+                }
+            }
         }
-        if (!mbar_wait(&bar_tma, 0)) {
-            ok = 0;
-            atomicExch(P.err, 1);
-        } else {
-            tc_fence_after();
+    } else if (warp == 1) {
+        // ---- MMA issuer: one tile into accumulator lt % 2
+        if (lane == 0) {
             constexpr uint32_t idesc = umma_idesc_bf16(kBM, kBN);
-            const int ksteps = P.kb * (kBK / 16);
-            for (int s = 0; s < ksteps; ++s) {
-                const int box = s >> 2, koff = (s & 3) * 32;  // 16 BF16 = 32 bytes inside a swizzle row
-                const uint64_t da = umma_desc_sw128(sA + box * kBoxBytes + koff);
-                const uint64_t db = umma_desc_sw128(sB + box * kBoxBytes + koff);
-                umma_bf16(tmem, da, db, idesc, s > 0 ? 1u : 0u);
-            }
-            umma_commit(&bar_mma);
-            if (!mbar_wait(&bar_mma, 0)) {
-                ok = 0;
-                atomicExch(P.err, 1);
-            }
-        }
-        ok_sh = ok;
-    }
-    __syncthreads();
-    tc_fence_after();
-
-    if (ok_sh) {
-        // epilogue: warp w owns accumulator lanes (tile rows) 32w .. 32w+31
-        const int row = m0 + 32 * warp + lane;
-        const float nxi = row < P.m ? P.nx[row] : 0.f;
-        unsigned char *stage = smem + warp * (4 * 4096);
-#pragma unroll 1
-        for (int c = 0; c < kBN / 32; ++c) {
-            uint32_t r[32];
-            tmem_ld_32x32b_x32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * c), r);
-            float *chunk = reinterpret_cast<float *>(stage + c * 4096);
+            int kk = 0, lt = 0;
+            for (int t = blockIdx.x; t < ntiles && !fail; t += gridDim.x, ++lt) {
+                const int b = lt & 1;
+                if (!mbar_wait(&tempty[b], ((uint32_t)(lt >> 1) & 1u) ^ 1u)) { fail = true; break; }
+                tc_fence_after();
+                const uint32_t td = tmem + (uint32_t)(b * kBN);
+                for (int kbi = 0; kbi < P.kb; ++kbi, ++kk) {
+                    const int q = kk % kStages;
+                    if (!mbar_wait(&full[q], (uint32_t)(kk / kStages) & 1u)) { fail = true; break; }
+                    tc_fence_after();
+                    unsigned char *sA = ops + (size_t)q * kStageOps;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const float4 yn = *reinterpret_cast<const float4 *>(ny_s + 32 * c + 4 * u);
-                float4 v;
-                v.x = fmaf(-2.f, __uint_as_float(r[4 * u + 0]), nxi + yn.x);
-                v.y = fmaf(-2.f, __uint_as_float(r[4 * u + 1]), nxi + yn.y);
-                v.z = fmaf(-2.f, __uint_as_float(r[4 * u + 2]), nxi + yn.z);
-                v.w = fmaf(-2.f, __uint_as_float(r[4 * u + 3]), nxi + yn.w);
-                // 128-byte swizzle: 16-byte unit u of row `lane` sits at unit u ^ (lane % 8)
-                *reinterpret_cast<float4 *>(chunk + lane * 32 + 4 * (u ^ (lane & 7))) = v;
-            }
-            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            __syncwarp();
-            if (lane == 0) {
-                tma_store_2d(&tC, n0 + 32 * c, m0 + 32 * warp, chunk);
-                asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+                    for (int s16 = 0; s16 < kBK / 16; ++s16)  // 16 BF16 = 32 bytes inside a swizzle row
+                        umma_bf16(td, umma_desc_sw128(sA + 32 * s16), umma_desc_sw128(sA + kBoxBytes + 32 * s16),
+                                  idesc, (kbi > 0 || s16 > 0) ? 1u : 0u);
+                    umma_commit(&empty[q]);  // the stage is free once these MMAs have read it
+                }
+                if (fail) break;
+                umma_commit(&tfull[b]);  // the accumulator is complete
             }
         }
-        // the staging buffer may be released once the stores have read it;
-        // their global writes complete with the grid
+    } else {
+        // ---- epilogue: warp w reads accumulator lanes 32 (w % 4) .. + 31,
+        // column chunks 2h, 2h + 1 with h = (w - 2) / 4
+        const int qd = warp & 3, h = (warp - 2) >> 2;
+        unsigned char *mystg = stg + (size_t)(warp - 2) * 2 * kChunkBytes;
+        int cb = 0, lt = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
+            const int b = lt & 1;
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait(&tfull[b], (uint32_t)(lt >> 1) & 1u) ? 1 : 0;
+            ok = __shfl_sync(FULL, ok, 0);
+            if (!ok) { fail = true; break; }
+            tc_fence_after();
+            const int m0 = (t / ntn) * kBM, n0 = (t % ntn) * kBN;
+            const int row = m0 + 32 * qd + lane;
+            const float nxi = row < P.m ? __ldg(P.nx + row) : 0.f;
+#pragma unroll 1
+            for (int c = 2 * h; c < 2 * h + 2; ++c) {
+                uint32_t r[32];
+                tmem_ld_32x32b_x32(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(b * kBN + 32 * c), r);
+                if (c == 2 * h + 1) {  // this warp is done with the accumulator
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tempty[b]);
+                }
+                // this staging buffer's previous store must have been read
+                if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
+                __syncwarp();
+                float *chunk = reinterpret_cast<float *>(mystg + cb * kChunkBytes);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int j = n0 + 32 * c + 4 * u;  // n is a multiple of 4
+                    const float4 yn = j < P.n ? __ldg(reinterpret_cast<const float4 *>(P.ny + j))
+                                              : make_float4(0.f, 0.f, 0.f, 0.f);
+                    float4 v;
+                    v.x = fmaf(-2.f, __uint_as_float(r[4 * u + 0]), nxi + yn.x);
+                    v.y = fmaf(-2.f, __uint_as_float(r[4 * u + 1]), nxi + yn.y);
+                    v.z = fmaf(-2.f, __uint_as_float(r[4 * u + 2]), nxi + yn.z);
+                    v.w = fmaf(-2.f, __uint_as_float(r[4 * u + 3]), nxi + yn.w);
+                    // 128-byte swizzle: 16-byte unit u of row `lane` sits at unit u ^ (lane % 8)
+                    *reinterpret_cast<float4 *>(chunk + lane * 32 + 4 * (u ^ (lane & 7))) = v;
+                }
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    tma_store_2d(&tC, n0 + 32 * c, m0 + 32 * qd, chunk);
+                    asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+                }
+                cb ^= 1;
+            }
+        }
+        // the staging buffers may be released once the stores have read
+        // them; their global writes complete with the grid
         if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
     }
+    if (fail) atomicExch(P.err, 1);
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
     }
@@ -340,19 +388,23 @@ const char *launch_cost_bf16(int m, int n, int d, const float *X, const float *Y
         !encode_2d(&tC, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, C, n, m, (uint64_t)n * 4, 32, 32))
         return "tensor-map encoding failed";
     const int kb = d / kBK;
-    const size_t smem = (size_t)std::max(2 * kb * kBoxBytes, kStageBytes) + 1024;
-    static size_t attr = 0;  // largest dynamic size requested so far
-    if (smem > attr) {
-        if (cudaFuncSetAttribute(k_cost_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    static int sms = 0;  // persistent grid: one CTA per SM
+    static bool attr_set = false;
+    if (!attr_set) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
+        if (cudaFuncSetAttribute(k_cost_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) !=
             cudaSuccess) {
             cudaGetLastError();
             return "shared-memory attribute rejected";
         }
-        attr = smem;
+        attr_set = true;
     }
     CostArgs P{m, n, kb, nx, ny, err_dev};
-    dim3 grid((n + kBN - 1) / kBN, (m + kBM - 1) / kBM);
-    k_cost_umma<<<grid, kThreads, smem, st>>>(tA, tB, tC, P);
+    const long long tiles = (long long)((m + kBM - 1) / kBM) * ((n + kBN - 1) / kBN);
+    const int grid = (int)std::min<long long>(tiles, sms);
+    k_cost_umma<<<grid, kThreads, kSmemBytes, st>>>(tA, tB, tC, P);
     return nullptr;
 }
 
