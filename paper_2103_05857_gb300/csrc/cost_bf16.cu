@@ -19,7 +19,7 @@
 // two per 32-lane quadrant of the accumulator, each taking half of the
 // tile's columns: it reads its 32 lanes (tcgen05.ld 32x32b) in chunks of 32
 // columns, hands the accumulator back, adds the norms, writes the chunk into
-// one of two 128-byte-swizzled staging buffers and stores it with a TMA
+// one of three 128-byte-swizzled staging buffers and stores it with a TMA
 // tensor store. So the next tile's loads and MMAs run under this tile's
 // stores, and the store of C (the bound) streams without gaps.
 //
@@ -51,7 +51,9 @@ constexpr int kEpiWarps = 8;                 // two per accumulator lane quadran
 constexpr int kThreads = (2 + kEpiWarps) * 32;  // producer, MMA, epilogue warps
 constexpr uint32_t kTmemCols = 2 * kBN;    // two accumulators
 constexpr int kChunkBytes = 32 * 128;      // 32 rows x 32 FP32, one TMA store
-constexpr size_t kSmemBytes = (size_t)kStages * kStageOps + (size_t)kEpiWarps * 2 * kChunkBytes + 1024;
+constexpr int kStgChunks = 3;              // staging buffers per epilogue warp
+constexpr size_t kSmemBytes =
+    (size_t)kStages * kStageOps + (size_t)kEpiWarps * kStgChunks * kChunkBytes + 1024;
 constexpr long long kSpinLimit = 1ll << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -248,7 +250,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cost_umma(const __grid_constant
         // ---- epilogue: warp w reads accumulator lanes 32 (w % 4) .. + 31,
         // column chunks 2h, 2h + 1 with h = (w - 2) / 4
         const int qd = warp & 3, h = (warp - 2) >> 2;
-        unsigned char *mystg = stg + (size_t)(warp - 2) * 2 * kChunkBytes;
+        unsigned char *mystg = stg + (size_t)(warp - 2) * kStgChunks * kChunkBytes;
         int cb = 0, lt = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
             const int b = lt & 1;
@@ -270,7 +272,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cost_umma(const __grid_constant
                     if (lane == 0) mbar_arrive(&tempty[b]);
                 }
                 // this staging buffer's previous store must have been read
-                if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
+                if (lane == 0) asm volatile("cp.async.bulk.wait_group.read %0;\n" ::"n"(kStgChunks - 1) : "memory");
                 __syncwarp();
                 float *chunk = reinterpret_cast<float *>(mystg + cb * kChunkBytes);
 #pragma unroll
@@ -292,7 +294,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cost_umma(const __grid_constant
                     tma_store_2d(&tC, n0 + 32 * c, m0 + 32 * qd, chunk);
                     asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
                 }
-                cb ^= 1;
+                cb = cb + 1 == kStgChunks ? 0 : cb + 1;
             }
         }
         // the staging buffers may be released once the stores have read
@@ -312,7 +314,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cost_umma(const __grid_constant
 // rows in one launch; one warp per row.
 __global__ void k_round_bf16(int m, int n, int d, const float *__restrict__ X, __nv_bfloat16 *__restrict__ Xb,
                              float *__restrict__ nx, const float *__restrict__ Y, __nv_bfloat16 *__restrict__ Yb,
-                             float *__restrict__ ny) {
+                             float *__restrict__ ny, bool vec) {
     const int lane = threadIdx.x & 31;
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -322,7 +324,22 @@ __global__ void k_round_bf16(int m, int n, int d, const float *__restrict__ X, _
         const float *src = isx ? X : Y;
         __nv_bfloat16 *dst = isx ? Xb : Yb;
         float s = 0.f;
-        for (int k = lane; k < d; k += kWarp) {
+        // d is a multiple of 64; with 16-byte aligned points every row starts
+        // on a 16-byte boundary: four consecutive elements per lane
+        for (int k = 4 * lane; vec && k < d; k += 4 * kWarp) {
+            const float4 x = __ldg(reinterpret_cast<const float4 *>(src + (size_t)i * d + k));
+            const __nv_bfloat162 lo = __floats2bfloat162_rn(x.x, x.y), hi = __floats2bfloat162_rn(x.z, x.w);
+            uint2 pk;
+            pk.x = *reinterpret_cast<const uint32_t *>(&lo);
+            pk.y = *reinterpret_cast<const uint32_t *>(&hi);
+            *reinterpret_cast<uint2 *>(dst + (size_t)i * d + k) = pk;
+            const float2 flo = __bfloat1622float2(lo), fhi = __bfloat1622float2(hi);
+            s = fmaf(flo.x, flo.x, s);
+            s = fmaf(flo.y, flo.y, s);
+            s = fmaf(fhi.x, fhi.x, s);
+            s = fmaf(fhi.y, fhi.y, s);
+        }
+        for (int k = lane; !vec && k < d; k += kWarp) {
             const __nv_bfloat16 v = __float2bfloat16_rn(src[(size_t)i * d + k]);
             dst[(size_t)i * d + k] = v;
             const float f = __bfloat162float(v);
@@ -380,7 +397,8 @@ const char *launch_cost_bf16(int m, int n, int d, const float *X, const float *Y
     p += r((size_t)m * 4);
     float *ny = reinterpret_cast<float *>(p);
 
-    k_round_bf16<<<std::min((m + n + 7) / 8, 152 * 8), 256, 0, st>>>(m, n, d, X, Xb, nx, Y, Yb, ny);
+    const bool vec = reinterpret_cast<uintptr_t>(X) % 16 == 0 && reinterpret_cast<uintptr_t>(Y) % 16 == 0;
+    k_round_bf16<<<std::min((m + n + 7) / 8, 152 * 8), 256, 0, st>>>(m, n, d, X, Xb, nx, Y, Yb, ny, vec);
 
     CUtensorMap tA, tB, tC;
     if (!encode_2d(&tA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, Xb, d, m, (uint64_t)d * 2, kBK, kBM) ||
