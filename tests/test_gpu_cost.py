@@ -66,6 +66,23 @@ def test_cost_bf16_matches_oracle(S, h, oracle_mod, m, n, d):
     assert torch.equal(C, C2)
 
 
+def test_cost_bf16_unaligned_points(S, h, oracle_mod):
+    """Points that start 4 bytes past a 16-byte boundary take the scalar
+    rounding path; the cost stays within the same bound of the oracle."""
+    m, n, d = 200, 136, 128
+    inst = W.feature_instance(7, m, n, d)
+    C = torch.empty((m, n), dtype=torch.float32, device="cuda")
+    bx = torch.zeros(m * d + 1, dtype=torch.float32, device="cuda")
+    by = torch.zeros(n * d + 1, dtype=torch.float32, device="cuda")
+    bx[1:] = dev(inst.X, torch.float32).reshape(-1)
+    by[1:] = dev(inst.Y, torch.float32).reshape(-1)
+    Xd, Yd = bx[1:], by[1:]
+    assert Xd.data_ptr() % 16 == 4 and Yd.data_ptr() % 16 == 4
+    st = S.lib.sr_ot_cost_bf16(h._h, m, n, d, S._ptr(Xd), S._ptr(Yd), S._ptr(C))
+    assert st == S.OK, h.last_error()
+    _check(oracle_mod, inst.X, inst.Y, host(C))
+
+
 def test_cost_bf16_full_size_sampled(S, h, oracle_mod):
     """8192 x 8192, d = 128 (the feature-space workload): 48 sampled rows
     against the oracle over all 8192 columns."""
