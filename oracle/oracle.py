@@ -190,3 +190,28 @@ def adjoint(X, Y, b, rho, T):
     _load().srot_or_adjoint(m, n, d, _dp(X), _dp(Y), _dp(b), float(rho), _dp(T), _dp(dX),
                             _dp(dY), _dp(db))
     return dX, dY, db
+
+
+def barycentric(Y, T):
+    """Colour-transfer projection (Sec. 5.1): the new centroid of source row i
+    is the T-weighted mean of the target points, x_hat_i = sum_j T_ij y_j /
+    sum_j T_ij (the minimiser of sum_j T_ij ||x - y_j||^2). A row that carries
+    no mass has no projection; it is returned as zeros."""
+    Y, T = _f64(Y), _f64(T)
+    mass = T.sum(axis=1)
+    out = np.zeros((T.shape[0], Y.shape[1]))
+    for i in range(T.shape[0]):
+        if mass[i] > 0.0:
+            out[i] = (T[i] @ Y) / mass[i]
+    return out
+
+
+def transfer_stats(a, b, T):
+    """Evaluation metrics of Sec. 5: the marginal constraint error
+    e_c = ||T 1 - a||_2 + ||T^T 1 - b||_2 (metric iii) with its two terms, and
+    the sparsity, the fraction of entries of T that are zero (metric iv)."""
+    a, b, T = _f64(a), _f64(b), _f64(T)
+    row_err = float(np.linalg.norm(T.sum(axis=1) - a))
+    col_err = float(np.linalg.norm(T.sum(axis=0) - b))
+    sparsity = float(np.count_nonzero(T == 0.0)) / T.size
+    return {"e_c": row_err + col_err, "row_err": row_err, "col_err": col_err, "sparsity": sparsity}

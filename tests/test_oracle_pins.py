@@ -528,3 +528,50 @@ def test_gap_adaptive_sampling_support(oracle_mod):
     drawn = set(ti.tolist())
     assert not drawn & set(range(0, 12, 3))
     assert drawn == {i for i in range(12) if i % 3}
+
+
+# ----------------------------------------------------------------------------
+# Colour-transfer tail (Sec. 5.1 projection, Sec. 5 metrics iii and iv)
+# ----------------------------------------------------------------------------
+def test_barycentric_is_the_weighted_least_squares_point(oracle_mod):
+    """The projection minimises sum_j T_ij ||x - y_j||^2: its gradient vanishes
+    there and every perturbation raises the objective."""
+    rng = np.random.default_rng(5)
+    m, n, d = 6, 9, 3
+    Y = rng.random((n, d))
+    T = rng.random((m, n)) * (rng.random((m, n)) < 0.6)
+    T[0] = 0.0  # a row with no mass
+    T[1] = 0.0
+    T[1, 4] = 0.37  # all its mass on one column
+    Xh = oracle_mod.barycentric(Y, T)
+    assert np.all(Xh[0] == 0.0)
+    np.testing.assert_allclose(Xh[1], Y[4], rtol=0, atol=1e-15)
+
+    def obj(i, x):
+        return float(sum(T[i, j] * np.sum((x - Y[j]) ** 2) for j in range(n)))
+    for i in range(2, m):
+        grad = sum(2.0 * T[i, j] * (Xh[i] - Y[j]) for j in range(n))
+        assert np.abs(grad).max() <= 1e-12
+        for _ in range(20):
+            dx = rng.normal(size=d) * 1e-3
+            assert obj(i, Xh[i] + dx) > obj(i, Xh[i])
+
+
+def test_transfer_stats_special_plans(oracle_mod):
+    """e_c vanishes for a plan that meets both marginals (the product plan a
+    b^T); for the initial plan of Thm 1 (all mass in column 0) only the column
+    term remains and equals ||e_0 - b||; sparsity counts zero cells."""
+    rng = np.random.default_rng(6)
+    m, n = 7, 5
+    a = rng.random(m); a /= a.sum()
+    b = rng.random(n); b /= b.sum()
+    s = oracle_mod.transfer_stats(a, b, np.outer(a, b))
+    assert s["e_c"] <= 1e-15 and s["sparsity"] == 0.0
+    T0 = np.zeros((m, n)); T0[:, 0] = a
+    s0 = oracle_mod.transfer_stats(a, b, T0)
+    e0 = np.zeros(n); e0[0] = 1.0
+    assert s0["row_err"] <= 1e-15
+    assert abs(s0["col_err"] - np.sqrt(((e0 - b) ** 2).sum())) <= 1e-15
+    assert abs(s0["e_c"] - s0["col_err"]) <= 1e-15
+    zeros = sum(1 for i in range(m) for j in range(n) if T0[i, j] == 0.0)
+    assert s0["sparsity"] == zeros / (m * n) == (n - 1) / n
