@@ -221,6 +221,33 @@ sr_ot_status sr_ot_grad_batched(sr_ot_handle h, const sr_ot_options *opts, int b
                                 const long long *off_T, const void *X, const void *Y,
                                 const void *b, const void *T, void *dX, void *dY, void *db);
 
+/* Colour-transfer tail (Sec. 5.1) and the evaluation metrics (iii), (iv) of
+   Sec. 5, from one pass over a plan T (the pass of sr_ot_grad):
+     Xhat_i   = sum_j T_ij y_j / sum_j T_ij      (the barycentric projection of
+                source row i, the minimiser of sum_j T_ij ||x - y_j||^2; rows
+                that carry no mass get zeros),
+     row_err  = ||T 1 - a||_2,  col_err = ||T^T 1 - b||_2,
+     e_c      = row_err + col_err,
+     sparsity = the fraction of entries of T equal to zero.
+   Device pointers, row-major, element type FP64 when opts->precision is
+   SR_OT_FP64 and FP32 otherwise: Y (n x d, may be NULL when Xhat is NULL),
+   a (m), b (n), T (m x n), Xhat (m x d, caller-owned, may be NULL). stats: a
+   host struct filled when the call returns (may be NULL; a and b may then be
+   NULL). Sums are taken in a fixed order (the result does not depend on
+   scheduling). Errors: EINVAL for NULL T, non-positive sizes, Xhat without
+   Y, stats without a or b; EUNSUPPORTED for d outside 1..31 when Xhat is
+   requested. */
+typedef struct {
+    double e_c;       /* ||T 1 - a||_2 + ||T^T 1 - b||_2                         */
+    double row_err;   /* ||T 1 - a||_2                                            */
+    double col_err;   /* ||T^T 1 - b||_2                                          */
+    double sparsity;  /* zero entries of T / (m n)                                */
+} sr_ot_transfer_stats;
+
+sr_ot_status sr_ot_transfer(sr_ot_handle h, const sr_ot_options *opts, int m, int n, int d,
+                            const void *Y, const void *a, const void *b, const void *T,
+                            void *Xhat, sr_ot_transfer_stats *stats);
+
 /*
  * Certificate of any feasible plan T (Thm 2): objective f, linearisation
  * duality gap g = sum_i g_i (eq. 11) and Lagrangian dual w = f - g.

@@ -22,6 +22,11 @@
 // The 8 warps' column partials are summed in a fixed order at the end. A
 // small finishing kernel reduces the per-band and per-tile partials in FP64
 // in a fixed order, so the result does not depend on scheduling.
+//
+// The same pass gives the colour-transfer tail (Sec. 5.1 and the metrics
+// (iii), (iv) of Sec. 5): the row partials sum_j T_ij (y_j, 1) are the
+// numerator and denominator of the barycentric projection, the row and
+// column sums the marginal errors, and the tiles count the zero entries.
 #include <algorithm>
 #include <type_traits>
 
@@ -103,6 +108,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_tiles(AdjArgs<Real> A) {
     const bool vec = V16 && (I.n % CPT == 0) && ((reinterpret_cast<uintptr_t>(Tm) & 15) == 0) &&
                      (!dCm || (reinterpret_cast<uintptr_t>(dCm) & 15) == 0);
     const Real *Xm = A.X ? A.X + I.oX : nullptr;
+    unsigned nzero = 0;  // zero entries of T seen by this thread (transfer statistics)
 
     // column partials: sum over the 8 warps in a fixed order, QC components at a time
     auto column_partials = [&](Real (&cacc)[CPT][P]) {
@@ -173,6 +179,15 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_tiles(AdjArgs<Real> A) {
 #pragma unroll
                     for (int c = 0; c < 4; ++c)
                         if (j0 + c < I.n) dCm[off + c] = e[c];
+                }
+            }
+            if (A.zeros) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if (r0 + r >= i1) break;
+                    const float e[4] = {tv[r].x, tv[r].y, tv[r].z, tv[r].w};
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) nzero += (j0 + c < I.n && e[c] == 0.f) ? 1u : 0u;
                 }
             }
             float v[32];
@@ -248,6 +263,14 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_tiles(AdjArgs<Real> A) {
                         if (j0 + c < I.n) dCm[off + c] = tv[r][c];
                 }
             }
+            if (A.zeros) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if (r0 + r >= i1) break;
+#pragma unroll
+                    for (int c = 0; c < CPT; ++c) nzero += (j0 + c < I.n && tv[r][c] == Real(0)) ? 1u : 0u;
+                }
+            }
             Real v[32];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
@@ -271,6 +294,10 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_tiles(AdjArgs<Real> A) {
         }
 
         column_partials(cacc);
+    }
+    if (A.zeros) {
+        const unsigned wz = __reduce_add_sync(0xffffffffu, nzero);
+        if (lane == 0 && wz) atomicAdd(A.zeros + k, (unsigned long long)wz);
     }
 }
 
@@ -306,10 +333,27 @@ __device__ inline void sum_partials(const Real *p, size_t stride, int count, dou
     }
 }
 
-// Finishing pass: each instance owns ceil(m / 256) row blocks (dX from the
-// row partials, summed over column tiles in ascending order) followed by
-// ceil(n / 256) column blocks (dY, db from the column partials, summed over
-// row bands in ascending order); a block never spans two instances.
+// Deterministic block sum (fixed butterfly per warp, warps in order); the
+// result is valid in thread 0. Every thread of the block must call it.
+__device__ inline double block_sum_fixed(double v) {
+    __shared__ double sh[kFinThreads / kWarp];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kFinThreads / kWarp; ++w) t += sh[w];
+    return t;
+}
+
+// Finishing pass: each instance owns ceil(m / 256) row blocks (dX and the
+// barycentric projection from the row partials, summed over column tiles in
+// ascending order) followed by ceil(n / 256) column blocks (dY, db from the
+// column partials, summed over row bands in ascending order); a block never
+// spans two instances. With tpart, each block also leaves the sum of its
+// squared marginal errors (rows: (T1 - a)_i^2, columns: (T^T 1 - b)_j^2).
 template <typename Real, int P>
 __global__ void __launch_bounds__(kFinThreads) k_adj_finish(AdjArgs<Real> A) {
     __shared__ int sk;
@@ -322,44 +366,85 @@ __global__ void __launch_bounds__(kFinThreads) k_adj_finish(AdjArgs<Real> A) {
     double acc[P];
 #pragma unroll
     for (int c = 0; c < P; ++c) acc[c] = 0.0;
+    double sq = 0.0;  // squared marginal error of this thread's row or column
     if (lb < rblocks) {
         const int i = lb * kFinThreads + (int)threadIdx.x;
-        if (i >= I.m || !A.dX) return;
-        sum_partials<Real, P>(A.rowpart + I.orp + (size_t)i * P, (size_t)I.m * P, I.ncol, acc);
-        double rs = 0.0;
-#pragma unroll
-        for (int c = 0; c < P; ++c)
-            if (c == d) rs = acc[c];
-#pragma unroll
-        for (int c = 0; c < P; ++c)
-            if (c < d) {
-                const double xv = (double)A.X[I.oX + (size_t)i * d + c];
-                A.dX[I.oX + (size_t)i * d + c] = (Real)(2.0 * (rs * xv - acc[c]));
-            }
-    } else {
-        const int j = (lb - rblocks) * kFinThreads + (int)threadIdx.x;
-        if (j >= I.n || !(A.dY || A.db)) return;
-        sum_partials<Real, P>(A.colpart + I.ocp + (size_t)j * P, (size_t)I.n * P, I.nbands, acc);
-        double s = 0.0;
-#pragma unroll
-        for (int c = 0; c < P; ++c)
-            if (c == d) s = acc[c];
-        if (A.dY) {
+        if (i < I.m && (A.dX || A.xhat || A.tpart)) {
+            sum_partials<Real, P>(A.rowpart + I.orp + (size_t)i * P, (size_t)I.m * P, I.ncol, acc);
+            double rs = 0.0;
 #pragma unroll
             for (int c = 0; c < P; ++c)
-                if (c < d) {
-                    const double yv = (double)A.Y[I.oY + (size_t)j * d + c];
-                    A.dY[I.oY + (size_t)j * d + c] = (Real)(2.0 * (s * yv - acc[c]));
-                }
+                if (c == d) rs = acc[c];
+            if (A.dX) {
+#pragma unroll
+                for (int c = 0; c < P; ++c)
+                    if (c < d) {
+                        const double xv = (double)A.X[I.oX + (size_t)i * d + c];
+                        A.dX[I.oX + (size_t)i * d + c] = (Real)(2.0 * (rs * xv - acc[c]));
+                    }
+            }
+            if (A.xhat) {
+#pragma unroll
+                for (int c = 0; c < P; ++c)
+                    if (c < d) A.xhat[I.oX + (size_t)i * d + c] = rs > 0.0 ? (Real)(acc[c] / rs) : Real(0);
+            }
+            if (A.tpart) {
+                const double e = rs - (double)A.a[I.oa + i];
+                sq = e * e;
+            }
         }
-        if (A.db) A.db[I.ob + j] = (Real)(-A.rho * (s - (double)A.b[I.ob + j]));
+    } else {
+        const int j = (lb - rblocks) * kFinThreads + (int)threadIdx.x;
+        if (j < I.n && (A.dY || A.db || A.tpart)) {
+            sum_partials<Real, P>(A.colpart + I.ocp + (size_t)j * P, (size_t)I.n * P, I.nbands, acc);
+            double s = 0.0;
+#pragma unroll
+            for (int c = 0; c < P; ++c)
+                if (c == d) s = acc[c];
+            if (A.dY) {
+#pragma unroll
+                for (int c = 0; c < P; ++c)
+                    if (c < d) {
+                        const double yv = (double)A.Y[I.oY + (size_t)j * d + c];
+                        A.dY[I.oY + (size_t)j * d + c] = (Real)(2.0 * (s * yv - acc[c]));
+                    }
+            }
+            if (A.db) A.db[I.ob + j] = (Real)(-A.rho * (s - (double)A.b[I.ob + j]));
+            if (A.tpart) {
+                const double e = s - (double)A.b[I.ob + j];
+                sq = e * e;
+            }
+        }
+    }
+    if (A.tpart) {
+        const double t = block_sum_fixed(sq);
+        if (threadIdx.x == 0) A.tpart[blockIdx.x] = t;
+    }
+}
+
+// Transfer statistics per instance from the finishing blocks' sums (in
+// ascending block order) and the zero count.
+template <typename Real>
+__global__ void k_transfer_stats(AdjArgs<Real> A) {
+    for (int k = threadIdx.x; k < A.ninst; k += blockDim.x) {
+        const AdjInst I = A.inst[k];
+        const int rblocks = (I.m + kFinThreads - 1) / kFinThreads, cblocks = (I.n + kFinThreads - 1) / kFinThreads;
+        double r2 = 0.0, c2 = 0.0;
+        for (int q = 0; q < rblocks; ++q) r2 += A.tpart[I.fin0 + q];
+        for (int q = 0; q < cblocks; ++q) c2 += A.tpart[I.fin0 + rblocks + q];
+        const double re = sqrt(r2), ce = sqrt(c2);
+        A.tstats[4 * k + 0] = re;
+        A.tstats[4 * k + 1] = ce;
+        A.tstats[4 * k + 2] = re + ce;
+        A.tstats[4 * k + 3] = (double)A.zeros[k] / ((double)I.m * (double)I.n);
     }
 }
 
 template <typename Real, int P>
 void launch_p(const AdjArgs<Real> &A, cudaStream_t st) {
     k_adj_tiles<Real, P><<<A.total_tiles, kAdjThreads, 0, st>>>(A);
-    if (A.dX || A.dY || A.db) k_adj_finish<Real, P><<<A.total_fin, kFinThreads, 0, st>>>(A);
+    if (A.dX || A.dY || A.db || A.xhat || A.tpart) k_adj_finish<Real, P><<<A.total_fin, kFinThreads, 0, st>>>(A);
+    if (A.tpart && A.tstats && A.zeros) k_transfer_stats<Real><<<1, 128, 0, st>>>(A);
 }
 
 }  // namespace

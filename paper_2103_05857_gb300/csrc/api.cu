@@ -24,7 +24,7 @@ namespace {
 enum WsSlot {
     WS_Q = 0, WS_PARTIAL, WS_R64, WS_RQ32, WS_COLPART, WS_ROWPART, WS_CERT, WS_PERM, WS_PERMKEY,
     WS_PERMIDX, WS_GSTORE, WS_STATUS, WS_COST, WS_CHECK, WS_SCRATCH, WS_ATOMS, WS_B_INST,
-    WS_B_QUEUE, WS_B_HEAD, WS_B_RES, WS_B_ATOMS, WS_B_BAD, WS_ADJ_INST, WS_ADJ_CP, WS_ADJ_RP, WS_FW_JS, WS_FW_UPART, WS_BF16, WS_BF16_ERR, WS_COUNT
+    WS_B_QUEUE, WS_B_HEAD, WS_B_RES, WS_B_ATOMS, WS_B_BAD, WS_ADJ_INST, WS_ADJ_CP, WS_ADJ_RP, WS_TR_PART, WS_TR_ZERO, WS_TR_STATS, WS_FW_JS, WS_FW_UPART, WS_BF16, WS_BF16_ERR, WS_COUNT
 };
 
 struct DevBuf {
@@ -657,21 +657,24 @@ __global__ void k_batch_check(const BatchInst *inst, int batch, const float *X, 
 // Envelope-theorem gradients (adjoint pass) for one or many instances.
 // ---------------------------------------------------------------------------
 template <typename Real>
-sr_ot_status grad_impl(sr_ot_handle h, const sr_ot_options *o, int ninst, const int *m, const int *n,
-                       int d, const long long *oX, const long long *oY, const long long *ob,
-                       const long long *oT, const void *X, const void *Y, const void *b, const void *T,
-                       void *dC, void *dX, void *dY, void *db) {
+sr_ot_status adjoint_impl(sr_ot_handle h, const sr_ot_options *o, int ninst, const int *m, const int *n,
+                          int d, const long long *oX, const long long *oY, const long long *ob,
+                          const long long *oT, const long long *oa, const void *X, const void *Y,
+                          const void *a, const void *b, const void *T, void *dC, void *dX, void *dY, void *db,
+                          void *xhat, double *stats) {
     if (!o) return fail(h, SR_OT_EINVAL, "opts is NULL");
     if (!std::isfinite(o->rho) || o->rho < 0.0) return fail(h, SR_OT_EINVAL, "rho must be finite and >= 0");
     if (!T) return fail(h, SR_OT_EINVAL, "T must be non-NULL");
     if ((dX || dY) && (!X || !Y)) return fail(h, SR_OT_EINVAL, "dX and dY need the points X and Y");
     if (db && !b) return fail(h, SR_OT_EINVAL, "db needs b");
-    if ((dX || dY) && (d < 1 || d > 31)) return fail(h, SR_OT_EUNSUPPORTED, "gradients take 1 <= d <= 31 (got %d)", d);
-    if (!(dX || dY) && (d < 1 || d > 31)) d = 3;  // d unused: no point gradients requested
-    if (!dC && !dX && !dY && !db) return SR_OT_OK;
+    if (xhat && !Y) return fail(h, SR_OT_EINVAL, "the barycentric projection needs the points Y");
+    if (stats && (!a || !b)) return fail(h, SR_OT_EINVAL, "the transfer statistics need a and b");
+    if ((dX || dY || xhat) && (d < 1 || d > 31)) return fail(h, SR_OT_EUNSUPPORTED, "point outputs take 1 <= d <= 31 (got %d)", d);
+    if (!(dX || dY || xhat) && (d < 1 || d > 31)) d = 3;  // d unused: no point outputs requested
+    if (!dC && !dX && !dY && !db && !xhat && !stats) return SR_OT_OK;
     for (int k = 0; k < ninst; ++k) {
         if (m[k] <= 0 || n[k] <= 0) return fail(h, SR_OT_EINVAL, "instance %d: m and n must be >= 1", k);
-        if (oX[k] < 0 || oY[k] < 0 || ob[k] < 0 || oT[k] < 0) return fail(h, SR_OT_EINVAL, "instance %d: negative offset", k);
+        if (oX[k] < 0 || oY[k] < 0 || ob[k] < 0 || oT[k] < 0 || oa[k] < 0) return fail(h, SR_OT_EINVAL, "instance %d: negative offset", k);
     }
     std::vector<AdjInst> inst(ninst);
     const AdjTotals tot = adj_plan(ninst, m, n, d, (int)sizeof(Real), inst.data());
@@ -681,6 +684,7 @@ sr_ot_status grad_impl(sr_ot_handle h, const sr_ot_options *o, int ninst, const 
         inst[k].oY = oY[k];
         inst[k].ob = ob[k];
         inst[k].oT = oT[k];
+        inst[k].oa = oa[k];
     }
     sr_ot_status st;
     AdjInst *d_inst;
@@ -689,6 +693,14 @@ sr_ot_status grad_impl(sr_ot_handle h, const sr_ot_options *o, int ninst, const 
     if ((st = ws_typed(h, WS_ADJ_CP, (size_t)tot.colpart, &cp))) return st;
     if ((st = ws_typed(h, WS_ADJ_RP, (size_t)tot.rowpart, &rp))) return st;
     CK(h, cudaMemcpyAsync(d_inst, inst.data(), sizeof(AdjInst) * ninst, cudaMemcpyHostToDevice, h->stream));
+    double *tpart = nullptr, *tstats = nullptr;
+    unsigned long long *zeros = nullptr;
+    if (stats) {
+        if ((st = ws_typed(h, WS_TR_PART, (size_t)tot.fin_blocks, &tpart))) return st;
+        if ((st = ws_typed(h, WS_TR_ZERO, (size_t)ninst, &zeros))) return st;
+        if ((st = ws_typed(h, WS_TR_STATS, (size_t)4 * ninst, &tstats))) return st;
+        CK(h, cudaMemsetAsync(zeros, 0, sizeof(unsigned long long) * ninst, h->stream));
+    }
     AdjArgs<Real> A;
     A.inst = d_inst;
     A.ninst = ninst;
@@ -704,6 +716,11 @@ sr_ot_status grad_impl(sr_ot_handle h, const sr_ot_options *o, int ninst, const 
     A.db = static_cast<Real *>(db);
     A.colpart = cp;
     A.rowpart = rp;
+    A.xhat = static_cast<Real *>(xhat);
+    A.a = static_cast<const Real *>(a);
+    A.tpart = tpart;
+    A.zeros = zeros;
+    A.tstats = tstats;
     A.total_tiles = (int)tot.tiles;
     A.total_cols = tot.cols;
     A.total_rows = tot.rows;
@@ -712,10 +729,21 @@ sr_ot_status grad_impl(sr_ot_handle h, const sr_ot_options *o, int ninst, const 
         ProfScope ps(h, SR_OT_PROF_GRAD);
         if (!launch_adjoint<Real>(A, h->stream)) return fail(h, SR_OT_EUNSUPPORTED, "d = %d out of range", d);
     }
-    h->launches += 1 + ((dY || db) ? 1 : 0) + (dX ? 1 : 0);
+    h->launches += 1 + ((dX || dY || db || xhat || stats) ? 1 : 0) + (stats ? 1 : 0);
     CKL(h);
+    if (stats) CK(h, cudaMemcpyAsync(stats, tstats, sizeof(double) * 4 * ninst, cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     return SR_OT_OK;
+}
+
+template <typename Real>
+sr_ot_status grad_impl(sr_ot_handle h, const sr_ot_options *o, int ninst, const int *m, const int *n,
+                       int d, const long long *oX, const long long *oY, const long long *ob,
+                       const long long *oT, const void *X, const void *Y, const void *b, const void *T,
+                       void *dC, void *dX, void *dY, void *db) {
+    std::vector<long long> oa(ninst > 0 ? ninst : 1, 0);
+    return adjoint_impl<Real>(h, o, ninst, m, n, d, oX, oY, ob, oT, oa.data(), X, Y, nullptr, b, T, dC, dX, dY,
+                              db, nullptr, nullptr);
 }
 
 sr_ot_status ensure_side_streams(sr_ot_handle h) {
@@ -1091,6 +1119,32 @@ sr_ot_status sr_ot_solve_batched(sr_ot_handle h, const sr_ot_options *opts, int 
                               static_cast<const float *>(X), static_cast<const float *>(Y),
                               static_cast<const float *>(a), static_cast<const float *>(b),
                               static_cast<float *>(T), res);
+}
+
+sr_ot_status sr_ot_transfer(sr_ot_handle h, const sr_ot_options *opts, int m, int n, int d, const void *Y,
+                            const void *a, const void *b, const void *T, void *Xhat, sr_ot_transfer_stats *stats) {
+    if (!h) return fail(nullptr, SR_OT_EINVAL, "handle is NULL");
+    h->err.clear();
+    sr_ot_status st;
+    if (!opts) return fail(h, SR_OT_EINVAL, "opts is NULL");
+    if ((st = check_sizes(h, m, n))) return st;
+    if ((st = check_stream_device(h))) return st;
+    const long long z = 0;
+    double out[4] = {0.0, 0.0, 0.0, 0.0};
+    double *so = stats ? out : nullptr;
+    if (opts->precision == SR_OT_FP64)
+        st = adjoint_impl<double>(h, opts, 1, &m, &n, d, &z, &z, &z, &z, &z, nullptr, Y, a, b, T, nullptr, nullptr,
+                                  nullptr, nullptr, Xhat, so);
+    else
+        st = adjoint_impl<float>(h, opts, 1, &m, &n, d, &z, &z, &z, &z, &z, nullptr, Y, a, b, T, nullptr, nullptr,
+                                 nullptr, nullptr, Xhat, so);
+    if (st == SR_OT_OK && stats) {
+        stats->row_err = out[0];
+        stats->col_err = out[1];
+        stats->e_c = out[2];
+        stats->sparsity = out[3];
+    }
+    return st;
 }
 
 sr_ot_status sr_ot_grad(sr_ot_handle h, const sr_ot_options *opts, int m, int n, int d,

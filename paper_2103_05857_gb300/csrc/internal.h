@@ -169,7 +169,7 @@ void set_handleless_error(const char *msg);
 // use the offsets of X, Y and b.
 struct AdjInst {
     int m, n;
-    long long oX, oY, ob, oT;
+    long long oX, oY, ob, oT, oa;
     int nbands, rh, ncol;  // row bands of rh rows; column tiles of 256 x (16 / element size)
     int tile0;             // first tile (CTA) of this instance
     long long col0, row0;  // prefix sums of n and m over the instances
@@ -189,6 +189,15 @@ struct AdjArgs {
     const Real *X, *Y, *b, *T;
     Real *dC, *dX, *dY, *db;  // any may be null (dC only for one instance)
     Real *colpart, *rowpart;  // workspace from adj_plan's totals
+    // colour-transfer tail (any may be null): barycentric projection (m x d,
+    // offsets of X), row weights a (offsets oa), per-finishing-block squared
+    // marginal errors (total_fin doubles), zero entries of T per instance,
+    // and per instance {||T1 - a||, ||T^T 1 - b||, e_c, sparsity}
+    Real *xhat;
+    const Real *a;
+    double *tpart;
+    unsigned long long *zeros;
+    double *tstats;
     int total_tiles;
     long long total_cols, total_rows;
     int total_fin;  // blocks of the finishing pass
@@ -199,7 +208,8 @@ int adj_width(int d);
 // Tiles and workspace of a set of instances (elem_bytes: 4 or 8); fills
 // out[k] except the offsets oX, oY, ob, oT.
 AdjTotals adj_plan(int ninst, const int *m, const int *n, int d, int elem_bytes, AdjInst *out);
-// Launch the tile pass and the finishing pass; false if d is out of range.
+// Launch the tile pass and the finishing pass (and, with tstats, the
+// transfer statistics); false if d is out of range.
 template <typename Real>
 bool launch_adjoint(const AdjArgs<Real> &A, cudaStream_t st);
 

@@ -24,7 +24,7 @@ EPOCH_AUTO, EPOCH_TWO_PHASE, EPOCH_PIPELINED, EPOCH_SPECULATIVE = 0, 1, 2, 3
 
 EXPORTS = ["sr_ot_default_options", "sr_ot_create", "sr_ot_set_stream", "sr_ot_destroy",
            "sr_ot_last_error", "sr_ot_solve", "sr_ot_solve_batched", "sr_ot_grad",
-           "sr_ot_grad_batched", "sr_ot_gap", "sr_ot_cost_bf16", "sr_ot_launch_count",
+           "sr_ot_grad_batched", "sr_ot_transfer", "sr_ot_gap", "sr_ot_cost_bf16", "sr_ot_launch_count",
            "sr_ot_profile_enable", "sr_ot_profile_read", "sr_ot_gap_noalloc"]
 PROF_EPOCH, PROF_CERT, PROF_BATCH, PROF_GRAD, PROF_COST = 0, 1, 2, 3, 4
 
@@ -37,6 +37,11 @@ class Options(ct.Structure):
         ("ga_global_only", ct.c_int), ("seed", ct.c_ulonglong), ("trace", ct.c_void_p),
         ("trace_capacity", ct.c_longlong), ("dense_only", ct.c_int), ("epoch_kernel", ct.c_int),
     ]
+
+
+class TransferStats(ct.Structure):
+    _fields_ = [("e_c", ct.c_double), ("row_err", ct.c_double), ("col_err", ct.c_double),
+                ("sparsity", ct.c_double)]
 
 
 class Result(ct.Structure):
@@ -76,6 +81,8 @@ def _load():
     lib.sr_ot_solve_batched.argtypes = [vp, ct.POINTER(Options), i, ip, ip, i, llp, llp, llp, llp,
                                         llp, vp, vp, vp, vp, vp, ct.POINTER(Result)]
     lib.sr_ot_grad.argtypes = [vp, ct.POINTER(Options), i, i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.sr_ot_transfer.argtypes = [vp, ct.POINTER(Options), i, i, i, vp, vp, vp, vp, vp,
+                                   ct.POINTER(TransferStats)]
     lib.sr_ot_grad_batched.argtypes = [vp, ct.POINTER(Options), i, ip, ip, i, llp, llp, llp, llp,
                                        vp, vp, vp, vp, vp, vp, vp]
     lib.sr_ot_gap.argtypes = [vp, ct.POINTER(Options), i, i, i, vp, vp, vp, vp, vp, vp, vp,
@@ -235,6 +242,21 @@ class Handle:
                             _ptr(out.get("db")))
         self._check(st, allow=(OK,))
         return out
+
+    def transfer(self, T, Y=None, a=None, b=None, projection=True, stats=True, opts=None, **kw):
+        """sr_ot_transfer: barycentric projection Xhat (m x d, a new tensor of
+        T's dtype, or None) and the statistics dict {e_c, row_err, col_err,
+        sparsity} (or None)."""
+        o = opts if opts is not None else options(**kw)
+        m, n = T.shape
+        d = 3 if Y is None else Y.shape[1]
+        Xh = torch.empty((m, d), dtype=T.dtype, device=T.device) if projection else None
+        ts = TransferStats()
+        st = lib.sr_ot_transfer(self._h, ct.byref(o), m, n, d, _ptr(Y), _ptr(a), _ptr(b), _ptr(T), _ptr(Xh),
+                                ct.byref(ts) if stats else None)
+        self._check(st, allow=(OK,))
+        out = {f: getattr(ts, f) for f, _ in TransferStats._fields_} if stats else None
+        return Xh, out
 
     def grad_batched(self, X, Y, b, T, sizes, offsets, want=("dX", "dY", "db"), d=3, opts=None, **kw):
         """sr_ot_grad_batched over packed buffers (offsets as in solve_batched:
