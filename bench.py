@@ -562,7 +562,22 @@ def bench_batch(args, s, ws, rank, local):
     if g_n:
         tbytes = 4.0 * pb.total_T + 4.0 * sum(3 * (i.m + i.n) * 2 + i.n * 2 for i in insts)
         line["roofline_adjoint"] = hbm_roofline(tbytes, g_ms / g_n, peaks, peak_src,
-                                                "k_adj_tiles + k_adj_cols + k_adj_rows", {"launches": g_n})
+                                                "k_adj_tiles + k_adj_finish", {"launches": g_n})
+    if backward:
+        # colour-transfer tail over the same plans (barycentric projection,
+        # e_c, sparsity; Sec. 5.1 and 5): device time of the library's own
+        # launches, outside the timed solve
+        h.profile(True)
+        for _ in range(4):
+            _, tstats = h.transfer_batched(pb.Y, pb.a, pb.b, pb.T, pb.sizes, pb.offsets, precision=S.FP32,
+                                           xhat_numel=pb.X.numel())
+        t_ms, t_n = h.profile_read(S.PROF_GRAD)
+        h.profile(False)
+        tb = 4.0 * pb.total_T + 4.0 * sum(3 * i.n + i.n + i.m + 3 * i.m for i in insts)
+        line["roofline_transfer"] = hbm_roofline(
+            tb, t_ms / max(t_n, 1), peaks, peak_src, "k_adj_tiles + k_adj_finish + k_transfer_stats",
+            {"launches": t_n, "e_c_max": max(t["e_c"] for t in tstats),
+             "sparsity_mean": float(np.mean([t["sparsity"] for t in tstats]))})
     h.close()
     return line, allinst
 
@@ -573,7 +588,7 @@ def bench_ours(args, ws, rank, local):
         line, insts = bench_batch(args, s, ws, rank, local)
     else:
         line, insts = bench_single(args, s, ws, rank, local)
-    for key in ("roofline", "roofline_cost", "roofline_adjoint"):
+    for key in ("roofline", "roofline_cost", "roofline_adjoint", "roofline_transfer"):
         if key in line:
             line[key]["traffic"] = captured_traffic(args.workload, key)
     if rank == 0:

@@ -248,6 +248,17 @@ sr_ot_status sr_ot_transfer(sr_ot_handle h, const sr_ot_options *opts, int m, in
                             const void *Y, const void *a, const void *b, const void *T,
                             void *Xhat, sr_ot_transfer_stats *stats);
 
+/* Batched form of sr_ot_transfer over packed instances (element offsets as in
+   sr_ot_solve_batched; Xhat is laid out like X: instance k's projection
+   starts at off_X[k]), one pass for all. stats: host array of `batch`
+   structs, or NULL. */
+sr_ot_status sr_ot_transfer_batched(sr_ot_handle h, const sr_ot_options *opts, int batch,
+                                    const int *m, const int *n, int d, const long long *off_X,
+                                    const long long *off_Y, const long long *off_a,
+                                    const long long *off_b, const long long *off_T, const void *Y,
+                                    const void *a, const void *b, const void *T, void *Xhat,
+                                    sr_ot_transfer_stats *stats);
+
 /*
  * Certificate of any feasible plan T (Thm 2): objective f, linearisation
  * duality gap g = sum_i g_i (eq. 11) and Lagrangian dual w = f - g.

@@ -1182,6 +1182,37 @@ sr_ot_status sr_ot_grad_batched(sr_ot_handle h, const sr_ot_options *opts, int b
                             dY, db);
 }
 
+sr_ot_status sr_ot_transfer_batched(sr_ot_handle h, const sr_ot_options *opts, int batch, const int *m,
+                                    const int *n, int d, const long long *off_X, const long long *off_Y,
+                                    const long long *off_a, const long long *off_b, const long long *off_T,
+                                    const void *Y, const void *a, const void *b, const void *T, void *Xhat,
+                                    sr_ot_transfer_stats *stats) {
+    if (!h) return fail(nullptr, SR_OT_EINVAL, "handle is NULL");
+    h->err.clear();
+    sr_ot_status st;
+    if (!opts) return fail(h, SR_OT_EINVAL, "opts is NULL");
+    if (batch <= 0) return fail(h, SR_OT_EINVAL, "batch must be >= 1");
+    if (!m || !n || !off_X || !off_Y || !off_a || !off_b || !off_T)
+        return fail(h, SR_OT_EINVAL, "size and offset arrays must be non-NULL");
+    if ((st = check_stream_device(h))) return st;
+    std::vector<double> out(stats ? 4 * (size_t)batch : 0);
+    double *so = stats ? out.data() : nullptr;
+    if (opts->precision == SR_OT_FP64)
+        st = adjoint_impl<double>(h, opts, batch, m, n, d, off_X, off_Y, off_b, off_T, off_a, nullptr, Y, a, b, T,
+                                  nullptr, nullptr, nullptr, nullptr, Xhat, so);
+    else
+        st = adjoint_impl<float>(h, opts, batch, m, n, d, off_X, off_Y, off_b, off_T, off_a, nullptr, Y, a, b, T,
+                                 nullptr, nullptr, nullptr, nullptr, Xhat, so);
+    if (st == SR_OT_OK && stats)
+        for (int k = 0; k < batch; ++k) {
+            stats[k].row_err = out[4 * k];
+            stats[k].col_err = out[4 * k + 1];
+            stats[k].e_c = out[4 * k + 2];
+            stats[k].sparsity = out[4 * k + 3];
+        }
+    return st;
+}
+
 long long sr_ot_launch_count(sr_ot_handle h) { return h ? h->launches : 0; }
 
 sr_ot_status sr_ot_profile_enable(sr_ot_handle h, int enable) {

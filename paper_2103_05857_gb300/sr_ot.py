@@ -24,7 +24,7 @@ EPOCH_AUTO, EPOCH_TWO_PHASE, EPOCH_PIPELINED, EPOCH_SPECULATIVE = 0, 1, 2, 3
 
 EXPORTS = ["sr_ot_default_options", "sr_ot_create", "sr_ot_set_stream", "sr_ot_destroy",
            "sr_ot_last_error", "sr_ot_solve", "sr_ot_solve_batched", "sr_ot_grad",
-           "sr_ot_grad_batched", "sr_ot_transfer", "sr_ot_gap", "sr_ot_cost_bf16", "sr_ot_launch_count",
+           "sr_ot_grad_batched", "sr_ot_transfer", "sr_ot_transfer_batched", "sr_ot_gap", "sr_ot_cost_bf16", "sr_ot_launch_count",
            "sr_ot_profile_enable", "sr_ot_profile_read", "sr_ot_gap_noalloc"]
 PROF_EPOCH, PROF_CERT, PROF_BATCH, PROF_GRAD, PROF_COST = 0, 1, 2, 3, 4
 
@@ -83,6 +83,8 @@ def _load():
     lib.sr_ot_grad.argtypes = [vp, ct.POINTER(Options), i, i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.sr_ot_transfer.argtypes = [vp, ct.POINTER(Options), i, i, i, vp, vp, vp, vp, vp,
                                    ct.POINTER(TransferStats)]
+    lib.sr_ot_transfer_batched.argtypes = [vp, ct.POINTER(Options), i, ip, ip, i, llp, llp, llp, llp, llp,
+                                           vp, vp, vp, vp, vp, ct.POINTER(TransferStats)]
     lib.sr_ot_grad_batched.argtypes = [vp, ct.POINTER(Options), i, ip, ip, i, llp, llp, llp, llp,
                                        vp, vp, vp, vp, vp, vp, vp]
     lib.sr_ot_gap.argtypes = [vp, ct.POINTER(Options), i, i, i, vp, vp, vp, vp, vp, vp, vp,
@@ -256,6 +258,30 @@ class Handle:
                                 ct.byref(ts) if stats else None)
         self._check(st, allow=(OK,))
         out = {f: getattr(ts, f) for f, _ in TransferStats._fields_} if stats else None
+        return Xh, out
+
+    def transfer_batched(self, Y, a, b, T, sizes, offsets, d=3, projection=True, stats=True, xhat_numel=None,
+                         opts=None, **kw):
+        """sr_ot_transfer_batched over packed buffers (offsets as in
+        solve_batched). Returns (packed Xhat laid out like X, or None; list of
+        statistics dicts, or None)."""
+        o = opts if opts is not None else options(**kw)
+        B = len(sizes)
+        mm = (ct.c_int * B)(*[int(s[0]) for s in sizes])
+        nn = (ct.c_int * B)(*[int(s[1]) for s in sizes])
+        cols = list(zip(*offsets))
+        arrs = [(ct.c_longlong * B)(*[int(v) for v in c]) for c in cols]
+        Xh = None
+        if projection:
+            numel = xhat_numel if xhat_numel is not None else max(int(v[0]) + int(s[0]) * d
+                                                                  for v, s in zip(offsets, sizes))
+            Xh = torch.zeros(numel, dtype=T.dtype, device=T.device)
+        ts = (TransferStats * B)()
+        st = lib.sr_ot_transfer_batched(self._h, ct.byref(o), B, mm, nn, d, arrs[0], arrs[1], arrs[2], arrs[3],
+                                        arrs[4], _ptr(Y), _ptr(a), _ptr(b), _ptr(T), _ptr(Xh),
+                                        ts if stats else None)
+        self._check(st, allow=(OK,))
+        out = [{f: getattr(t, f) for f, _ in TransferStats._fields_} for t in ts] if stats else None
         return Xh, out
 
     def grad_batched(self, X, Y, b, T, sizes, offsets, want=("dX", "dY", "db"), d=3, opts=None, **kw):

@@ -136,3 +136,31 @@ def test_transfer_full_size_sampled(S, h, oracle_mod):
     for k in ("row_err", "col_err", "e_c"):
         assert abs(st[k] - rs[k]) <= 2e-6 * (np.linalg.norm(a) + np.linalg.norm(b)), k
     assert st["sparsity"] == rs["sparsity"]
+
+
+def test_transfer_batched_matches_per_instance(S, h, oracle_mod):
+    """One packed pass over uneven instances gives each instance's projection
+    and statistics (compared with the oracle instance by instance)."""
+    from paper_2103_05857_gb300.batch import PackedBatch
+    insts = [W.colour_instance(90 + k, m, n, rho=10.0, b_dirichlet=True).rounded()
+             for k, (m, n) in enumerate([(130, 70), (1, 5), (600, 257), (64, 1100)])]
+    pb = PackedBatch(insts)
+    plans = []
+    for k, inst in enumerate(insts):
+        a, b, T, _ = _plan(60 + k, inst.m, inst.n, support=3)
+        T = np.asarray(T * (inst.a / a)[:, None], dtype=np.float32).astype(np.float64)  # rows sum to inst.a
+        pb.plan(k).copy_(dev(T, torch.float32))
+        plans.append(T)
+    Xh, stats = h.transfer_batched(pb.Y, pb.a, pb.b, pb.T, pb.sizes, pb.offsets, precision=S.FP32,
+                                   xhat_numel=pb.X.numel())
+    Xh = host(Xh)
+    for k, inst in enumerate(insts):
+        ox = pb.offsets[k][0]
+        got = Xh[ox:ox + inst.m * 3].reshape(inst.m, 3)
+        ref = oracle_mod.barycentric(inst.Y, plans[k])
+        assert np.abs(got - ref).max() <= 2e-6 * np.abs(ref).max(), k
+        rs = oracle_mod.transfer_stats(inst.a, inst.b, plans[k])
+        tol = 2e-6 * (np.linalg.norm(inst.a) + np.linalg.norm(inst.b))
+        for key in ("row_err", "col_err", "e_c"):
+            assert abs(stats[k][key] - rs[key]) <= tol, (k, key)
+        assert stats[k]["sparsity"] == rs["sparsity"], k
