@@ -54,9 +54,9 @@ CAPTURED_TRAFFIC = {
         "bytes": 4398848, "files": ("solve_spec.cu", "atoms.cuh", "step.cuh", "cpasync.cuh", "common.cuh"),
         "digest": "b92b9df6ebe2dd2d"},
     ("feature8192_d128", "roofline_cost"): {
-        "bytes": 4284672 + 203198208, "files": ("cost_bf16.cu", "common.cuh"), "digest": "37d37fe188a2335d"},
+        "bytes": 4290048 + 207054592, "files": ("cost_bf16.cu", "common.cuh"), "digest": "37d37fe188a2335d"},
     ("colour_batch64_2048", "roofline_adjoint"): {
-        "bytes": 1077008384 + 37366272, "files": ("adjoint.cu", "common.cuh"), "digest": "d8ea0ea53dff60cb"},
+        "bytes": 1077040896 + 37680640, "files": ("adjoint.cu", "common.cuh"), "digest": "270fe6a595a572c2"},
 }
 
 
