@@ -365,6 +365,46 @@ def test_active_set_overflow_falls_back_to_dense(S, h, oracle_mod):
                   "BCPFW", "ELS", "CYCLIC", 2, T0=f32(T1))
 
 
+@pytest.mark.parametrize("order", ["CYCLIC", "PERMUTE"])
+def test_pairwise_overflow_mid_epoch_all_kernels(S, h, oracle_mod, order):
+    """Row 5 starts with 63 atoms (the record's limit) on its most expensive
+    columns, so its pairwise step must append a 64th: every active-set kernel
+    stops at that update and the dense kernel finishes the epoch. The trace and
+    the plan agree bit for bit across the three kernels, and the epochs replay
+    the oracle."""
+    m, n = 48, 300
+    inst = W.colour_instance(321, m, n, rho=10.0).rounded()
+    C = oracle_mod.cost(inst.X, inst.Y)
+    T0 = np.zeros((m, n))
+    T0[:, 0] = inst.a
+    cols = np.argsort(C[5])[-63:]
+    T0[5] = 0.0
+    T0[5, cols] = inst.a[5] / 63
+    T0 = f32(T0)
+    ep = 3
+    out = []
+    for ek in (S.EPOCH_TWO_PHASE, S.EPOCH_PIPELINED, S.EPOCH_SPECULATIVE):
+        cap = ep * m
+        tr = torch.full((4 * cap,), -1, dtype=torch.int32, device="cuda")
+        T = dev(T0, torch.float32).contiguous()
+        res = h.solve(dev(inst.a, torch.float32), dev(inst.b, torch.float32), T, X=dev(inst.X, torch.float32),
+                      Y=dev(inst.Y, torch.float32), precision=S.FP32, variant=S.BCPFW, step=S.ELS,
+                      order=getattr(S, order), seed=5, rho=inst.rho, max_epochs=ep, warm_start=True,
+                      trace=tr, trace_capacity=cap, epoch_kernel=ek)
+        assert res["status"] in (S.OK, S.NOT_CONVERGED), res
+        out.append((tr.cpu().numpy(), T.cpu().numpy()))
+    for k in (1, 2):
+        np.testing.assert_array_equal(out[0][0], out[k][0])
+        np.testing.assert_array_equal(out[0][1], out[k][1])
+    tr0 = out[0][0].reshape(-1, 4)
+    first5 = tr0[np.nonzero(tr0[:, 0] == 5)[0][0]]
+    assert first5[1] not in set(cols.tolist())  # its LMO vertex is a 64th atom: the overflow happens
+    if order == "CYCLIC":
+        replay_epochs(S, h, oracle_mod, inst, C,
+                      dict(X=dev(inst.X, torch.float32), Y=dev(inst.Y, torch.float32)),
+                      "BCPFW", "ELS", "CYCLIC", 2, T0=T0)
+
+
 @pytest.mark.parametrize("variant,step", [("BCFW", "DEC"), ("BCPFW", "ELS"), ("BCAFW", "ELS")])
 def test_fp32_full_size_colour4096(S, h, oracle_mod, variant, step):
     """colour4096_fp32 (m = n = 4096, Dirichlet b) in the launch configuration
