@@ -75,6 +75,12 @@ typedef enum { SR_OT_DEC = 0, SR_OT_ELS = 1 } sr_ot_step;
  * accumulation and FP32 norms (points mode, d a multiple of 64). */
 typedef enum { SR_OT_FP64 = 0, SR_OT_FP32 = 1, SR_OT_FP32_BF16COST = 2 } sr_ot_precision;
 
+/* Cost built from points (sr_ot_options.cost_kind). */
+typedef enum {
+    SR_OT_COST_SQUARED = 0,   /* C_ij = ||x_i - y_j||^2                             */
+    SR_OT_COST_EUCLIDEAN = 1  /* C_ij = ||x_i - y_j||_2 (the paper's, Sec. 5.1)     */
+} sr_ot_cost_kind;
+
 /* Active-set epoch kernels for FP32 pairwise solves (sr_ot_options.epoch_kernel). */
 typedef enum {
     SR_OT_EPOCH_AUTO = 0,
@@ -114,6 +120,14 @@ typedef struct {
                                  order, n <= 4096), PIPELINED (n <= 8192),
                                  TWO_PHASE. A kernel that does not apply falls
                                  back the same way.                            */
+    int cost_kind;            /* cost from points X, Y: SR_OT_COST_SQUARED
+                                 (default) or SR_OT_COST_EUCLIDEAN, the paper's
+                                 ||x_i - y_j||_2 (Sec. 5.1), built once into the
+                                 handle's workspace (m x n) and solved as a
+                                 given cost. Ignored when C is given.
+                                 sr_ot_solve_batched, the point gradients dX,
+                                 dY of sr_ot_grad and the BF16 cost take the
+                                 squared cost only (EUNSUPPORTED otherwise).   */
 } sr_ot_options;
 
 typedef struct {

@@ -244,6 +244,8 @@ sr_ot_status check_opts(sr_ot_handle h, const sr_ot_options *o) {
     if (o->trace && o->trace_capacity < 0) return fail(h, SR_OT_EINVAL, "trace_capacity must be >= 0");
     if (o->epoch_kernel < SR_OT_EPOCH_AUTO || o->epoch_kernel > SR_OT_EPOCH_SPECULATIVE)
         return fail(h, SR_OT_EINVAL, "unknown epoch_kernel %d", o->epoch_kernel);
+    if (o->cost_kind != SR_OT_COST_SQUARED && o->cost_kind != SR_OT_COST_EUCLIDEAN)
+        return fail(h, SR_OT_EINVAL, "unknown cost_kind %d", o->cost_kind);
     return SR_OT_OK;
 }
 
@@ -313,7 +315,9 @@ sr_ot_status make_inst(sr_ot_handle h, const sr_ot_options *o, int m, int n, int
     if (d <= 0) return fail(h, SR_OT_EINVAL, "d must be >= 1 in points mode (got %d)", d);
     const Real *Xr = static_cast<const Real *>(X), *Yr = static_cast<const Real *>(Y);
     if ((st = check_inputs<Real>(h, m, n, in->a, in->b, Xr, (long long)m * d, Yr, (long long)n * d))) return st;
+    const bool euclid = o->cost_kind == SR_OT_COST_EUCLIDEAN;
     if (o->precision == SR_OT_FP32_BF16COST) {
+        if (euclid) return fail(h, SR_OT_EUNSUPPORTED, "the BF16 cost is the squared one");
         if constexpr (std::is_same<Real, float>::value) {
             Real *Cw;
             if ((st = ws_typed(h, WS_COST, (size_t)m * n, &Cw))) return st;
@@ -326,7 +330,7 @@ sr_ot_status make_inst(sr_ot_handle h, const sr_ot_options *o, int m, int n, int
             return fail(h, SR_OT_EINVAL, "BF16 cost needs the FP32 element type");
         }
     }
-    if (d == 3) {
+    if (d == 3 && !euclid) {
         in->cost_mode = kCostPts3;
         in->X = Xr;
         in->Y = Yr;
@@ -336,7 +340,7 @@ sr_ot_status make_inst(sr_ot_handle h, const sr_ot_options *o, int m, int n, int
     if ((st = ws_typed(h, WS_COST, (size_t)m * n, &Cw))) return st;
     {
         ProfScope ps(h, SR_OT_PROF_COST);
-        launch_cost_plain<Real>(m, n, d, Xr, Yr, Cw, h->stream);
+        launch_cost_plain<Real>(m, n, d, Xr, Yr, Cw, h->stream, euclid);
     }
     h->launches += 1;
     CKL(h);
@@ -669,6 +673,8 @@ sr_ot_status adjoint_impl(sr_ot_handle h, const sr_ot_options *o, int ninst, con
     if (db && !b) return fail(h, SR_OT_EINVAL, "db needs b");
     if (xhat && !Y) return fail(h, SR_OT_EINVAL, "the barycentric projection needs the points Y");
     if (stats && (!a || !b)) return fail(h, SR_OT_EINVAL, "the transfer statistics need a and b");
+    if ((dX || dY) && o->cost_kind != SR_OT_COST_SQUARED)
+        return fail(h, SR_OT_EUNSUPPORTED, "the point gradients dX, dY are those of the squared cost");
     if ((dX || dY || xhat) && (d < 1 || d > 31)) return fail(h, SR_OT_EUNSUPPORTED, "point outputs take 1 <= d <= 31 (got %d)", d);
     if (!(dX || dY || xhat) && (d < 1 || d > 31)) d = 3;  // d unused: no point outputs requested
     if (!dC && !dX && !dY && !db && !xhat && !stats) return SR_OT_OK;
@@ -767,6 +773,7 @@ sr_ot_status solve_batched_impl(sr_ot_handle h, const sr_ot_options *o, int batc
     if (!X || !Y || !a || !b || !T) return fail(h, SR_OT_EINVAL, "X, Y, a, b, T must be non-NULL");
     if (d != 3) return fail(h, SR_OT_EUNSUPPORTED, "batched solves take points with d = 3 (got %d)", d);
     if (o->precision != SR_OT_FP32) return fail(h, SR_OT_EUNSUPPORTED, "batched solves run in SR_OT_FP32");
+    if (o->cost_kind != SR_OT_COST_SQUARED) return fail(h, SR_OT_EUNSUPPORTED, "batched solves take the squared cost");
     if (o->variant == SR_OT_FW) return fail(h, SR_OT_EUNSUPPORTED, "batched solves run the block-coordinate variants");
     if (o->order == SR_OT_GAP_ADAPTIVE) return fail(h, SR_OT_EUNSUPPORTED, "batched solves take cyclic, permuted or uniform order");
     sr_ot_status st;

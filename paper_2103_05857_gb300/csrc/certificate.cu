@@ -468,7 +468,7 @@ void launch_make_perm(unsigned long long seed, long long epoch, int m, int *perm
 // ---------------------------------------------------------------------------
 template <typename Real>
 __global__ void k_cost_plain(int m, int n, int d, const Real *__restrict__ X,
-                             const Real *__restrict__ Y, Real *__restrict__ C) {
+                             const Real *__restrict__ Y, Real *__restrict__ C, bool euclid) {
     __shared__ Real xs[16][17], ys[16][17];
     int ti = threadIdx.y, tj = threadIdx.x;
     int i = blockIdx.y * 16 + ti, j = blockIdx.x * 16 + tj;
@@ -481,21 +481,29 @@ __global__ void k_cost_plain(int m, int n, int d, const Real *__restrict__ X,
         __syncthreads();
         int kmax = min(16, d - k0);
         for (int k = 0; k < kmax; ++k) {
-            Real dl = xs[ti][k] - ys[tj][k];
-            acc += dl * dl;
+            // ascending k, every operation rounded on its own (no contraction)
+            if constexpr (std::is_same<Real, double>::value) {
+                const double dl = dsub(xs[ti][k], ys[tj][k]);
+                acc = dadd(acc, dmul(dl, dl));
+            } else {
+                const float dl = __fsub_rn(xs[ti][k], ys[tj][k]);
+                acc = __fadd_rn(acc, __fmul_rn(dl, dl));
+            }
         }
         __syncthreads();
     }
-    if (i < m && j < n) C[(size_t)i * n + j] = acc;
+    if (i < m && j < n) C[(size_t)i * n + j] = euclid ? sqrt(acc) : acc;
 }
 
 template <typename Real>
-void launch_cost_plain(int m, int n, int d, const Real *X, const Real *Y, Real *C, cudaStream_t st) {
+void launch_cost_plain(int m, int n, int d, const Real *X, const Real *Y, Real *C, cudaStream_t st,
+                       bool euclid) {
     dim3 blk(16, 16), grd(ceil_div(n, 16), ceil_div(m, 16));
-    k_cost_plain<Real><<<grd, blk, 0, st>>>(m, n, d, X, Y, C);
+    k_cost_plain<Real><<<grd, blk, 0, st>>>(m, n, d, X, Y, C, euclid);
 }
 
-template void launch_cost_plain<float>(int, int, int, const float *, const float *, float *, cudaStream_t);
-template void launch_cost_plain<double>(int, int, int, const double *, const double *, double *, cudaStream_t);
+template void launch_cost_plain<float>(int, int, int, const float *, const float *, float *, cudaStream_t, bool);
+template void launch_cost_plain<double>(int, int, int, const double *, const double *, double *, cudaStream_t,
+                                        bool);
 
 }  // namespace srot

@@ -91,10 +91,11 @@ size_t cost_bf16_workspace(int m, int n, int d);
 const char *launch_cost_bf16(int m, int n, int d, const float *X, const float *Y, float *C, void *ws,
                              int *err_dev, cudaStream_t st);
 
-// Materialise C_ij = ||x_i - y_j||^2 for general d on the CUDA cores.
+// Materialise C_ij = ||x_i - y_j||^2 (euclid: ||x_i - y_j||_2) for any d on
+// the CUDA cores, summed over ascending k without contraction.
 template <typename Real>
 void launch_cost_plain(int m, int n, int d, const Real *X, const Real *Y, Real *C,
-                       cudaStream_t st);
+                       cudaStream_t st, bool euclid = false);
 
 // Single-instance epoch of block updates.
 template <typename Real>

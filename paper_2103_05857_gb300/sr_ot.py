@@ -21,6 +21,7 @@ CYCLIC, PERMUTE, UNIFORM, GAP_ADAPTIVE = 0, 1, 2, 3
 DEC, ELS = 0, 1
 FP64, FP32, FP32_BF16COST = 0, 1, 2
 EPOCH_AUTO, EPOCH_TWO_PHASE, EPOCH_PIPELINED, EPOCH_SPECULATIVE = 0, 1, 2, 3
+COST_SQUARED, COST_EUCLIDEAN = 0, 1
 
 EXPORTS = ["sr_ot_default_options", "sr_ot_create", "sr_ot_set_stream", "sr_ot_destroy",
            "sr_ot_last_error", "sr_ot_solve", "sr_ot_solve_batched", "sr_ot_grad",
@@ -35,7 +36,7 @@ class Options(ct.Structure):
         ("rho", ct.c_double), ("tol_rel_gap", ct.c_double), ("max_epochs", ct.c_longlong),
         ("gap_every", ct.c_int), ("refresh_every", ct.c_int), ("ga_M", ct.c_int),
         ("ga_global_only", ct.c_int), ("seed", ct.c_ulonglong), ("trace", ct.c_void_p),
-        ("trace_capacity", ct.c_longlong), ("dense_only", ct.c_int), ("epoch_kernel", ct.c_int),
+        ("trace_capacity", ct.c_longlong), ("dense_only", ct.c_int), ("epoch_kernel", ct.c_int), ("cost_kind", ct.c_int),
     ]
 
 

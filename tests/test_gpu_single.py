@@ -125,6 +125,76 @@ def test_fp64_dec_trajectory_bit_identical(S, h, oracle_mod, order, epochs):
     assert abs(res["gap"] - ro["g"]) <= 1e-12 * ro["f"]
 
 
+@pytest.mark.parametrize("d,order", [(3, "CYCLIC"), (5, "PERMUTE")])
+def test_fp64_euclidean_cost_trajectory_bit_identical(S, h, oracle_mod, d, order):
+    """The paper's cost ||x_i - y_j||_2 (Sec. 5.1) from points: the argmin
+    sequence and the plan of BCFW-DEC match the oracle run on the oracle's
+    Euclidean cost bit for bit (the cost is built with the oracle's summation
+    order and a correctly rounded square root)."""
+    m, n = 120, 250
+    rng = np.random.default_rng(d)
+    X, Y = rng.random((m, d)), rng.random((n, d))
+    a = W.dirichlet_weights(d, m)
+    b = W.dirichlet_weights(d + 1, n)
+    C = oracle_mod.cost(X, Y, squared=False)
+    seed, epochs = 8, 6
+    To, ro, ti, tj, _ = oracle_mod.solve(C, a, b, rho=5.0, variant=oracle_mod.BCFW, step=oracle_mod.DEC,
+                                         order=getattr(oracle_mod, order), seed=seed, max_epochs=epochs,
+                                         trace=True)
+    cap = epochs * m
+    tr = _trace_buf(cap)
+    T = torch.zeros((m, n), dtype=torch.float64, device="cuda")
+    res = h.solve(dev(a, torch.float64), dev(b, torch.float64), T, X=dev(X, torch.float64),
+                  Y=dev(Y, torch.float64), precision=S.FP64, variant=S.BCFW, step=S.DEC,
+                  order=getattr(S, order), seed=seed, rho=5.0, max_epochs=epochs, trace=tr,
+                  trace_capacity=cap, cost_kind=S.COST_EUCLIDEAN)
+    trh = tr.cpu().numpy().reshape(-1, 4)
+    np.testing.assert_array_equal(trh[:, 0], ti)
+    np.testing.assert_array_equal(trh[:, 1], tj)
+    np.testing.assert_array_equal(host(T), To)
+    assert rel(res["objective"], ro["f"]) <= 1e-13
+    # the certificate of the same plan under the Euclidean cost
+    g = h.gap(dev(a, torch.float64), dev(b, torch.float64), T, X=dev(X, torch.float64), Y=dev(Y, torch.float64),
+              precision=S.FP64, rho=5.0, cost_kind=S.COST_EUCLIDEAN)
+    cert = oracle_mod.certificate(C, a, b, 5.0, To)
+    assert rel(g["objective"], cert["f"]) <= 1e-13 and abs(g["gap"] - cert["g"]) <= 1e-12 * cert["f"]
+
+
+def test_fp32_euclidean_cost_converges_to_oracle_optimum(S, h, oracle_mod):
+    inst = W.colour_instance(41, 300, 400, rho=10.0, b_dirichlet=True).rounded()
+    C = oracle_mod.cost(inst.X, inst.Y, squared=False)
+    _, ro, *_ = oracle_mod.solve(C, inst.a, inst.b, rho=inst.rho, variant=oracle_mod.BCPFW, step=oracle_mod.ELS,
+                                 max_epochs=50000, tol_rel_gap=1e-10, gap_every=5)
+    T = torch.zeros((inst.m, inst.n), dtype=torch.float32, device="cuda")
+    res = h.solve(dev(inst.a, torch.float32), dev(inst.b, torch.float32), T, X=dev(inst.X, torch.float32),
+                  Y=dev(inst.Y, torch.float32), precision=S.FP32, variant=S.BCPFW, step=S.ELS, rho=inst.rho,
+                  max_epochs=20000, tol_rel_gap=1e-6, cost_kind=S.COST_EUCLIDEAN)
+    assert res["status"] == S.OK, res
+    assert ro["f"] - 1e-9 <= res["objective"] <= ro["f"] * (1 + 1.2e-6)
+
+
+def test_euclidean_cost_rejected_where_unsupported(S, h):
+    m, n = 8, 12
+    X = torch.rand((m, 3), device="cuda")
+    Y = torch.rand((n, 3), device="cuda")
+    a = torch.full((m,), 1.0 / m, device="cuda")
+    b = torch.full((n,), 1.0 / n, device="cuda")
+    T = torch.zeros((m, n), device="cuda")
+    o = S.options(precision=S.FP32, cost_kind=S.COST_EUCLIDEAN)
+    dX = torch.empty((m, 3), device="cuda")
+    assert S.lib.sr_ot_grad(h._h, o, m, n, 3, S._ptr(X), S._ptr(Y), None, S._ptr(b), S._ptr(T), None,
+                            S._ptr(dX), None, None) == S.EUNSUPPORTED
+    o2 = S.options(precision=S.FP32_BF16COST, cost_kind=S.COST_EUCLIDEAN)
+    X64 = torch.rand((m, 64), device="cuda")
+    Y64 = torch.rand((n, 64), device="cuda")
+    res = S.Result()
+    assert S.lib.sr_ot_solve(h._h, o2, m, n, 64, None, S._ptr(X64), S._ptr(Y64), S._ptr(a), S._ptr(b),
+                             S._ptr(T), 0, res) == S.EUNSUPPORTED
+    o3 = S.options(precision=S.FP32, cost_kind=7)
+    assert S.lib.sr_ot_solve(h._h, o3, m, n, 3, None, S._ptr(X), S._ptr(Y), S._ptr(a), S._ptr(b),
+                             S._ptr(T), 0, res) == S.EINVAL
+
+
 def test_fp64_given_cost_matches_point_cost(S, h, oracle_mod):
     inst = W.colour_instance(3, 150, 333, rho=25.0)
     C = oracle_mod.cost(inst.X, inst.Y)
