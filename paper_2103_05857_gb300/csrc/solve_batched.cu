@@ -61,7 +61,7 @@ size_t batched_smem() {
     b += 2 * ((NTC / kWarp) + 1) * sizeof(BRed);     // reduction slots
     b += 64 * sizeof(double) + 64;                   // certificate partials, flags
     b += (size_t)kRowMax * 16;                       // per-row a, 1/a, 1/(2 rho a)
-    b += 2 * (size_t)kAtomRecord * 16;               // two-slot atom-record ring
+    b += 4 * (size_t)kAtomRecord * 16;               // four-slot atom-record ring
     return b;
 }
 
@@ -84,7 +84,8 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_batched(BatchArgs B) {
     // per row {a_i, 1 / a_i, 1 / (2 rho a_i)}: the control warp reads them
     // from shared memory instead of loading and dividing on its chain
     float4 *arow = reinterpret_cast<float4 *>(sflag + 16);
-    // atom records of the current and next row, streamed by compute warp 0
+    // atom records of the current and the next two rows (slot = update % 4),
+    // streamed by compute warp 0
     int4 *aring = reinterpret_cast<int4 *>(arow + kRowMax);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -209,17 +210,24 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_batched(BatchArgs B) {
             // ---- m block updates ---------------------------------------------
             float cst[CPT];
             int i_next = row_of(0);
-            // atom records: row of update p in ring slot p & 1; compute warp 0
-            // streams the next row's record during update p (not when that
-            // record is being rewritten: the row of update p or p-1)
+            // atom records: row of update p in ring slot p & 3; compute warp 0
+            // streams the record of update p + 2 during update p, unless that
+            // row is updated before its use (the rows of updates p, p + 1)
+            int i_p1 = m > 1 ? row_of(1) : -1;
+            bool pre_cur = true;                    // the current row's record is in its slot
+            int i_prev = -1;                        // the row of update p - 1
+            bool pre_next = i_p1 >= 0 && i_p1 != i_next;  // the next one's
             if (warp == 0) {
                 cp16(aring + lane, grec + (size_t)i_next * kAtomRecord + lane);
                 cp16(aring + 32 + lane, grec + (size_t)i_next * kAtomRecord + 32 + lane);
                 commit();
-                wait_groups<0>();
+                if (pre_next) {
+                    cp16(aring + kAtomRecord + lane, grec + (size_t)i_p1 * kAtomRecord + lane);
+                    cp16(aring + kAtomRecord + 32 + lane, grec + (size_t)i_p1 * kAtomRecord + 32 + lane);
+                }
+                commit();
+                wait_groups<1>();  // row 0's record
             }
-            bool pre_cur = true;  // the current row's record is in its slot
-            int i_prev = -1;
             float xn0 = 0.f, xn1 = 0.f, xn2 = 0.f;
             xn0 = X[(size_t)i_next * 3];
             xn1 = X[(size_t)i_next * 3 + 1];
@@ -249,7 +257,7 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_batched(BatchArgs B) {
                 const long long k = k0 + p;
                 const int i = i_next;
                 const float x0 = xn0, x1 = xn1, x2 = xn2;
-                const int slot = p & 1;
+                const int slot = p & 3;
                 if (p + 1 < m) {
                     i_next = i_far;
                     xn0 = xf0;
@@ -266,12 +274,16 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_batched(BatchArgs B) {
                 DF t_vdf{0.f, 0.f};
                 float ai = 0.f, gmx = 0.f, inv = 0.f;
                 LaneAtoms at_cur;
-                // the next row's record travels unless it is being rewritten
-                const bool pre_next = p + 1 < m && i_next != i && i_next != i_prev;
-                if (warp == 0 && pre_next) {
-                    int4 *dst = aring + (size_t)(slot ^ 1) * kAtomRecord;
-                    cp16(dst + lane, grec + (size_t)i_next * kAtomRecord + lane);
-                    cp16(dst + 32 + lane, grec + (size_t)i_next * kAtomRecord + 32 + lane);
+                // the record of update p + 2 travels unless that row is
+                // rewritten just before the copy or before its use (updates
+                // p - 1, p, p + 1)
+                const bool pre_far = p + 2 < m && i_far != i && i_far != i_next && i_far != i_prev;
+                if (warp == 0) {
+                    if (pre_far) {
+                        int4 *dst = aring + (size_t)((p + 2) & 3) * kAtomRecord;
+                        cp16(dst + lane, grec + (size_t)i_far * kAtomRecord + lane);
+                        cp16(dst + 32 + lane, grec + (size_t)i_far * kAtomRecord + 32 + lane);
+                    }
                     commit();
                 }
                 if (!ctrl) {
@@ -366,14 +378,16 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_batched(BatchArgs B) {
                         cst[2 * hh + 1] = c.y;
                     }
                 }
-                if (warp == 0 && pre_next) wait_groups<0>();  // the next row's record
+                if (warp == 0) wait_groups<1>();  // the next row's record (p + 2's may be in flight)
                 par ^= 1;
                 __syncthreads();  // (B)
                 if (sflag[0]) break;
                 ++updates;
                 pre_cur = pre_next;
+                pre_next = pre_far;
                 i_prev = i;
             }
+            if (warp == 0) wait_groups<0>();  // a record copy may still be in flight after an early stop
             if (sflag[0]) { status = sflag[0]; break; }
 
             // ---- certificate (Thm 2) ------------------------------------------
