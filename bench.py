@@ -13,7 +13,8 @@ Other workloads (--workload):
   colour256_fp64       FP64 BCFW, decay rule, cyclic, 200 epochs
   colour_batch512      512 instances, m, n ~ U{64..2048}, one persistent launch
   feature8192_d128     BF16 tensor-core cost (d = 128) + FP32 solve to 1e-6
-  colour_batch64_2048  64 x (2048 x 2048): batched solve + adjoint (backward)
+  colour_batch64_2048  64 x (2048 x 2048): batched solve + adjoint (backward); the
+                       colour-transfer pass over the same plans is timed on its own
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
