@@ -126,8 +126,9 @@ typedef struct {
                                  handle's workspace (m x n) and solved as a
                                  given cost. Ignored when C is given.
                                  sr_ot_solve_batched, the point gradients dX,
-                                 dY of sr_ot_grad and the BF16 cost take the
-                                 squared cost only (EUNSUPPORTED otherwise).   */
+                                 dY of sr_ot_grad, the BF16 cost and the points
+                                 form of sr_ot_gap_noalloc take the squared
+                                 cost only (EUNSUPPORTED otherwise).           */
 } sr_ot_options;
 
 typedef struct {
@@ -306,7 +307,8 @@ sr_ot_status sr_ot_cost_bf16(sr_ot_handle h, int m, int n, int d, const float *X
  * library as a static __device__ variable, present on every device that
  * loads the library until the process exits. It fits any m with n up to
  * 208,000 columns; larger n fail with SR_OT_EUNSUPPORTED. The cost must be
- * C or d = 3 points; precision SR_OT_FP64 or SR_OT_FP32.
+ * C or d = 3 points (squared cost only: with SR_OT_COST_EUCLIDEAN pass the
+ * cost as C, else SR_OT_EUNSUPPORTED); precision SR_OT_FP64 or SR_OT_FP32.
  *
  * `device` must be the device the pointers live on; `cuda_stream` as in
  * sr_ot_create. The first call on a device looks up the array's device

@@ -203,6 +203,9 @@ sr_ot_status sr_ot_gap_noalloc(int device, void *cuda_stream, const sr_ot_option
     if (!a || !b || !T) return nfail(SR_OT_EINVAL, "a, b and T must be non-NULL");
     if (opts->precision == SR_OT_FP32_BF16COST)
         return nfail(SR_OT_EINVAL, "the no-allocation certificate takes SR_OT_FP64 or SR_OT_FP32");
+    if ((X || Y) && opts->cost_kind != SR_OT_COST_SQUARED)
+        return nfail(SR_OT_EUNSUPPORTED, "the no-allocation certificate builds the squared cost from points only "
+                                         "(pass the Euclidean cost as C)");
     int cur = -1;
     cudaError_t e = cudaGetDevice(&cur);
     if (e != cudaSuccess) {

@@ -82,4 +82,18 @@ def test_noalloc_certificate_matches_handle_path():
                                  None, ct.byref(res))
     assert st == S.EUNSUPPORTED
     assert b"scratch" in S.lib.sr_ot_last_error(None)
+
+    # the Euclidean cost is not built from points here (it would need a
+    # buffer): rejected, not silently replaced by the squared one
+    m, n = 8, 12
+    X = torch.rand((m, 3), device="cuda")
+    Y = torch.rand((n, 3), device="cuda")
+    a = torch.full((m,), 1.0 / m, device="cuda")
+    b = torch.full((n,), 1.0 / n, device="cuda")
+    T = torch.zeros((m, n), device="cuda")
+    opts = S.options(precision=S.FP32, cost_kind=S.COST_EUCLIDEAN)
+    st = S.lib.sr_ot_gap_noalloc(0, ct.c_void_p(stream.cuda_stream), ct.byref(opts), m, n, 3, None,
+                                 X.data_ptr(), Y.data_ptr(), a.data_ptr(), b.data_ptr(), T.data_ptr(),
+                                 None, ct.byref(res))
+    assert st == S.EUNSUPPORTED
     h.close()
