@@ -25,8 +25,8 @@
 // Warps 0..NWP-1 produce segment minima (their columns: quads tid + NTC g),
 // warps NWP, NWP+1 (atom warps, even and odd updates) stream the atom
 // records, take the away statistics and publish the row's data, warps
-// NWP+2, NWP+3 are the chain (even and odd updates). With NWP = 4 each
-// chain warp shares its scheduler with one producer only. They
+// NWP+2 .. NWP+1+kChain are the chain (update u goes to warp u mod kChain):
+// while one warp decides and applies an update, the next prepares its own. They
 // synchronise through mbarriers only (no polling): per slot a "full" barrier
 // on which the producers and the atom warp arrive (release) once their words
 // for update u are stored and on which the chain waits (acquire), and per
@@ -53,8 +53,10 @@ constexpr int kSpecLag = 4;        // producers run at most this many updates ah
 constexpr int kSpecSlots = 8;      // candidate / atom-warp slots (> kSpecLag)
 constexpr int kSpecRecAhead = 4;   // atom records are fetched this many updates early
 constexpr int kSpecRecSlots = 16;  // record slots (> kSpecLag + kSpecRecAhead)
+constexpr int kChain = 3;          // chain warps; warp c takes the updates u = c mod kChain
 constexpr long long kSpecSpin = 1ll << 26;  // polls before a wait gives up
 static_assert(kSpecSlots > kSpecLag && kSpecRecSlots > kSpecLag + kSpecRecAhead, "slot rings too small");
+static_assert(kChain >= 2 && kChain <= kSpecLag, "the hand-over columns must lie inside the history window");
 
 __device__ inline unsigned saddr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ inline int vload(const int *p) { return *reinterpret_cast<const volatile int *>(p); }
@@ -83,13 +85,15 @@ constexpr int kAtomWords = 3;  // atom warp output per update: int4 words
 }  // namespace
 
 template <int NWP, int G>
-__global__ void __launch_bounds__(NWP * kWarp + 4 * kWarp, 1) k_epoch_spec(EpochArgs<float> A) {
+__global__ void __launch_bounds__(NWP * kWarp + (2 + kChain) * kWarp, 1) k_epoch_spec(EpochArgs<float> A) {
     constexpr int NTC = NWP * kWarp;  // producer threads
-    constexpr int AW = NWP;  // atom warps NWP, NWP + 1; chain warps NWP + 2, NWP + 3
-    constexpr int NT = NTC + 4 * kWarp;
+    constexpr int AW = NWP;  // atom warps NWP, NWP + 1; chain warps NWP + 2 ...
+    constexpr int NT = NTC + (2 + kChain) * kWarp;
+    constexpr int NE = 2 * (kChain - 1);  // hand-over columns: those of updates u-kChain+1 .. u-1
     constexpr int WID = NTC * 4 * G;
     static_assert(WID <= 8192, "column index must fit 13 bits");
-    static_assert(NWP + 2 * kSpecLag <= kWarp, "candidates and changed columns must fit one warp");
+    static_assert(NWP + 2 * (kSpecLag - kChain + 1) <= kWarp && NE <= kWarp,
+                  "candidates and changed columns must fit one warp");
     extern __shared__ __align__(16) unsigned char smem[];
     float *qh = reinterpret_cast<float *>(smem);
     float *ql = qh + WID;
@@ -282,12 +286,14 @@ __global__ void __launch_bounds__(NWP * kWarp + 4 * kWarp, 1) k_epoch_spec(Epoch
         }
         wait_groups<0>();
     } else {
-        // ================= two chain warps: even and odd updates =========
-        // Warp NWP + 2 + (u & 1) takes update u. It prepares u (segment
-        // minima, the columns changed by updates ver..u-2, the away
-        // statistics) while the other warp decides and applies u - 1; then
-        // it takes the two columns e1, e2 that u - 1 changes, waits until
-        // their residual is stored, evaluates them and decides.
+        // ================= chain warps ====================================
+        // Warp NWP + 2 + (u mod kChain) takes update u. It prepares u
+        // (segment minima, the columns changed by updates ver..u-kChain, the
+        // away statistics) while the other chain warps decide and apply the
+        // updates before it; then it takes the NE columns that updates
+        // u-kChain+1 .. u-1 change (visible once u-1 is decided), waits until
+        // the residual of u-1 (and so of all before it) is stored, evaluates
+        // them and decides.
         const int cwi = warp - (NWP + 2);
         bool aborted = false;
         auto wait_bar = [&](uint64_t *b, unsigned parity) -> bool {
@@ -304,7 +310,7 @@ __global__ void __launch_bounds__(NWP * kWarp + 4 * kWarp, 1) k_epoch_spec(Epoch
             }
             return true;
         };
-        for (int u = cwi; u < m; u += 2) {
+        for (int u = cwi; u < m; u += kChain) {
             const long long k = A.k0 + u;
             const int slot = u % kSpecSlots;
             const int ps = (u + kSpecSlots - 1) % kSpecSlots;  // slot of update u - 1
@@ -331,8 +337,8 @@ __global__ void __launch_bounds__(NWP * kWarp + 4 * kWarp, 1) k_epoch_spec(Epoch
                     key = (uint32_t)cw;
                     col = cj;
                 }
-            } else if (lane < NWP + 2 * (kSpecLag - 1)) {
-                const int w = u - 2 - ((lane - NWP) >> 1);
+            } else if (lane < NWP + 2 * (kSpecLag - kChain + 1)) {
+                const int w = u - kChain - ((lane - NWP) >> 1);
                 if (w >= ver && w >= 0) {
                     const int2 d = dec[w % kSpecSlots];
                     const int c = ((lane - NWP) & 1) ? d.y : d.x;
@@ -366,22 +372,39 @@ __global__ void __launch_bounds__(NWP * kWarp + 4 * kWarp, 1) k_epoch_spec(Epoch
             const int pj = __reduce_min_sync(FULL, key == pk ? col : 0x7FFFFFFF);
             const bool olddirty = (at.j[0] >= 0 && lastmod[at.j[0]] >= ver) ||
                                   (at.cnt > 32 && at.j[1] >= 0 && lastmod[at.j[1]] >= ver);
-            // ---- hand-over: the columns update u-1 changes, then their residual
-            int e1 = -1, e2 = -1;
+            // ---- hand-over: the columns updates u-kChain+1 .. u-1 change
+            // (all visible once u-1 is decided: its warp waited for the
+            // decisions before it), then their residual
+            int ev[NE];
+#pragma unroll
+            for (int e = 0; e < NE; ++e) ev[e] = -1;
             if (u >= 1) {
                 if (!wait_bar(decided + ps, pp)) { aborted = true; break; }
-                const int2 d = dec[ps];
-                e1 = d.x;
-                e2 = d.y;
+#pragma unroll
+                for (int dd = 1; dd < kChain; ++dd) {
+                    if (u - dd >= 0) {
+                        const int2 d = dec[(u - dd) % kSpecSlots];
+                        ev[2 * (dd - 1)] = d.x;
+                        ev[2 * (dd - 1) + 1] = d.y;
+                    }
+                }
             }
-            auto hit = [&](int c) { return c >= 0 && (c == e1 || c == e2); };
+            auto hit = [&](int c) {
+                bool hh = false;
+#pragma unroll
+                for (int e = 0; e < NE; ++e) hh = hh || (c >= 0 && c == ev[e]);
+                return hh;
+            };
             const bool redo_atoms = __any_sync(FULL, olddirty || hit(at.j[0]) || (at.cnt > 32 && hit(at.j[1])));
             const bool redo_lmo = hit(pj);
-            // what does not depend on the residual of u - 1: the cost of the
-            // row at e1, e2 and the record position of the likely vertex pj
-            const int ec = lane == 0 ? e1 : e2;
+            // what does not depend on the residual of the last updates: the
+            // cost of the row at the hand-over columns (lane e: column ev[e])
+            // and the record position of the likely vertex pj
+            int ec = -1;
+#pragma unroll
+            for (int e = 0; e < NE; ++e) ec = lane == e ? ev[e] : ec;
             float ce = 0.f;
-            if (lane < 2 && ec >= 0) {
+            if (ec >= 0) {
                 const float4 y = ys[ec];
                 const float d0 = x0 - y.x, d1 = x1 - y.y, d2 = x2 - y.z;
                 ce = fmaf(d2, d2, fmaf(d1, d1, __fmul_rn(d0, d0)));
@@ -407,10 +430,12 @@ __global__ void __launch_bounds__(NWP * kWarp + 4 * kWarp, 1) k_epoch_spec(Epoch
                 fk = __reduce_min_sync(FULL, kb);
                 js = __reduce_min_sync(FULL, kb == fk ? bj : 0x7FFFFFFF);
             } else {
-                const uint32_t ke = (lane < 2 && ec >= 0) ? f2key(ce + qh[ec]) : 0xFFFFFFFFu;
-                const uint32_t k1 = __shfl_sync(FULL, ke, 0), k2 = __shfl_sync(FULL, ke, 1);
-                if (e1 >= 0 && (k1 < fk || (k1 == fk && e1 < js))) { fk = k1; js = e1; }
-                if (e2 >= 0 && (k2 < fk || (k2 == fk && e2 < js))) { fk = k2; js = e2; }
+                const uint32_t ke = ec >= 0 ? f2key(ce + qh[ec]) : 0xFFFFFFFFu;
+#pragma unroll
+                for (int e = 0; e < NE; ++e) {
+                    const uint32_t kk = __shfl_sync(FULL, ke, e);
+                    if (ev[e] >= 0 && (kk < fk || (kk == fk && ev[e] < js))) { fk = kk; js = ev[e]; }
+                }
             }
             const float gmin = key2f(fk);
             DF tvd{__int_as_float(w0.y), __int_as_float(w0.z)};
@@ -491,7 +516,7 @@ static void launch_spec(const EpochArgs<float> &A, cudaStream_t st) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
         attr_set = true;
     }
-    kern<<<1, NWP * kWarp + 4 * kWarp, spec_smem<NWP, G>(), st>>>(A);
+    kern<<<1, NWP * kWarp + (2 + kChain) * kWarp, spec_smem<NWP, G>(), st>>>(A);
 }
 
 bool launch_epoch_spec(const EpochArgs<float> &A, cudaStream_t st) {
