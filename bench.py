@@ -52,8 +52,8 @@ BATCH_WORKLOADS = ("colour_batch512", "colour_batch64_2048")
 # is built from are the ones captured: their digest at capture time must match.
 CAPTURED_TRAFFIC = {
     ("colour4096_fp32", "roofline"): {
-        "bytes": 4398848, "files": ("solve_spec.cu", "atoms.cuh", "step.cuh", "cpasync.cuh", "common.cuh"),
-        "digest": "b92b9df6ebe2dd2d"},
+        "bytes": 4404736, "files": ("solve_spec.cu", "atoms.cuh", "step.cuh", "cpasync.cuh", "common.cuh"),
+        "digest": "98a8fa3fca754c5f"},
     ("feature8192_d128", "roofline_cost"): {
         "bytes": 4290048 + 207054592, "files": ("cost_bf16.cu", "common.cuh"), "digest": "37d37fe188a2335d"},
     ("colour_batch64_2048", "roofline_adjoint"): {
@@ -228,7 +228,7 @@ def epoch_kernel_name(s, n):
         return "k_epoch_sparse (one CTA, m block updates; active-set, away steps)"
     if s["precision"] != "FP32_BF16COST" and n <= 4096:
         return ("k_epoch_spec (one CTA, m block updates; pairwise; segment minima and away statistics taken "
-                "ahead by producer warps, two alternating chain warps)")
+                "ahead by producer warps, three chain warps in rotation)")
     if n <= 8192:
         return "k_epoch_pipe (one CTA, m block updates; active-set, pairwise, two control warps)"
     return "k_epoch_sparse (one CTA, m block updates; active-set, pairwise)"
