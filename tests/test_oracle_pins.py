@@ -575,3 +575,24 @@ def test_transfer_stats_special_plans(oracle_mod):
     assert abs(s0["e_c"] - s0["col_err"]) <= 1e-15
     zeros = sum(1 for i in range(m) for j in range(n) if T0[i, j] == 0.0)
     assert s0["sparsity"] == zeros / (m * n) == (n - 1) / n
+
+
+def test_euclidean_cost_pins(oracle_mod):
+    """The paper's cost ||x_i - y_j||_2 (Sec. 5.1): equal to numpy's vector
+    norm cell by cell, its square is the squared cost, it is a metric
+    (symmetric, zero on the diagonal of a cloud with itself, triangle
+    inequality through any third point), and a 3-4-5 pair gives 5."""
+    rng = np.random.default_rng(12)
+    X, Y, Z = rng.random((9, 4)), rng.random((7, 4)), rng.random((5, 4))
+    E = oracle_mod.cost(X, Y, squared=False)
+    for i in range(9):
+        for j in range(7):
+            assert abs(E[i, j] - np.linalg.norm(X[i] - Y[j])) <= 1e-15
+    np.testing.assert_allclose(E ** 2, oracle_mod.cost(X, Y), rtol=1e-14, atol=0)
+    XX = oracle_mod.cost(X, X, squared=False)
+    assert np.all(np.diag(XX) == 0.0) and np.array_equal(XX, XX.T)
+    XZ, ZY = oracle_mod.cost(X, Z, squared=False), oracle_mod.cost(Z, Y, squared=False)
+    for k in range(5):
+        assert np.all(E <= XZ[:, k:k + 1] + ZY[k:k + 1, :] + 1e-15)
+    P = oracle_mod.cost(np.array([[0.0, 0.0, 0.0]]), np.array([[3.0, 4.0, 0.0]]), squared=False)
+    assert P[0, 0] == 5.0
