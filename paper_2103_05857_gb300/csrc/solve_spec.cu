@@ -372,6 +372,10 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + kChain) * kWarp, 1) k_epoch
             const int pj = __reduce_min_sync(FULL, key == pk ? col : 0x7FFFFFFF);
             const bool olddirty = (at.j[0] >= 0 && lastmod[at.j[0]] >= ver) ||
                                   (at.cnt > 32 && at.j[1] >= 0 && lastmod[at.j[1]] >= ver);
+            // the record position of the likely vertex pj (off the hand-over)
+            bool present = false;
+            int jpos = -1;
+            atom_weight(at, pj, &present, &jpos);
             // ---- hand-over: the columns updates u-kChain+1 .. u-1 change
             // (all visible once u-1 is decided: its warp waited for the
             // decisions before it), then their residual
@@ -399,7 +403,6 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + kChain) * kWarp, 1) k_epoch
             const bool redo_lmo = hit(pj);
             // what does not depend on the residual of the last updates: the
             // cost of the row at the hand-over columns (lane e: column ev[e])
-            // and the record position of the likely vertex pj
             int ec = -1;
 #pragma unroll
             for (int e = 0; e < NE; ++e) ec = lane == e ? ev[e] : ec;
@@ -409,9 +412,6 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + kChain) * kWarp, 1) k_epoch
                 const float d0 = x0 - y.x, d1 = x1 - y.y, d2 = x2 - y.z;
                 ce = fmaf(d2, d2, fmaf(d1, d1, __fmul_rn(d0, d0)));
             }
-            bool present = false;
-            int jpos = -1;
-            atom_weight(at, pj, &present, &jpos);
             if (u >= 1 && !wait_bar(done + ps, pp)) { aborted = true; break; }
             uint32_t fk = pk;
             int js = pj;
