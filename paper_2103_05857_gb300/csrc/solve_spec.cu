@@ -53,10 +53,11 @@ constexpr int kSpecLag = 4;        // producers run at most this many updates ah
 constexpr int kSpecSlots = 8;      // candidate / atom-warp slots (> kSpecLag)
 constexpr int kSpecRecAhead = 4;   // atom records are fetched this many updates early
 constexpr int kSpecRecSlots = 16;  // record slots (> kSpecLag + kSpecRecAhead)
-constexpr int kChain = 3;          // chain warps; warp c takes the updates u = c mod kChain
+constexpr int kChain = 3;          // chain warps; warp c takes the updates u = c mod kChain (exactly
+                                   // 3: the hand-over takes the columns of u-2, then those of u-1)
 constexpr long long kSpecSpin = 1ll << 26;  // polls before a wait gives up
 static_assert(kSpecSlots > kSpecLag && kSpecRecSlots > kSpecLag + kSpecRecAhead, "slot rings too small");
-static_assert(kChain >= 2 && kChain <= kSpecLag, "the hand-over columns must lie inside the history window");
+static_assert(kChain == 3 && kChain <= kSpecLag, "the hand-over takes the columns of u-2 and u-1");
 
 __device__ inline unsigned saddr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ inline int vload(const int *p) { return *reinterpret_cast<const volatile int *>(p); }
@@ -89,11 +90,9 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + kChain) * kWarp, 1) k_epoch
     constexpr int NTC = NWP * kWarp;  // producer threads
     constexpr int AW = NWP;  // atom warps NWP, NWP + 1; chain warps NWP + 2 ...
     constexpr int NT = NTC + (2 + kChain) * kWarp;
-    constexpr int NE = 2 * (kChain - 1);  // hand-over columns: those of updates u-kChain+1 .. u-1
     constexpr int WID = NTC * 4 * G;
     static_assert(WID <= 8192, "column index must fit 13 bits");
-    static_assert(NWP + 2 * (kSpecLag - kChain + 1) <= kWarp && NE <= kWarp,
-                  "candidates and changed columns must fit one warp");
+    static_assert(NWP + 2 * (kSpecLag - kChain + 1) <= kWarp, "candidates and changed columns must fit one warp");
     extern __shared__ __align__(16) unsigned char smem[];
     float *qh = reinterpret_cast<float *>(smem);
     float *ql = qh + WID;
@@ -290,10 +289,10 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + kChain) * kWarp, 1) k_epoch
         // Warp NWP + 2 + (u mod kChain) takes update u. It prepares u
         // (segment minima, the columns changed by updates ver..u-kChain, the
         // away statistics) while the other chain warps decide and apply the
-        // updates before it; then it takes the NE columns that updates
-        // u-kChain+1 .. u-1 change (visible once u-1 is decided), waits until
-        // the residual of u-1 (and so of all before it) is stored, evaluates
-        // them and decides.
+        // updates before it; then it merges the columns that u-2 changed
+        // (decided and stored an update earlier), takes the two that u-1
+        // changes once u-1 is decided, waits until their residual is stored,
+        // evaluates them and decides.
         const int cwi = warp - (NWP + 2);
         bool aborted = false;
         auto wait_bar = [&](uint64_t *b, unsigned parity) -> bool {
@@ -376,47 +375,53 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + kChain) * kWarp, 1) k_epoch
             bool present = false;
             int jpos = -1;
             atom_weight(at, pj, &present, &jpos);
-            // ---- hand-over: the columns updates u-kChain+1 .. u-1 change
-            // (all visible once u-1 is decided: its warp waited for the
-            // decisions before it), then their residual
-            int ev[NE];
-#pragma unroll
-            for (int e = 0; e < NE; ++e) ev[e] = -1;
+            // ---- hand-over, 1: update u-2, decided and stored an update
+            // earlier: the exact keys of its two columns join the prepared
+            // minimum (a prepared minimum on one of them was stale: the full
+            // LMO is taken instead)
+            int c2[2] = {-1, -1}, c1[2] = {-1, -1};
+            if (u >= 2) {
+                const int s2 = (u - 2) % kSpecSlots;
+                const unsigned p2 = (unsigned)((u - 2) / kSpecSlots) & 1u;
+                if (!wait_bar(decided + s2, p2) || !wait_bar(done + s2, p2)) { aborted = true; break; }
+                const int2 d = dec[s2];
+                c2[0] = d.x;
+                c2[1] = d.y;
+            }
+            bool redo_lmo = pj >= 0 && (pj == c2[0] || pj == c2[1]);
+            uint32_t fk = pk;
+            int js = pj;
+            {
+                const int c = lane == 0 ? c2[0] : c2[1];
+                const uint32_t ke = (lane < 2 && c >= 0) ? f2key(grad(c)) : 0xFFFFFFFFu;
+                const uint32_t k0 = __shfl_sync(FULL, ke, 0), k1 = __shfl_sync(FULL, ke, 1);
+                if (c2[0] >= 0 && (k0 < fk || (k0 == fk && c2[0] < js))) { fk = k0; js = c2[0]; }
+                if (c2[1] >= 0 && (k1 < fk || (k1 == fk && c2[1] < js))) { fk = k1; js = c2[1]; }
+            }
+            const int pj2 = js;
+            if (pj2 != pj) atom_weight(at, pj2, &present, &jpos);
+            // ---- hand-over, 2: update u-1, its columns, then their residual
             if (u >= 1) {
                 if (!wait_bar(decided + ps, pp)) { aborted = true; break; }
-#pragma unroll
-                for (int dd = 1; dd < kChain; ++dd) {
-                    if (u - dd >= 0) {
-                        const int2 d = dec[(u - dd) % kSpecSlots];
-                        ev[2 * (dd - 1)] = d.x;
-                        ev[2 * (dd - 1) + 1] = d.y;
-                    }
-                }
+                const int2 d = dec[ps];
+                c1[0] = d.x;
+                c1[1] = d.y;
             }
-            auto hit = [&](int c) {
-                bool hh = false;
-#pragma unroll
-                for (int e = 0; e < NE; ++e) hh = hh || (c >= 0 && c == ev[e]);
-                return hh;
-            };
+            redo_lmo = redo_lmo || (pj2 >= 0 && (pj2 == c1[0] || pj2 == c1[1]));
+            auto hit = [&](int c) { return c >= 0 && (c == c1[0] || c == c1[1] || c == c2[0] || c == c2[1]); };
             const bool redo_atoms = __any_sync(FULL, olddirty || hit(at.j[0]) || (at.cnt > 32 && hit(at.j[1])));
-            const bool redo_lmo = hit(pj);
-            // what does not depend on the residual of the last updates: the
-            // cost of the row at the hand-over columns (lane e: column ev[e])
-            int ec = -1;
-#pragma unroll
-            for (int e = 0; e < NE; ++e) ec = lane == e ? ev[e] : ec;
+            // what does not depend on the residual of u-1: the cost of the
+            // row at its two columns (lanes 0, 1)
+            const int ec = lane == 0 ? c1[0] : c1[1];
             float ce = 0.f;
-            if (ec >= 0) {
+            if (lane < 2 && ec >= 0) {
                 const float4 y = ys[ec];
                 const float d0 = x0 - y.x, d1 = x1 - y.y, d2 = x2 - y.z;
                 ce = fmaf(d2, d2, fmaf(d1, d1, __fmul_rn(d0, d0)));
             }
             if (u >= 1 && !wait_bar(done + ps, pp)) { aborted = true; break; }
-            uint32_t fk = pk;
-            int js = pj;
             if (redo_lmo) {
-                // the prepared minimum sits on a column u - 1 changed: full LMO
+                // the prepared minimum sits on a column changed since: full LMO
                 float bv = INF;
                 int bj = 0x7FFFFFFF;
                 for (int q = lane; q < WID / 4; q += kWarp) {
@@ -430,12 +435,10 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + kChain) * kWarp, 1) k_epoch
                 fk = __reduce_min_sync(FULL, kb);
                 js = __reduce_min_sync(FULL, kb == fk ? bj : 0x7FFFFFFF);
             } else {
-                const uint32_t ke = ec >= 0 ? f2key(ce + qh[ec]) : 0xFFFFFFFFu;
-#pragma unroll
-                for (int e = 0; e < NE; ++e) {
-                    const uint32_t kk = __shfl_sync(FULL, ke, e);
-                    if (ev[e] >= 0 && (kk < fk || (kk == fk && ev[e] < js))) { fk = kk; js = ev[e]; }
-                }
+                const uint32_t ke = (lane < 2 && ec >= 0) ? f2key(ce + qh[ec]) : 0xFFFFFFFFu;
+                const uint32_t k0 = __shfl_sync(FULL, ke, 0), k1 = __shfl_sync(FULL, ke, 1);
+                if (c1[0] >= 0 && (k0 < fk || (k0 == fk && c1[0] < js))) { fk = k0; js = c1[0]; }
+                if (c1[1] >= 0 && (k1 < fk || (k1 == fk && c1[1] < js))) { fk = k1; js = c1[1]; }
             }
             const float gmin = key2f(fk);
             DF tvd{__int_as_float(w0.y), __int_as_float(w0.z)};
@@ -461,7 +464,7 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + kChain) * kWarp, 1) k_epoch
                 gmx = st.t_v * ra;  // same rounding as the two-phase kernel
                 inv = ia;
             }
-            if (js != pj) atom_weight(at, js, &present, &jpos);
+            if (js != pj2) atom_weight(at, js, &present, &jpos);
             const Step<float> S = decide_pairwise(st, gmin, js, ai, rho, gmx, inv, n);
             // ---- decision of u: the columns it changes, for the other warp
             const bool moved = S.kind == 2 && S.v != S.js && st.vpos >= 0;
