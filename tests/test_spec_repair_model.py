@@ -1,0 +1,144 @@
+"""The repair rule of the speculative BCPFW kernel (solve_spec.cu), modelled on
+the host: for every interleaving its barriers allow, the repaired LMO equals
+the exact one (the LMO of Sec. 3.1, eq. 7: argmin of grad_ij = C_ij + q_j over
+j, ties to the smallest j).
+
+What the kernel guarantees about the residual q each party reads, as versions
+(version k = q after the first k block updates of the epoch; a pairwise step,
+Alg. A.3, changes q in the two columns j*, v only):
+  - producers take their segment minima for update u with every column at some
+    version in [ver, u], ver = max(u - 4, 0) (they wait until update u - 5 is
+    applied), each column independently (reads race with the chain's stores);
+  - the chain warp of u prepares after its own update u - 3 (so every column is
+    at version >= u - 2), with the updates u - 2, u - 1 possibly half applied;
+    the last-change marks of u - 4 and u - 3 are visible, those of u - 2 and
+    u - 1 may or may not be;
+  - after the hand-over of u - 2 every column is at version >= u - 1; after that
+    of u - 1 at version u.
+The atom warp takes the away vertex (Alg. A.3: the atom with the largest
+gradient) at versions in [ver, u] as well; the chain takes it again when one of
+the row's atom columns changed since ver. The model draws all of these at
+random (with many exact ties in C + q), runs the chain's steps in the kernel's
+order and compares with the exact LMO and away vertex.
+"""
+import numpy as np
+
+LAG = 4
+
+
+def _min(keys):
+    return min(keys) if keys else (np.inf, 1 << 30)
+
+
+def _chain_lmo(rng, u, C, q0, dec, deltas, nseg, atoms, drop=None):
+    """The kernel's LMO and away vertex for update u under one random
+    interleaving. `drop` leaves one repair out (a planted mistake): "stale" (no
+    segment recompute), "history" (no columns of u-3, u-4), "c2" or "c1" (no
+    hand-over merge), "atoms" (the atom warp's away statistics always kept)."""
+    n = len(C)
+    seg_of = (np.arange(n) // 4) % nseg  # quads interleaved over the producer warps
+
+    def value(j, k):  # grad at column j with q at version k
+        return C[j] + q0[j] + sum(deltas[w][j] for w in range(k) if dec[w] is not None and j in dec[w])
+
+    ver = u - LAG if u > LAG else 0
+    # atom warp: away vertex (largest gradient over the row's atoms, ties to
+    # the smallest column) with every atom column at a version in [ver, u]
+    away = min((-value(j, int(rng.integers(ver, u + 1))), j) for j in atoms)[1]
+    # producers: per column a version in [ver, u]
+    cand = {}
+    for s in range(nseg):
+        cols = np.nonzero(seg_of == s)[0]
+        if len(cols) == 0:  # (the kernel pads: such a segment never wins)
+            continue
+        vals = [(value(j, int(rng.integers(ver, u + 1))), int(j)) for j in cols]
+        cand[s] = min(vals)
+    # prepare: visible last-change marks and per column a version in [u-2, u]
+    lo = max(u - 2, 0)
+    visible = {w for w in range(u) if w <= u - 3 or rng.random() < 0.5}
+
+    def lastmod(j):
+        ws = [w for w in range(u) if w in visible and dec[w] is not None and j in dec[w]]
+        return max(ws) if ws else -1
+
+    def prep_value(j):
+        return value(j, int(rng.integers(lo, u + 1)))
+
+    keys = []
+    for s in cand:
+        val, cj = cand[s]
+        if lastmod(cj) >= ver and drop != "stale":  # stale segment: recomputed now
+            cols = np.nonzero(seg_of == s)[0]
+            keys.append(min((prep_value(j), int(j)) for j in cols))
+        else:
+            keys.append((val, cj))
+    for w in (u - 3, u - 4):  # columns of the updates before the hand-over
+        if w >= ver and w >= 0 and dec[w] is not None and drop != "history":
+            keys.extend((prep_value(c), c) for c in dec[w])
+    olddirty = any(lastmod(j) >= ver for j in atoms)
+    fk, js = _min(keys)
+    pj = js
+    # hand-over 1: update u-2 is applied, u-1 may be half applied
+    c2 = dec[u - 2] if u >= 2 and dec[u - 2] is not None and drop != "c2" else ()
+    redo = pj in c2
+    for c in c2:
+        k = value(c, int(rng.integers(max(u - 1, 0), u + 1)))
+        if (k, c) < (fk, js):
+            fk, js = k, c
+    pj2 = js
+    # hand-over 2: update u-1 is applied, every column at version u
+    c1 = dec[u - 1] if u >= 1 and dec[u - 1] is not None and drop != "c1" else ()
+    redo = redo or pj2 in c1
+    if redo:
+        fk, js = min((value(j, u), j) for j in range(n))
+    else:
+        for c in c1:
+            k = value(c, u)
+            if (k, c) < (fk, js):
+                fk, js = k, c
+    # away statistics: taken again when an atom column changed since ver
+    hit = any(j in c1 or j in c2 for j in atoms)
+    if (olddirty or hit) and drop != "atoms":
+        away = min((-value(j, u), j) for j in atoms)[1]
+    return js, away, value
+
+
+def _mismatches(seed, trials, drop=None):
+    rng = np.random.default_rng(seed)
+    bad = 0
+    for _ in range(trials):
+        n = int(rng.integers(8, 72))
+        nseg = int(rng.integers(1, 5))
+        u = int(rng.integers(0, 14))
+        # small integers: many exact ties between columns
+        C = rng.integers(0, 6, n).astype(float)
+        q0 = rng.integers(-3, 4, n).astype(float)
+        dec, deltas = [], []
+        for w in range(u):
+            if rng.random() < 0.8:
+                a, b = (int(v) for v in rng.choice(n, 2, replace=False))
+                dec.append((a, b))
+                d = np.zeros(n)
+                d[a] = float(rng.integers(1, 4))    # mass moved onto j*: its q grows
+                d[b] = -float(rng.integers(1, 4))   # and off v: its q drops
+                deltas.append(d)
+            else:
+                dec.append(None)
+                deltas.append(np.zeros(n))
+        atoms = [int(j) for j in rng.choice(n, int(rng.integers(1, 6)), replace=False)]
+        js, away, value = _chain_lmo(rng, u, C, q0, dec, deltas, nseg, atoms, drop)
+        exact = min((value(j, u), j) for j in range(n))[1]
+        exact_away = min((-value(j, u), j) for j in atoms)[1]
+        bad += (js != exact) or (away != exact_away)
+    return bad
+
+
+def test_speculative_repair_gives_the_exact_lmo():
+    assert _mismatches(2103, 4000) == 0
+
+
+def test_each_repair_is_needed():
+    """Leaving out any one repair makes the model return wrong LMOs on the
+    same kind of draws, so the test above has something to catch."""
+    for drop in ("stale", "history", "c2", "c1", "atoms"):
+        assert _mismatches(7, 1500, drop) > 0, drop
