@@ -21,9 +21,22 @@ the row's atom columns changed since ver. The model draws all of these at
 random (with many exact ties in C + q), runs the chain's steps in the kernel's
 order and compares with the exact LMO and away vertex.
 """
+import os
+import re
+
 import numpy as np
 
-LAG = 4
+SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2103_05857_gb300",
+                   "csrc", "solve_spec.cu")
+
+
+def _kernel_constant(name):
+    with open(SRC) as fh:
+        return int(re.search(r"constexpr int %s = (\d+);" % name, fh.read()).group(1))
+
+
+LAG = _kernel_constant("kSpecLag")      # producers run at most this many updates ahead
+CHAIN = _kernel_constant("kChain")      # chain warps in rotation
 
 
 def _min(keys):
@@ -53,9 +66,11 @@ def _chain_lmo(rng, u, C, q0, dec, deltas, nseg, atoms, drop=None):
             continue
         vals = [(value(j, int(rng.integers(ver, u + 1))), int(j)) for j in cols]
         cand[s] = min(vals)
-    # prepare: visible last-change marks and per column a version in [u-2, u]
-    lo = max(u - 2, 0)
-    visible = {w for w in range(u) if w <= u - 3 or rng.random() < 0.5}
+    # prepare: after the warp's own update u - CHAIN (and the wait for u - CHAIN - 1
+    # within it): marks up to u - CHAIN visible, the later ones maybe; every
+    # column at a version in [u - CHAIN + 1, u]
+    lo = max(u - CHAIN + 1, 0)
+    visible = {w for w in range(u) if w <= u - CHAIN or rng.random() < 0.5}
 
     def lastmod(j):
         ws = [w for w in range(u) if w in visible and dec[w] is not None and j in dec[w]]
@@ -72,7 +87,7 @@ def _chain_lmo(rng, u, C, q0, dec, deltas, nseg, atoms, drop=None):
             keys.append(min((prep_value(j), int(j)) for j in cols))
         else:
             keys.append((val, cj))
-    for w in (u - 3, u - 4):  # columns of the updates before the hand-over
+    for w in range(u - CHAIN, u - LAG - 1, -1):  # columns of the updates before the hand-over
         if w >= ver and w >= 0 and dec[w] is not None and drop != "history":
             keys.extend((prep_value(c), c) for c in dec[w])
     olddirty = any(lastmod(j) >= ver for j in atoms)
@@ -131,6 +146,12 @@ def _mismatches(seed, trials, drop=None):
         exact_away = min((-value(j, u), j) for j in atoms)[1]
         bad += (js != exact) or (away != exact_away)
     return bad
+
+
+def test_model_follows_the_kernel_constants():
+    """The hand-over takes the columns of u-2 and u-1 (three chain warps), the
+    other changed columns are the ones of u-CHAIN .. u-LAG."""
+    assert CHAIN == 3 and LAG >= CHAIN
 
 
 def test_speculative_repair_gives_the_exact_lmo():
