@@ -71,6 +71,16 @@ def _load():
             lib.srot_or_solve.restype = ct.c_int
             lib.srot_or_solve.argtypes = [ct.c_int, ct.c_int, dp, dp, dp, ct.POINTER(Opts), dp,
                                           ip, ip, ct.c_longlong, dp, ct.POINTER(Result)]
+            lib.srot_or_solve_ex.restype = ct.c_int
+            lib.srot_or_solve_ex.argtypes = [ct.c_int, ct.c_int, dp, dp, dp, ct.POINTER(Opts), dp,
+                                             ip, ip, ct.c_longlong, dp, dp, dp, ct.POINTER(Result)]
+            lib.srot_or_sample_from.restype = ct.c_int
+            lib.srot_or_sample_from.argtypes = [dp, ct.c_int, ct.c_uint64]
+            lib.srot_or_uniform_index.restype = ct.c_int
+            lib.srot_or_uniform_index.argtypes = [ct.c_uint64, ct.c_int]
+            lib.srot_or_apply_step.restype = None
+            lib.srot_or_apply_step.argtypes = [ct.c_int, dp, dp, dp, ct.c_int, ct.c_int, ct.c_int,
+                                               ct.c_int, ct.c_double]
             lib.srot_or_block_step.restype = ct.c_int
             lib.srot_or_block_step.argtypes = [ct.c_int, ct.c_int, dp, dp, dp, dp, ct.c_int,
                                                ct.c_longlong, ct.POINTER(Opts), ip, ip, ip, dp]
@@ -136,11 +146,14 @@ def certificate(C, a, b, rho, T):
     return dict(f=out[0], g=out[1], w=out[2], lin=out[3], pen=out[4], g_rows=g_rows, s=s)
 
 
-def solve(C, a, b, T0=None, trace: bool = False, **kw):
+def solve(C, a, b, T0=None, trace: bool = False, epoch_state: bool = False, **kw):
     """Run the block-coordinate solver (Alg. 1, A.2, A.3, A.4) or full FW (Alg. A.1).
 
     Returns (T, result_dict, trace_i, trace_j, history) where history rows are
-    (epoch, f, g) for every certificate taken."""
+    (epoch, f, g) for every certificate taken. With epoch_state=True the
+    result dict also holds "ga_hist" (epochs x m: the gap-adaptive sampling
+    gaps at the end of each epoch, after its global update if one was due)
+    and "T_hist" (epochs x m x n: the plan at the end of each epoch)."""
     C, a, b = _f64(C), _f64(a), _f64(b)
     m, n = C.shape
     o = make_opts(warm_start=int(T0 is not None), **kw)
@@ -149,14 +162,21 @@ def solve(C, a, b, T0=None, trace: bool = False, **kw):
     ti = np.empty(max(cap, 1), dtype=np.int32)
     tj = np.empty(max(cap, 1), dtype=np.int32)
     hist = np.zeros(3 * max(int(o.max_epochs), 1) + 3)
+    ga_hist = T_hist = None
+    if epoch_state:
+        ga_hist = np.full((max(int(o.max_epochs), 1), m), np.nan)
+        T_hist = np.full((max(int(o.max_epochs), 1), m, n), np.nan)
     res = Result()
-    _load().srot_or_solve(m, n, _dp(C), _dp(a), _dp(b), ct.byref(o), _dp(T),
-                          _ip(ti) if trace else None, _ip(tj) if trace else None, cap,
-                          _dp(hist), ct.byref(res))
+    _load().srot_or_solve_ex(m, n, _dp(C), _dp(a), _dp(b), ct.byref(o), _dp(T),
+                             _ip(ti) if trace else None, _ip(tj) if trace else None, cap,
+                             _dp(hist), _dp(ga_hist), _dp(T_hist), ct.byref(res))
     if res.status != 0:
         raise ValueError(f"oracle solve rejected the options (status {res.status})")
     rd = dict(f=res.f, g=res.g, w=res.w, epochs=res.epochs, updates=res.updates,
               converged=bool(res.converged))
+    if epoch_state:
+        rd["ga_hist"] = ga_hist[: int(res.epochs)]
+        rd["T_hist"] = T_hist[: int(res.epochs)]
     h = hist.reshape(-1, 3)[: int(res.n_hist)]
     k = int(res.updates)
     return T, rd, (ti[:k] if trace else None), (tj[:k] if trace else None), h
@@ -177,6 +197,30 @@ def block_step(C, a, T, r, i, k, **kw):
     if st != 0:
         raise ValueError("oracle block step rejected the options")
     return js.value, v.value, dr.value, gam.value
+
+
+def apply_step(a, T, r, i, direction, jstar, v, gamma):
+    """Apply a given decision (direction 0 FW, 1 away, 2 pairwise, -1 none;
+    LMO vertex jstar, away atom v, step gamma) to row i of (T, r) in place,
+    with the same update arithmetic as a block step."""
+    a = _f64(a)
+    assert T.dtype == np.float64 and T.flags.c_contiguous
+    assert r.dtype == np.float64 and r.flags.c_contiguous
+    n = T.shape[1]
+    _load().srot_or_apply_step(n, _dp(a), _dp(T), _dp(r), int(i), int(direction), int(jstar), int(v),
+                               float(gamma))
+
+
+def sample_from(g, u64: int) -> int:
+    """The gap-adaptive sampling step (Alg. A.4) for one 64-bit uniform draw:
+    an index with probability proportional to max(g_i, 0)."""
+    g = _f64(g)
+    return int(_load().srot_or_sample_from(_dp(g), len(g), int(u64) & (2**64 - 1)))
+
+
+def uniform_index(u64: int, m: int) -> int:
+    """The uniform block order's index floor(u * m) for one 64-bit draw."""
+    return int(_load().srot_or_uniform_index(int(u64) & (2**64 - 1), int(m)))
 
 
 def adjoint(X, Y, b, rho, T):

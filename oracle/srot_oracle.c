@@ -188,6 +188,47 @@ typedef struct {
     double gamma;
 } or_step_info;
 
+/* Apply one decided block update to row t_i and the residual r (Alg. 1,
+ * line "t_i <- (1 - gamma) t_i + gamma s_i"; Alg. A.2 away step; Alg. A.3
+ * pairwise step, with the atom v dropped when gamma reaches its maximum).
+ * dir: 0 Frank-Wolfe direction toward a_i e_js, 1 away direction from the
+ * atom v (gamma_max = alpha_v / (1 - alpha_v), alpha_v = t_iv / a_i),
+ * 2 pairwise move of mass from v to js (gamma_max = alpha_v), -1 no move. */
+static void or_apply_step(int n, double *ti, double ai, double *r, int dir, int js,
+                          int v, double gam) {
+    if (dir == 0) {
+        double omg = 1.0 - gam;
+        for (int j = 0; j < n; ++j) {
+            double told = ti[j];
+            double tnew = omg * told;
+            if (j == js) tnew = tnew + gam * ai;
+            r[j] = r[j] + (tnew - told);
+            ti[j] = tnew;
+        }
+    } else if (dir == 1) {
+        double alpha = ti[v] / ai;
+        double gmax = alpha / (1.0 - alpha);
+        double opg = 1.0 + gam;
+        for (int j = 0; j < n; ++j) {
+            double told = ti[j];
+            double tnew = opg * told;
+            if (j == v) tnew = (gam >= gmax) ? 0.0 : tnew - gam * ai;
+            r[j] = r[j] + (tnew - told);
+            ti[j] = tnew;
+        }
+    } else if (dir == 2 && v != js) {
+        double gmax = ti[v] / ai;
+        double moved = (gam >= gmax) ? ti[v] : gam * ai;
+        double tv_old = ti[v], tj_old = ti[js];
+        double tv_new = (gam >= gmax) ? 0.0 : tv_old - moved;
+        double tj_new = tj_old + moved;
+        r[v] = r[v] + (tv_new - tv_old);
+        r[js] = r[js] + (tj_new - tj_old);
+        ti[v] = tv_new;
+        ti[js] = tj_new;
+    }
+}
+
 /* One block update of row i (Alg. 1; Alg. A.2; Alg. A.3). `k` is the
  * global block-update counter used by the decay rule 2m/(k+2m) (Alg. 1,
  * written for m blocks). T row i and r are updated in place. */
@@ -221,14 +262,7 @@ static int or_block_update(int m, int n, const double *Ci, double *ti, double ai
             }
             gam = or_line_search(g_fw, dd, rho, 1.0);
         }
-        double omg = 1.0 - gam;
-        for (int j = 0; j < n; ++j) {
-            double told = ti[j];
-            double tnew = omg * told;
-            if (j == js) tnew = tnew + gam * ai;
-            r[j] = r[j] + (tnew - told);
-            ti[j] = tnew;
-        }
+        or_apply_step(n, ti, ai, r, 0, js, -1, gam);
         info->dir = 0; info->gamma = gam;
         return 0;
     }
@@ -254,14 +288,7 @@ static int or_block_update(int m, int n, const double *Ci, double *ti, double ai
                 dd = dd + dl * dl;
             }
             double gam = or_line_search(g_fw, dd, rho, 1.0);
-            double omg = 1.0 - gam;
-            for (int j = 0; j < n; ++j) {
-                double told = ti[j];
-                double tnew = omg * told;
-                if (j == js) tnew = tnew + gam * ai;
-                r[j] = r[j] + (tnew - told);
-                ti[j] = tnew;
-            }
+            or_apply_step(n, ti, ai, r, 0, js, v, gam);
             info->dir = 0; info->gamma = gam;
         } else {
             double alpha = ti[v] / ai;
@@ -272,14 +299,7 @@ static int or_block_update(int m, int n, const double *Ci, double *ti, double ai
                 dd = dd + dl * dl;
             }
             double gam = or_line_search(g_aw, dd, rho, gmax);
-            double opg = 1.0 + gam;
-            for (int j = 0; j < n; ++j) {
-                double told = ti[j];
-                double tnew = opg * told;
-                if (j == v) tnew = (gam >= gmax) ? 0.0 : tnew - gam * ai;
-                r[j] = r[j] + (tnew - told);
-                ti[j] = tnew;
-            }
+            or_apply_step(n, ti, ai, r, 1, js, v, gam);
             info->dir = 1; info->gamma = gam;
         }
         return 0;
@@ -291,14 +311,7 @@ static int or_block_update(int m, int n, const double *Ci, double *ti, double ai
     double dd = 2.0 * ai * ai;
     double gmax = ti[v] / ai;
     double gam = or_line_search(g_pw, dd, rho, gmax);
-    double moved = (gam >= gmax) ? ti[v] : gam * ai;
-    double tv_old = ti[v], tj_old = ti[js];
-    double tv_new = (gam >= gmax) ? 0.0 : tv_old - moved;
-    double tj_new = tj_old + moved;
-    r[v] = r[v] + (tv_new - tv_old);
-    r[js] = r[js] + (tj_new - tj_old);
-    ti[v] = tv_new;
-    ti[js] = tj_new;
+    or_apply_step(n, ti, ai, r, 2, js, v, gam);
     info->dir = 2; info->gamma = gam;
     return 0;
 }
@@ -315,6 +328,15 @@ int srot_or_block_step(int m, int n, const double *C, const double *a, double *T
     free(grad);
     *jstar = info.jstar; *v = info.v; *dir = info.dir; *gamma = info.gamma;
     return st;
+}
+
+/* Public entry that applies a GIVEN decision (direction dir, LMO vertex
+ * jstar, away atom v, step gamma) to row i of (T, r) with the same update
+ * arithmetic as a block step; used to follow another solver's decision at a
+ * point where the two may legitimately differ (an exact tie). */
+void srot_or_apply_step(int n, const double *a, double *T, double *r, int i, int dir,
+                        int jstar, int v, double gamma) {
+    or_apply_step(n, T + (size_t)i * n, a[i], r, dir, jstar, v, gamma);
 }
 
 /* Uniform permutation of 0..m-1 for epoch e: positions sorted by a random
@@ -338,9 +360,11 @@ void srot_or_permutation(uint64_t seed, long long epoch, int m, int *perm) {
 }
 
 /* Gap-adaptive sampling (Sec. 4.2, Alg. A.4): index i with probability
- * proportional to max(g_i, 0), by a linear scan of the cumulative sum. */
-static int or_sample_gap(const double *gst, int m, uint64_t seed, long long k) {
-    uint64_t u64 = srot_or_draw(seed, 3, (uint64_t)k);
+ * proportional to max(g_i, 0), by inverse transform of one uniform draw u64:
+ * with u = top 53 bits of u64 in [0, 1) and cum_i the running sum of the
+ * clamped gaps, the smallest i of positive weight with cum_i > u * total
+ * (a linear scan of the cumulative sum). All weights zero: uniform index. */
+int srot_or_sample_from(const double *gst, int m, uint64_t u64) {
     double total = 0.0;
     for (int i = 0; i < m; ++i) total = total + (gst[i] > 0.0 ? gst[i] : 0.0);
     if (!(total > 0.0)) return or_scale(u64, m);
@@ -355,6 +379,13 @@ static int or_sample_gap(const double *gst, int m, uint64_t seed, long long k) {
         if (cum > target && w > 0.0) return i;
     }
     return last_pos;
+}
+
+/* Uniform block index floor(u * m) of draw u64 (the uniform order, Sec. 3.1). */
+int srot_or_uniform_index(uint64_t u64, int m) { return or_scale(u64, m); }
+
+static int or_sample_gap(const double *gst, int m, uint64_t seed, long long k) {
+    return srot_or_sample_from(gst, m, srot_or_draw(seed, 3, (uint64_t)k));
 }
 
 static void or_global_gap_update(int m, int n, const double *C, const double *a,
@@ -379,9 +410,25 @@ static int or_solve_fw(int m, int n, const double *C, const double *a,
                        const double *b, const srot_or_opts *o, double *T,
                        double *hist, srot_or_result *res);
 
+int srot_or_solve_ex(int m, int n, const double *C, const double *a, const double *b,
+                     const srot_or_opts *o, double *T, int *trace_i, int *trace_j,
+                     long long trace_cap, double *hist, double *ga_hist, double *T_hist,
+                     srot_or_result *res);
+
 int srot_or_solve(int m, int n, const double *C, const double *a, const double *b,
                   const srot_or_opts *o, double *T, int *trace_i, int *trace_j,
                   long long trace_cap, double *hist, srot_or_result *res) {
+    return srot_or_solve_ex(m, n, C, a, b, o, T, trace_i, trace_j, trace_cap, hist, NULL, NULL, res);
+}
+
+/* As srot_or_solve, and optionally records, at the end of every epoch e
+ * (after that epoch's global gap update, if one is due): the sampling gaps
+ * g_i into ga_hist[e*m .. e*m+m) (gap-adaptive order only) and the plan into
+ * T_hist[e*m*n .. (e+1)*m*n). Both need max_epochs epochs of room. */
+int srot_or_solve_ex(int m, int n, const double *C, const double *a, const double *b,
+                     const srot_or_opts *o, double *T, int *trace_i, int *trace_j,
+                     long long trace_cap, double *hist, double *ga_hist, double *T_hist,
+                     srot_or_result *res) {
     memset(res, 0, sizeof(*res));
     if (m <= 0 || n <= 0 || o->gap_every < 1 || o->rho < 0.0) { res->status = -1; return -1; }
     if (o->variant != OR_BCFW && o->variant != OR_FW && o->step != OR_ELS) { res->status = -1; return -1; }
@@ -433,6 +480,10 @@ int srot_or_solve(int m, int n, const double *C, const double *a, const double *
         }
         if (status) break;
         if (ga && ((ep + 1) % gaM == 0)) or_global_gap_update(m, n, C, a, T, r, o->rho, gst);
+        if (ga && ga_hist)
+            for (int i = 0; i < m; ++i) ga_hist[(size_t)ep * m + i] = gst[i];
+        if (T_hist)
+            for (size_t e = 0; e < mn; ++e) T_hist[(size_t)ep * mn + e] = T[e];
         int last = (ep + 1 == o->max_epochs);
         if ((ep + 1) % o->gap_every == 0 || last) {
             srot_or_certificate(m, n, C, a, b, o->rho, T, cert, NULL, NULL);

@@ -530,6 +530,158 @@ def test_gap_adaptive_sampling_support(oracle_mod):
     assert drawn == {i for i in range(12) if i % 3}
 
 
+def _chi2_pvalue(counts, probs):
+    from scipy.stats import chi2
+    counts = np.asarray(counts, dtype=np.float64)
+    exp = counts.sum() * np.asarray(probs, dtype=np.float64)
+    keep = exp > 0
+    stat = float((((counts - exp) ** 2)[keep] / exp[keep]).sum())
+    return float(chi2.sf(stat, int(keep.sum()) - 1))
+
+
+def test_gap_adaptive_sampling_frequencies(oracle_mod):
+    """Alg. A.4 samples block i with probability g_i / sum_k g_k over the
+    clamped gaps max(g_i, 0). 10^5 draws of the sampling step, fed with
+    64-bit uniforms from numpy's own generator, match those probabilities by
+    a chi-square test; entries with zero or negative gap are never drawn; and
+    the same counts reject the plausible mistakes (weights g_i^2, or uniform
+    over the rows with a positive gap)."""
+    g = np.array([0.5, 0.0, -0.2, 1.0, 2.5, 0.0, 0.3, 1e-3, 0.7, -1e-9, 0.05])
+    rng = np.random.default_rng(2024)
+    draws = rng.integers(0, 2**64, size=100_000, dtype=np.uint64)
+    counts = np.zeros(len(g), dtype=np.int64)
+    for u in draws.tolist():
+        counts[oracle_mod.sample_from(g, u)] += 1
+    gp = np.maximum(g, 0.0)
+    assert counts[gp == 0].sum() == 0
+    assert _chi2_pvalue(counts, gp / gp.sum()) > 1e-4
+    assert _chi2_pvalue(counts, gp ** 2 / (gp ** 2).sum()) < 1e-12
+    pos = (gp > 0).astype(float)
+    assert _chi2_pvalue(counts, pos / pos.sum()) < 1e-12
+
+
+def test_gap_adaptive_sampling_interval_boundaries(oracle_mod):
+    """Inverse-transform sampling gives block i the half-open interval
+    [cum_{i-1}, cum_i) of u * total, so each block's probability is exactly
+    its weight's share: a draw landing on cum_i belongs to the next block of
+    positive weight, u = 0 to the first, the largest u to the last; with all
+    gaps zero the draw falls back to a uniform index."""
+    g = np.array([1.0, 1.0, 0.0, 2.0])  # total 4: cum = 1, 2, 2, 4
+    u = lambda x: int(x * 2**64)  # x a multiple of 2^-53 is represented exactly
+    assert oracle_mod.sample_from(g, 0) == 0
+    assert oracle_mod.sample_from(g, u(0.25) - 2048) == 0   # u just below 1/4
+    assert oracle_mod.sample_from(g, u(0.25)) == 1          # target 1.0 = cum_0
+    assert oracle_mod.sample_from(g, u(0.5) - 2048) == 1
+    assert oracle_mod.sample_from(g, u(0.5)) == 3           # target 2.0: block 2 has no weight
+    assert oracle_mod.sample_from(g, 2**64 - 1) == 3
+    assert oracle_mod.sample_from(np.array([0.0, 0.0, 3.0]), 0) == 2
+    z = np.zeros(5)
+    assert [oracle_mod.sample_from(z, -(-(k * 2**64) // 5)) for k in range(5)] == [0, 1, 2, 3, 4]
+
+
+def test_uniform_order_draws(oracle_mod):
+    """The uniform block order (Sec. 3.1) picks floor(u m): the index is the
+    j with u in [j 2^64 / m, (j+1) 2^64 / m), checked at both ends of every
+    interval for m = 10 and 7; the block frequencies of a uniform-order run
+    (m = 7, 21,000 updates) pass a chi-square test against 1/m."""
+    for m in (10, 7):
+        for j in range(m):
+            lo = -(-(j * 2**64) // m)          # smallest u with floor(u m / 2^64) = j
+            hi = -(-((j + 1) * 2**64) // m) - 1
+            assert oracle_mod.uniform_index(lo, m) == j
+            assert oracle_mod.uniform_index(hi, m) == j
+    X, Y, a, b, rho = random_problem(3, 7, 4, 2.0)
+    C = oracle_mod.cost(X, Y)
+    _, _, ti, _, _ = oracle_mod.solve(C, a, b, rho=rho, variant=oracle_mod.BCFW, step=oracle_mod.DEC,
+                                      order=oracle_mod.UNIFORM, seed=77, max_epochs=3000, trace=True)
+    counts = np.bincount(ti, minlength=7)
+    assert _chi2_pvalue(counts, np.full(7, 1 / 7)) > 1e-4
+
+
+def _gap_rows(oracle_mod, C, a, b, rho, T):
+    return oracle_mod.certificate(C, a, b, rho, T)["g_rows"]
+
+
+def test_gap_adaptive_global_update_cadence(oracle_mod):
+    """Alg. A.4 with inner updates (GAD-M, M = 3): the sampling gaps are all
+    recomputed after epochs 3 and 6 (and once at the start), and only then.
+    At those epochs every stored g_i equals the gap of row i at the epoch's
+    plan (the certificate, Thm 2); at the others, rows not drawn in the epoch
+    keep their previous value bit for bit, and the row drawn last holds its
+    gap after its own update (the post-update reading of the inner update).
+    The first draw of every epoch is the sampling step applied to the gaps
+    stored at the end of the epoch before."""
+    X, Y, a, b, rho = random_problem(21, 16, 12, 4.0)
+    C = oracle_mod.cost(X, Y)
+    m, M, E, seed = 16, 3, 7, 5
+    _, res, ti, _, _ = oracle_mod.solve(C, a, b, rho=rho, variant=oracle_mod.BCFW, step=oracle_mod.ELS,
+                                        order=oracle_mod.GAP, ga_M=M, seed=seed, max_epochs=E, trace=True,
+                                        epoch_state=True)
+    gh, Th = res["ga_hist"], res["T_hist"]
+    T0 = np.zeros((m, 12))
+    T0[:, 0] = a
+    prev = _gap_rows(oracle_mod, C, a, b, rho, T0)  # the exact update at k = 0
+    for e in range(E):
+        cert = _gap_rows(oracle_mod, C, a, b, rho, Th[e])
+        drawn = ti[e * m:(e + 1) * m]
+        assert drawn[0] == oracle_mod.sample_from(prev, oracle_mod.draw(seed, 3, e * m))
+        if (e + 1) % M == 0:
+            np.testing.assert_allclose(gh[e], cert, rtol=1e-10, atol=1e-15)
+        else:
+            rest = np.setdiff1d(np.arange(m), drawn)
+            assert len(rest) > 0
+            np.testing.assert_array_equal(gh[e][rest], prev[rest])
+            last = drawn[-1]
+            assert abs(gh[e][last] - cert[last]) <= 1e-10 * abs(cert[last]) + 1e-13 * np.abs(cert).max()
+            assert np.abs(gh[e] - cert).max() > 1e-9 * np.abs(cert).max()  # not a global update
+        prev = gh[e]
+
+
+def test_gap_adaptive_global_only_cadence(oracle_mod):
+    """BCFW-GAS (global updates only): the sampling gaps are recomputed after
+    every epoch and frozen within it, so every draw of epoch e is the
+    sampling step applied to the certificate's row gaps at the end of epoch
+    e - 1 (at T0 for the first epoch)."""
+    X, Y, a, b, rho = random_problem(22, 14, 10, 3.0)
+    C = oracle_mod.cost(X, Y)
+    m, E, seed = 14, 5, 9
+    _, res, ti, _, _ = oracle_mod.solve(C, a, b, rho=rho, variant=oracle_mod.BCFW, step=oracle_mod.ELS,
+                                        order=oracle_mod.GAP, ga_global_only=1, ga_M=4, seed=seed,
+                                        max_epochs=E, trace=True, epoch_state=True)
+    gh, Th = res["ga_hist"], res["T_hist"]
+    T0 = np.zeros((m, 10))
+    T0[:, 0] = a
+    prev = _gap_rows(oracle_mod, C, a, b, rho, T0)
+    for e in range(E):
+        for k in range(e * m, (e + 1) * m):
+            assert ti[k] == oracle_mod.sample_from(prev, oracle_mod.draw(seed, 3, k))
+        np.testing.assert_allclose(gh[e], _gap_rows(oracle_mod, C, a, b, rho, Th[e]), rtol=1e-10, atol=1e-15)
+        prev = gh[e]
+
+
+def test_apply_step_reproduces_block_steps(oracle_mod):
+    """Applying a block step's own decision to a copy of the state gives the
+    state that the block step produced, bit for bit, for every direction
+    (Frank-Wolfe, away with and without a drop, pairwise)."""
+    X, Y, a, b, rho = random_problem(31, 9, 11, 6.0)
+    C = oracle_mod.cost(X, Y)
+    rng = np.random.default_rng(0)
+    seen = set()
+    for variant in (oracle_mod.BCFW, oracle_mod.BCAFW, oracle_mod.BCPFW):
+        T = random_plan(rng, a, 11, sparse=True)
+        r = T.sum(0) - b
+        for k in range(60):
+            i = k % 9
+            T2, r2 = T.copy(), r.copy()
+            js, v, dr, gam = oracle_mod.block_step(C, a, T, r, i, k, variant=variant,
+                                                   step=oracle_mod.ELS, rho=rho)
+            oracle_mod.apply_step(a, T2, r2, i, dr, js, v, gam)
+            np.testing.assert_array_equal(T2, T)
+            np.testing.assert_array_equal(r2, r)
+            seen.add(dr)
+    assert seen >= {0, 1, 2}
+
+
 # ----------------------------------------------------------------------------
 # Colour-transfer tail (Sec. 5.1 projection, Sec. 5 metrics iii and iv)
 # ----------------------------------------------------------------------------
