@@ -7,6 +7,12 @@ envelope-theorem gradient at the returned plan:
     dX = 2 (diag(T 1) X - T Y),  dY = 2 (diag(T^T 1) Y - T^T X),  db = -rho (T^T 1 - b).
 The gradient with respect to the row marginal a is not provided (None).
 Only the multiplication by the incoming scalar gradient happens in torch.
+
+Backward reuses the very options struct the forward solve ran with (rho,
+precision, cost kind), so the adjoint is always taken for the problem that
+was solved: a library default for rho applies to both, and a cost the point
+gradients do not cover (the Euclidean cost) is refused by the library's own
+check in sr_ot_grad rather than given the squared-cost formula.
 """
 from __future__ import annotations
 
@@ -15,18 +21,30 @@ import torch
 from . import sr_ot as S
 
 
+def _solve_options(solve_kw, dtype):
+    """The sr_ot_options of a solve: `opts=` as given, else built from the
+    keyword arguments (precision defaulting to the tensors' dtype)."""
+    kw = dict(solve_kw)
+    o = kw.pop("opts", None)
+    if o is None:
+        kw.setdefault("precision", S.FP32 if dtype == torch.float32 else S.FP64)
+        o = S.options(**kw)
+    elif kw:
+        raise TypeError("pass either opts= or keyword options, not both")
+    return o
+
+
 class SemiRelaxedOT(torch.autograd.Function):
     """value = min_T <C(X, Y), T> + (rho/2) ||T^T 1 - b||^2, T >= 0, T 1 = a."""
 
     @staticmethod
     def forward(ctx, X, Y, b, a, handle, solve_kw):
-        kw = dict(solve_kw)
-        prec = kw.setdefault("precision", S.FP32 if X.dtype == torch.float32 else S.FP64)
+        o = _solve_options(solve_kw, X.dtype)
         m, n = X.shape[0], Y.shape[0]
         T = torch.zeros((m, n), dtype=X.dtype, device=X.device)
-        res = handle.solve(a, b, T, X=X.contiguous(), Y=Y.contiguous(), **kw)
+        res = handle.solve(a, b, T, X=X.contiguous(), Y=Y.contiguous(), opts=o)
         ctx.handle = handle
-        ctx.kw = {"rho": kw.get("rho", 1.0), "precision": prec}
+        ctx.opts = o
         ctx.save_for_backward(X, Y, b, T)
         ctx.result = res
         return torch.tensor(res["objective"], dtype=X.dtype, device=X.device)
@@ -41,7 +59,7 @@ class SemiRelaxedOT(torch.autograd.Function):
             want.append("dY")
         if ctx.needs_input_grad[2]:
             want.append("db")
-        out = ctx.handle.grad(T, X=X.contiguous(), Y=Y.contiguous(), b=b, want=tuple(want), **ctx.kw)
+        out = ctx.handle.grad(T, X=X.contiguous(), Y=Y.contiguous(), b=b, want=tuple(want), opts=ctx.opts)
         gX = out["dX"] * g if "dX" in out else None
         gY = out["dY"] * g if "dY" in out else None
         gb = out["db"] * g if "db" in out else None
@@ -49,7 +67,8 @@ class SemiRelaxedOT(torch.autograd.Function):
 
 
 def semi_relaxed_ot(X, Y, a, b, handle, **solve_kw):
-    """Differentiable optimal value (0-dim tensor) of one instance."""
+    """Differentiable optimal value (0-dim tensor) of one instance. Options as
+    keyword arguments of sr_ot.options, or one `opts=` struct."""
     return SemiRelaxedOT.apply(X, Y, b, a, handle, solve_kw)
 
 
@@ -60,12 +79,13 @@ class SemiRelaxedOTBatched(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, X, Y, b, a, sizes, offsets, handle, solve_kw):
+        o = _solve_options(solve_kw, X.dtype)
         total_T = sum(int(m) * int(n) for m, n in sizes)
         T = torch.zeros(total_T, dtype=X.dtype, device=X.device)
-        st, res = handle.solve_batched(X, Y, a, b, T, sizes, offsets, **solve_kw)
+        st, res = handle.solve_batched(X, Y, a, b, T, sizes, offsets, opts=o)
         ctx.handle = handle
         ctx.sizes, ctx.offsets = sizes, offsets
-        ctx.rho = solve_kw.get("rho", 1.0)
+        ctx.opts = o
         ctx.save_for_backward(X, Y, b, T)
         ctx.results = res
         vals = torch.tensor([r["objective"] for r in res], dtype=torch.float64)
@@ -74,8 +94,7 @@ class SemiRelaxedOTBatched(torch.autograd.Function):
     @staticmethod
     def backward(ctx, g):
         X, Y, b, T = ctx.saved_tensors
-        out = ctx.handle.grad_batched(X, Y, b, T, ctx.sizes, ctx.offsets, rho=ctx.rho,
-                                      precision=S.FP32)
+        out = ctx.handle.grad_batched(X, Y, b, T, ctx.sizes, ctx.offsets, opts=ctx.opts)
         ms = torch.tensor([int(s[0]) for s in ctx.sizes], device=g.device)
         ns = torch.tensor([int(s[1]) for s in ctx.sizes], device=g.device)
         # packed layouts follow the instance order with offsets as built by PackedBatch

@@ -238,3 +238,43 @@ def test_autograd_batched(S, h):
         oX = pb.offsets[k][0]
         sl = slice(oX, oX + 3 * insts[k].m)
         assert torch.allclose(X.grad[sl], (k + 1) * ref["dX"][sl], rtol=1e-6, atol=1e-9)
+
+
+def test_autograd_uses_the_solves_rho(S, h, oracle_mod):
+    """Without an explicit rho the forward solve runs the library default
+    (rho = 10); backward must differentiate that same problem, so db equals
+    -10 (T^T 1 - b) at the returned plan (the oracle's adjoint at rho = 10),
+    and an `opts=` struct carries its rho through as well."""
+    from paper_2103_05857_gb300.autograd import semi_relaxed_ot
+    inst = W.colour_instance(57, 40, 50, b_dirichlet=True).rounded()
+    a = dev(inst.a, torch.float32)
+    for kw in (dict(variant=S.BCPFW, step=S.ELS, tol_rel_gap=1e-7, max_epochs=20000),
+               dict(opts=S.options(variant=S.BCPFW, step=S.ELS, tol_rel_gap=1e-7, max_epochs=20000,
+                                   rho=3.0, precision=S.FP32))):
+        rho = 3.0 if "opts" in kw else 10.0
+        b = dev(inst.b, torch.float32).requires_grad_(True)
+        X = dev(inst.X, torch.float32).requires_grad_(True)
+        Y = dev(inst.Y, torch.float32)
+        val = semi_relaxed_ot(X, Y, a, b, h, **kw)
+        val.backward()
+        T = torch.zeros((inst.m, inst.n), dtype=torch.float32, device="cuda")
+        h.solve(a, b.detach(), T, X=X.detach(), Y=Y, precision=S.FP32, rho=rho, variant=S.BCPFW, step=S.ELS,
+                tol_rel_gap=1e-7, max_epochs=20000)
+        dXo, _, dbo = oracle_mod.adjoint(inst.X, inst.Y, inst.b, rho, host(T))
+        np.testing.assert_allclose(host(b.grad), dbo, rtol=1e-4, atol=1e-7 * rho)
+        np.testing.assert_allclose(host(X.grad), dXo, rtol=1e-4, atol=1e-6)
+
+
+def test_autograd_refuses_point_gradients_of_the_euclidean_cost(S, h):
+    """The adjoint formula for dX, dY is that of the squared cost; a forward
+    solve on the Euclidean cost must not be given it: backward carries the
+    solve's cost kind to sr_ot_grad, which refuses."""
+    from paper_2103_05857_gb300.autograd import semi_relaxed_ot
+    inst = W.colour_instance(58, 30, 40).rounded()
+    X = dev(inst.X, torch.float32).requires_grad_(True)
+    val = semi_relaxed_ot(X, dev(inst.Y, torch.float32), dev(inst.a, torch.float32), dev(inst.b, torch.float32),
+                          h, variant=S.BCPFW, step=S.ELS, tol_rel_gap=1e-6, max_epochs=5000,
+                          cost_kind=S.COST_EUCLIDEAN)
+    with pytest.raises(S.SrOtError) as e:
+        val.backward()
+    assert e.value.status == S.EUNSUPPORTED
