@@ -296,27 +296,33 @@ sr_ot_status sr_ot_cost_bf16(sr_ot_handle h, int m, int n, int d, const float *X
                              const float *Y, float *C);
 
 /*
- * The certificate of sr_ot_gap for callers that cannot allocate memory: code
- * inside a CUDA graph capture or under a caller-owned memory pool, embedded
- * runtimes that own every allocation, real-time loops where an allocation
- * (and the synchronisation it may imply) is not allowed. The paper has no
- * counterpart; this is an interface of this library only.
+ * The certificate of sr_ot_gap for callers that cannot allocate device
+ * memory where they need it: an application whose caching allocator has
+ * reserved the device's memory up front, a plug-in inside a host program
+ * that owns every allocation, a long-running service that must not fail on
+ * fragmentation after start-up. The paper has no counterpart; this is an
+ * interface of this library only.
  *
  * It takes no handle and allocates nothing: no cudaMalloc/cudaFree, no
  * pinned buffer. Its scratch is a fixed 4 MiB array compiled into the
  * library as a static __device__ variable, present on every device that
- * loads the library until the process exits. It fits any m with n up to
- * 208,000 columns; larger n fail with SR_OT_EUNSUPPORTED. The cost must be
- * C or d = 3 points (squared cost only: with SR_OT_COST_EUCLIDEAN pass the
- * cost as C, else SR_OT_EUNSUPPORTED); precision SR_OT_FP64 or SR_OT_FP32.
+ * loads the library until the process exits. Every n <= 207,552 fits for
+ * any m (smaller m leave room for slightly larger n); sizes that do not fit
+ * fail with SR_OT_EUNSUPPORTED and a message naming the bytes needed. The
+ * cost must be C or d = 3 points (squared cost only: with
+ * SR_OT_COST_EUCLIDEAN pass the cost as C, else SR_OT_EUNSUPPORTED);
+ * precision SR_OT_FP64 or SR_OT_FP32.
  *
  * `device` must be the device the pointers live on; `cuda_stream` as in
- * sr_ot_create. The first call on a device looks up the array's device
+ * sr_ot_create. The calling thread's current device is the same before and
+ * after the call. The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress); make that first call before any stream
- * capture. Every call reuses the same array and leaves its last contents
- * there, so calls whose kernels overlap on the GPU race: serialise them.
- * Arguments, outputs (res on the host, g_rows optional device doubles) and
- * errors are as for sr_ot_gap; the error message is sr_ot_last_error(NULL).
+ * capture. The call synchronises `cuda_stream` before it returns (it reads
+ * the input checks and the certificate back to the host). Every call
+ * reuses the same array and leaves its last contents there, so calls whose
+ * kernels overlap on the GPU race: serialise them. Arguments, outputs (res
+ * on the host, g_rows optional device doubles) and errors are as for
+ * sr_ot_gap; the error message is sr_ot_last_error(NULL).
  */
 sr_ot_status sr_ot_gap_noalloc(int device, void *cuda_stream, const sr_ot_options *opts, int m,
                                int n, int d, const void *C, const void *X, const void *Y,

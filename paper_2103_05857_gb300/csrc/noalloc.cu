@@ -1,20 +1,27 @@
 // noalloc.cu -- sr_ot_gap_noalloc: the duality-gap certificate without any
 // memory allocation.
 //
-// Some callers cannot allocate device memory: code running inside a CUDA
-// graph capture or a custom memory pool that must not be disturbed, embedded
-// runtimes that own every allocation themselves, or real-time loops where an
-// allocation (and the implicit synchronisation it can cause) is forbidden.
-// This entry point serves them: it takes no handle (creating one allocates a
-// pinned result buffer) and runs the certificate kernels on a fixed scratch
-// area that lives in this file as a static __device__ array, so it is part
-// of the module image and exists on every device that loads the library,
-// until the process exits.
+// Some callers cannot allocate device memory at the point where they want a
+// certificate: an application whose caching allocator has reserved the
+// device's memory up front, a plug-in embedded in a host program that owns
+// every allocation, a long-running service that must not fail on
+// fragmentation after start-up. This entry point serves them: it takes no
+// handle (creating one allocates a workspace and a pinned result buffer) and
+// runs the certificate kernels on a fixed scratch area that lives in this
+// file as a static __device__ array, so it is part of the module image and
+// exists on every device that loads the library, until the process exits.
+// The call synchronises its stream before it returns (it reads the input
+// checks and the certificate back to the host).
 //
-// Limits: scratch is kNoAllocScratchBytes; sizes whose certificate work area
-// does not fit are rejected with SR_OT_EUNSUPPORTED. The cost must be given
-// (C) or come from d = 3 points (no materialised cost for other d, no BF16
-// tensor-core cost).
+// Limits: scratch is kNoAllocScratchBytes. The certificate's column sums are
+// taken in row chunks; when the default chunking does not fit, one chunk is
+// used (the column sums are then summed over all rows in one pass, which is
+// slower but needs n doubles only). Sizes that do not fit even then are
+// rejected with SR_OT_EUNSUPPORTED. With 4 MiB every n <= 207,552 fits for
+// any m (the bound is reached for m >= 9,721, where the row pass uses its
+// largest grid); smaller m leave room for slightly larger n.
+// The cost must be given (C) or come from d = 3 points (no materialised cost
+// for other d, no BF16 tensor-core cost).
 //
 // Sharing: every call uses the same array and leaves the last call's values
 // in it. Calls whose kernels overlap on the GPU (different streams or
@@ -75,6 +82,19 @@ sr_ot_status scratch_address(int device, unsigned char **out) {
     return SR_OT_OK;
 }
 
+size_t rounded(size_t bytes);
+
+// Bytes of scratch that a certificate plan `w` of an m x n instance takes.
+size_t scratch_need(const srot::CertWork &w, int n);
+
+// Restores the calling thread's current device when it goes out of scope.
+struct DeviceGuard {
+    int saved = -1;
+    ~DeviceGuard() {
+        if (saved >= 0) cudaSetDevice(saved);
+    }
+};
+
 template <typename T>
 T *carve(unsigned char *&cur, size_t count) {
     T *p = reinterpret_cast<T *>(cur);
@@ -83,6 +103,13 @@ T *carve(unsigned char *&cur, size_t count) {
 }
 
 size_t rounded(size_t bytes) { return ((bytes + 255) / 256) * 256; }
+
+size_t scratch_need(const srot::CertWork &w, int n) {
+    return rounded((size_t)w.nchunks * n * sizeof(double)) + rounded((size_t)n * sizeof(double)) +
+           rounded((size_t)n * sizeof(float)) + rounded((size_t)2 * w.ncolblocks * sizeof(double)) +
+           rounded((size_t)3 * w.nrowblocks * sizeof(double)) + rounded(srot::kCertCount * sizeof(double)) +
+           rounded(4 * sizeof(int));
+}
 
 template <typename Real>
 __global__ void k_noalloc_check(int m, int n, const Real *a, const Real *b, const Real *src,
@@ -129,10 +156,12 @@ sr_ot_status gap_noalloc(int device, cudaStream_t st, const sr_ot_options *o, in
 
     CertWork w;
     cert_work_shape(m, n, &w.nchunks, &w.rows_per_chunk, &w.ncolblocks, &w.nrowblocks);
-    const size_t need = rounded((size_t)w.nchunks * n * sizeof(double)) + rounded((size_t)n * sizeof(double)) +
-                        rounded((size_t)n * sizeof(float)) + rounded((size_t)2 * w.ncolblocks * sizeof(double)) +
-                        rounded((size_t)3 * w.nrowblocks * sizeof(double)) +
-                        rounded(kCertCount * sizeof(double)) + rounded(4 * sizeof(int));
+    if (scratch_need(w, n) > kNoAllocScratchBytes) {
+        // one row chunk: the column partials shrink to n doubles
+        w.nchunks = 1;
+        w.rows_per_chunk = std::max(8, m);
+    }
+    const size_t need = scratch_need(w, n);
     if (need > kNoAllocScratchBytes)
         return nfail(SR_OT_EUNSUPPORTED,
                      "m = %d, n = %d needs %zu bytes of certificate scratch; the no-allocation entry point has %zu",
@@ -212,9 +241,13 @@ sr_ot_status sr_ot_gap_noalloc(int device, void *cuda_stream, const sr_ot_option
         cudaGetLastError();
         return nfail(SR_OT_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
     }
-    if (cur != device && (e = cudaSetDevice(device)) != cudaSuccess) {
-        cudaGetLastError();
-        return nfail(SR_OT_ECUDA, "cudaSetDevice(%d): %s", device, cudaGetErrorString(e));
+    DeviceGuard guard;  // the caller's current device is restored on every return
+    if (cur != device) {
+        if ((e = cudaSetDevice(device)) != cudaSuccess) {
+            cudaGetLastError();
+            return nfail(SR_OT_ECUDA, "cudaSetDevice(%d): %s", device, cudaGetErrorString(e));
+        }
+        guard.saved = cur;
     }
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     if (opts->precision == SR_OT_FP64)
