@@ -42,8 +42,7 @@ sys.path.insert(0, ROOT)
 UNIT = "block-updates/s"
 VARIANTS = {"BCFW": 0, "BCAFW": 1, "BCPFW": 2}
 L2_FLUSH_BYTES = 256 << 20
-SMS = 152                 # GB300: 2 dies x 76 SMs
-FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM
+FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (Blackwell)
 FLOPS_PER_GRAD = 8        # d = 3 cost (3 sub, 3 mul/fma) + residual add + compare
 BATCH_WORKLOADS = ("colour_batch512", "colour_batch64_2048")
 
@@ -126,10 +125,16 @@ def measured_peaks():
             "sm_max_mhz": 2070.0}, "fallback"
 
 
+def sm_count():
+    """Streaming multiprocessors of the current device, as the device reports them."""
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+
+
 def fp32_peak_tflops(peaks):
     """CUDA-core FP32 peak from unit counts and the maximum SM clock
-    (152 SMs x 128 lanes x 2 flops per FMA x clock)."""
-    return SMS * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    (SMs x 128 lanes x 2 flops per FMA x clock)."""
+    return sm_count() * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
 
 
 class ClockSampler:
@@ -369,7 +374,7 @@ def alu_roofline(flops, avg_ms, peaks, peak_src, kernel, extra=None):
     peak = fp32_peak_tflops(peaks)
     achieved = flops / (avg_ms / 1e3) / 1e12
     r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-         "traffic": None, "peak_source": f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+         "traffic": None, "peak_source": f"derived: {sm_count()} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                         f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({peak_src} clock)",
          "kernel": kernel, "avg_launch_ms": avg_ms}
     if extra:
