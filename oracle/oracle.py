@@ -259,3 +259,38 @@ def transfer_stats(a, b, T):
     col_err = float(np.linalg.norm(T.sum(axis=0) - b))
     sparsity = float(np.count_nonzero(T == 0.0)) / T.size
     return {"e_c": row_err + col_err, "row_err": row_err, "col_err": col_err, "sparsity": sparsity}
+
+
+def transport_lp(C, a, b):
+    """The optimal plan T*_LP of the unrelaxed, unregularised transport
+    problem (Sec. 2: min <C, T> over T >= 0, T 1 = a, T^T 1 = b), the
+    reference plan of the evaluation metrics (v) and (vi) of Sec. 5. The
+    linear program is solved by a library LP solver (scipy's HiGHS) as one
+    step. Both marginals must carry the same total mass; b is rescaled to
+    a's total first (float32-rounded weights differ in the last bits)."""
+    import scipy.optimize as so
+    import scipy.sparse as sp
+    C, a, b = _f64(C), _f64(a), _f64(b)
+    m, n = C.shape
+    b = b * (a.sum() / b.sum())
+    rows = sp.kron(sp.eye(m), np.ones((1, n)))
+    cols = sp.kron(np.ones((1, m)), sp.eye(n))
+    A = sp.vstack([rows, cols]).tocsr()
+    res = so.linprog(C.ravel(), A_eq=A, b_eq=np.concatenate([a, b]), bounds=(0, None), method="highs")
+    if res.status != 0:
+        raise RuntimeError(f"transport LP failed: {res.message}")
+    return np.maximum(res.x.reshape(m, n), 0.0)
+
+
+def lp_metrics(C, T, T_lp):
+    """Evaluation metrics (v) and (vi) of Sec. 5 against the LP plan T*_LP:
+    the transport matrix error e_m = ||T - T*_LP|| / ||T*_LP|| (Frobenius
+    norm; the paper does not name the norm) and the value error
+    e_v = |<T, C> - <T*_LP, C>| / |<T*_LP, C>|."""
+    C, T, L = _f64(C), _f64(T), _f64(T_lp)
+    diff = float(np.sqrt(((T - L) ** 2).sum()))
+    lnorm = float(np.sqrt((L ** 2).sum()))
+    value, lp_value = float((T * C).sum()), float((L * C).sum())
+    return {"e_m": diff / lnorm, "e_v": abs(value - lp_value) / abs(lp_value), "diff_norm": diff,
+            "lp_norm": lnorm, "value": value, "lp_value": lp_value}
+

@@ -748,3 +748,117 @@ def test_euclidean_cost_pins(oracle_mod):
         assert np.all(E <= XZ[:, k:k + 1] + ZY[k:k + 1, :] + 1e-15)
     P = oracle_mod.cost(np.array([[0.0, 0.0, 0.0]]), np.array([[3.0, 4.0, 0.0]]), squared=False)
     assert P[0, 0] == 5.0
+
+
+# ----------------------------------------------------------------------------
+# Reference plan of the LP-based metrics (Sec. 5, metrics v and vi)
+# ----------------------------------------------------------------------------
+def _lp_vertices(C, a, b):
+    """Brute force over the vertices of the transportation polytope: every
+    set of m + n - 1 cells whose equality system (row sums a, column sums b)
+    has a unique nonnegative solution is a basic feasible solution; return
+    the cheapest one and its cost."""
+    m, n = C.shape
+    cells = [(i, j) for i in range(m) for j in range(n)]
+    best, best_T = np.inf, None
+    for basis in itertools.combinations(range(m * n), m + n - 1):
+        A = np.zeros((m + n, m + n - 1))
+        for k, cidx in enumerate(basis):
+            i, j = cells[cidx]
+            A[i, k] = 1.0
+            A[m + j, k] = 1.0
+        if np.linalg.matrix_rank(A) < m + n - 1:
+            continue
+        x, *_ = np.linalg.lstsq(A, np.concatenate([a, b]), rcond=None)
+        if np.abs(A @ x - np.concatenate([a, b])).max() > 1e-12 or x.min() < -1e-13:
+            continue
+        T = np.zeros((m, n))
+        for k, cidx in enumerate(basis):
+            T[cells[cidx]] = x[k]
+        v = float((T * C).sum())
+        if v < best - 1e-14:
+            best, best_T = v, T
+    return best, best_T
+
+
+@pytest.mark.parametrize("seed,m,n", [(1, 2, 3), (2, 3, 3), (3, 3, 2), (4, 1, 4)])
+def test_transport_lp_is_the_cheapest_vertex(oracle_mod, seed, m, n):
+    """T*_LP is the cheapest vertex of the transportation polytope
+    (enumerated by brute force on tiny sizes) and is feasible."""
+    rng = np.random.default_rng(seed)
+    C = rng.random((m, n))
+    a = rng.random(m) + 0.1
+    a /= a.sum()
+    b = rng.random(n) + 0.1
+    b /= b.sum()
+    L = oracle_mod.transport_lp(C, a, b)
+    v, Tv = _lp_vertices(C, a, b)
+    assert abs(float((L * C).sum()) - v) <= 1e-12
+    np.testing.assert_allclose(L, Tv, atol=1e-12)
+    np.testing.assert_allclose(L.sum(1), a, atol=1e-12)
+    np.testing.assert_allclose(L.sum(0), b, atol=1e-12)
+    assert L.min() >= 0.0
+
+
+def test_transport_lp_dual_certificate(oracle_mod):
+    """Optimality of T*_LP without the solver: potentials u, v solved from
+    u_i + v_j = C_ij on its support (a spanning tree of cells for a
+    non-degenerate problem) are dual feasible, u_i + v_j <= C_ij everywhere,
+    and <a, u> + <b, v> = <C, T*_LP> (LP duality)."""
+    rng = np.random.default_rng(9)
+    m, n = 7, 9
+    C = rng.random((m, n))
+    a = rng.random(m) + 0.1
+    a /= a.sum()
+    b = rng.random(n) + 0.1
+    b /= b.sum()
+    L = oracle_mod.transport_lp(C, a, b)
+    supp = np.argwhere(L > 1e-14)
+    assert len(supp) == m + n - 1  # non-degenerate basis
+    A = np.zeros((len(supp) + 1, m + n))
+    rhs = np.zeros(len(supp) + 1)
+    for k, (i, j) in enumerate(supp):
+        A[k, i] = 1.0
+        A[k, m + j] = 1.0
+        rhs[k] = C[i, j]
+    A[-1, 0] = 1.0  # fix the free constant: u_0 = 0
+    uv = np.linalg.solve(A, rhs)
+    u, v = uv[:m], uv[m:]
+    assert (u[:, None] + v[None, :] - C).max() <= 1e-12
+    assert abs(a @ u + b @ v - float((L * C).sum())) <= 1e-12
+
+
+def test_semi_relaxed_value_tends_to_the_lp_value(oracle_mod):
+    """The semi-relaxed problem penalises the column marginal with weight
+    rho / 2 (Sec. 3, eq. 5 with rho = 1/lambda): its optimal value increases
+    with rho and approaches the LP value from below as rho grows, at rate
+    O(1/rho)."""
+    X, Y, a, b, _ = random_problem(5, 4, 5, 1.0)
+    C = oracle_mod.cost(X, Y)
+    lp = float((oracle_mod.transport_lp(C, a, b) * C).sum())
+    vals = []
+    for rho in (1.0, 10.0, 100.0, 1000.0):
+        _, r, *_ = oracle_mod.solve(C, a, b, rho=rho, variant=oracle_mod.BCPFW, step=oracle_mod.ELS,
+                                    max_epochs=200000, tol_rel_gap=1e-13, gap_every=10)
+        vals.append(r["f"])
+    assert all(x < y for x, y in zip(vals, vals[1:]))
+    assert vals[-1] <= lp + 1e-12
+    gaps = [lp - v for v in vals]
+    assert gaps[-1] <= 1.5 * gaps[-2] / 10.0 and gaps[-1] >= 0.0
+
+
+def test_lp_metrics_closed_forms(oracle_mod):
+    """e_m and e_v of Sec. 5 on plans with known answers: the product plan
+    (all entries 1/9) against the diagonal plan (1/3 on the diagonal) has
+    ||T - L|| = sqrt(18)/9 and ||L|| = sqrt(3)/3, so e_m = sqrt(6)/3; with
+    C = [[1,2,3],[2,1,2],[3,2,1]] the values are <L, C> = 1 and
+    <T, C> = 17/9, so e_v = 8/9; a plan against itself gives 0."""
+    L = np.eye(3) / 3.0
+    T = np.full((3, 3), 1.0 / 9.0)
+    C = np.array([[1.0, 2, 3], [2, 1, 2], [3, 2, 1]])
+    r = oracle_mod.lp_metrics(C, T, L)
+    assert abs(r["e_m"] - np.sqrt(6.0) / 3.0) <= 1e-15
+    assert abs(r["e_v"] - 8.0 / 9.0) <= 1e-15
+    r0 = oracle_mod.lp_metrics(C, L, L)
+    assert r0["e_m"] == 0.0 and r0["e_v"] == 0.0
+
