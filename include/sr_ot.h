@@ -87,8 +87,14 @@ typedef enum {
     SR_OT_EPOCH_TWO_PHASE = 1,    /* the next row's LMO waits for the current update   */
     SR_OT_EPOCH_PIPELINED = 2,    /* the next row's LMO and away vertex overlap the
                                      current update (two alternating control warps)    */
-    SR_OT_EPOCH_SPECULATIVE = 3   /* LMOs of the next rows taken ahead against an older
-                                     residual and repaired at the changed columns      */
+    SR_OT_EPOCH_SPECULATIVE = 3,  /* LMOs of the next rows taken ahead against an older
+                                     residual and repaired at the changed columns;
+                                     three chain warps take the updates in turn        */
+    SR_OT_EPOCH_SPECULATIVE_ONE_CHAIN = 4, /* the same, one chain warp takes every update
+                                     (no hand-over between chain warps)                */
+    SR_OT_EPOCH_SPECULATIVE_SPLIT = 5  /* the same, two preparer warps take the look-ahead
+                                     of each update and one decider warp decides and
+                                     applies every update                             */
 } sr_ot_epoch_kernel;
 
 typedef struct {
@@ -129,6 +135,23 @@ typedef struct {
                                  dY of sr_ot_grad, the BF16 cost and the points
                                  form of sr_ot_gap_noalloc take the squared
                                  cost only (EUNSUPPORTED otherwise).           */
+    long long spin_limit;     /* device waits of the speculative epoch kernel
+                                 (mbarrier hand-overs between its warps, and
+                                 start_gate) give up after this many probes:
+                                 the kernel then stops, records the timeout and
+                                 the call returns SR_OT_ETIMEOUT with the handle
+                                 still usable. 0 = the default, 2^26 probes
+                                 (well above any legitimate wait). >= 0.       */
+    int batch_warm_start;     /* sr_ot_solve_batched only: 1 = every instance
+                                 starts from the feasible plan the caller left
+                                 in T (rows summing to a), 0 = from T0
+                                 (sr_ot_solve has its own warm_start argument) */
+    const int *start_gate;    /* optional DEVICE int: the speculative epoch
+                                 kernel waits (bounded by spin_limit) until it
+                                 reads non-zero there before its first update;
+                                 NULL = no gate. It lets the timeout path be
+                                 exercised: a gate that nothing opens makes the
+                                 call return SR_OT_ETIMEOUT.                   */
 } sr_ot_options;
 
 typedef struct {
@@ -146,7 +169,7 @@ typedef struct {
 
 /* Fill *opts with defaults: BCFW, cyclic, DEC, FP32, rho = 10, tol 0,
  * max_epochs 100, gap_every 1, refresh_every 1, ga_M 1, seed 0, no trace,
- * dense_only 0. */
+ * dense_only 0, spin_limit 0 (default bound), no start gate. */
 void sr_ot_default_options(sr_ot_options *opts);
 
 /* Create a handle bound to CUDA device `device` and stream `cuda_stream`
@@ -194,7 +217,9 @@ sr_ot_status sr_ot_solve(sr_ot_handle h, const sr_ot_options *opts, int m, int n
  * times tol_rel_gap (a certificate reads the instance's whole plan).
  * m[k], n[k]: HOST arrays of per-instance sizes. off_X, off_Y, off_a, off_b,
  * off_T: HOST arrays of per-instance ELEMENT offsets into the packed device
- * buffers X, Y, a, b, T. Each instance starts from T0 = (a_i e_0).
+ * buffers X, Y, a, b, T. Each instance starts from T0 = (a_i e_0), or with
+ * opts->batch_warm_start from the plan in T (the tile autotuner then does not
+ * run: it would write the plans).
  * res: HOST array of `batch` results; each instance has its own status.
  */
 sr_ot_status sr_ot_solve_batched(sr_ot_handle h, const sr_ot_options *opts, int batch,
@@ -275,6 +300,36 @@ sr_ot_status sr_ot_transfer_batched(sr_ot_handle h, const sr_ot_options *opts, i
                                     sr_ot_transfer_stats *stats);
 
 /*
+ * Evaluation metrics (v) and (vi) of Sec. 5: the distance of a plan T from a
+ * reference plan T_lp, which the paper takes as T*_LP, the optimal plan of
+ * the unrelaxed transport problem (min <C, T> over T >= 0, T 1 = a,
+ * T^T 1 = b; the caller computes it with any exact OT solver):
+ *   e_m = ||T - T_lp||_F / ||T_lp||_F,
+ *   e_v = |<T, C> - <T_lp, C>| / |<T_lp, C>|.
+ * Cost as in sr_ot_gap: exactly one of C (m x n) or d = 3 points X, Y (the
+ * squared cost, or the Euclidean one with SR_OT_COST_EUCLIDEAN, evaluated on
+ * the fly as the solver evaluates it); other d: pass C (SR_OT_EUNSUPPORTED).
+ * DEVICE pointers, row-major, FP64 for SR_OT_FP64 and FP32 otherwise. One
+ * pass over T and T_lp; FP32 products are summed with compensation per lane
+ * and in FP64 across lanes, in a fixed order (deterministic). Uses
+ * opts->precision and opts->cost_kind only. out: HOST struct, filled when the
+ * call returns. Errors: EINVAL (NULL pointers, sizes, both or neither cost
+ * source), EUNSUPPORTED (points with d != 3), ENOMEM, ECUDA.
+ */
+typedef struct {
+    double e_m;        /* ||T - T_lp||_F / ||T_lp||_F                        */
+    double e_v;        /* |<T, C> - <T_lp, C>| / |<T_lp, C>|                 */
+    double diff_norm;  /* ||T - T_lp||_F                                     */
+    double lp_norm;    /* ||T_lp||_F                                         */
+    double value;      /* <T, C>                                             */
+    double lp_value;   /* <T_lp, C>                                          */
+} sr_ot_lp_metrics_result;
+
+sr_ot_status sr_ot_lp_metrics(sr_ot_handle h, const sr_ot_options *opts, int m, int n, int d,
+                              const void *C, const void *X, const void *Y, const void *T,
+                              const void *T_lp, sr_ot_lp_metrics_result *out);
+
+/*
  * Certificate of any feasible plan T (Thm 2): objective f, linearisation
  * duality gap g = sum_i g_i (eq. 11) and Lagrangian dual w = f - g.
  * Cost as in sr_ot_solve. If g_rows is non-NULL it receives the per-row
@@ -339,12 +394,26 @@ sr_ot_status sr_ot_gap_noalloc(int device, void *cuda_stream, const sr_ot_option
  *   SR_OT_PROF_BATCH  batched persistent solves
  *   SR_OT_PROF_GRAD   adjoint kernels
  *   SR_OT_PROF_COST   cost materialisation (plain or BF16 tensor-core GEMM)
+ *   SR_OT_PROF_METRICS  the pass of sr_ot_lp_metrics
  * sr_ot_profile_read returns the total milliseconds and the number of timed
  * launch groups of one class; sr_ot_profile_enable(h, 1) also resets them.
  */
 enum { SR_OT_PROF_EPOCH = 0, SR_OT_PROF_CERT = 1, SR_OT_PROF_BATCH = 2, SR_OT_PROF_GRAD = 3,
-       SR_OT_PROF_COST = 4, SR_OT_PROF_KINDS = 5 };
+       SR_OT_PROF_COST = 4, SR_OT_PROF_METRICS = 5, SR_OT_PROF_KINDS = 6 };
 long long sr_ot_launch_count(sr_ot_handle h);
+
+/*
+ * Latency floor of the speculative epoch kernel's update chain (observability,
+ * not in the paper). One CTA runs `updates` (>= 1) dependent updates that keep
+ * only what the solver's chain keeps: read the residual at the two columns the
+ * previous update changed, compare-select, form the pairwise step, write the
+ * residual of two columns, publish; with `chain_warps` = 3 the updates rotate
+ * over three warps that hand over through mbarriers as the solver's do, with
+ * 1 one warp runs them all. *ns_per_update receives the device time per update
+ * (CUDA events on the handle's stream around the launch). Errors: EINVAL
+ * (chain_warps not 1 or 3, updates < 1, NULL output), ETIMEOUT, ECUDA.
+ */
+sr_ot_status sr_ot_profile_chain_floor(sr_ot_handle h, int chain_warps, int updates, double *ns_per_update);
 sr_ot_status sr_ot_profile_enable(sr_ot_handle h, int enable);
 sr_ot_status sr_ot_profile_read(sr_ot_handle h, int kind, double *total_ms, long long *groups);
 

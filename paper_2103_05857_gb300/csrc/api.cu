@@ -24,7 +24,7 @@ namespace {
 enum WsSlot {
     WS_Q = 0, WS_PARTIAL, WS_R64, WS_RQ32, WS_COLPART, WS_ROWPART, WS_CERT, WS_PERM, WS_PERMKEY,
     WS_PERMIDX, WS_GSTORE, WS_STATUS, WS_COST, WS_CHECK, WS_SCRATCH, WS_ATOMS, WS_B_INST,
-    WS_B_QUEUE, WS_B_HEAD, WS_B_RES, WS_B_ATOMS, WS_B_BAD, WS_ADJ_INST, WS_ADJ_CP, WS_ADJ_RP, WS_TR_PART, WS_TR_ZERO, WS_TR_STATS, WS_FW_JS, WS_FW_UPART, WS_BF16, WS_BF16_ERR, WS_COUNT
+    WS_B_QUEUE, WS_B_HEAD, WS_B_RES, WS_B_ATOMS, WS_B_BAD, WS_ADJ_INST, WS_ADJ_CP, WS_ADJ_RP, WS_TR_PART, WS_TR_ZERO, WS_TR_STATS, WS_FW_JS, WS_FW_UPART, WS_BF16, WS_BF16_ERR, WS_MET, WS_COST32, WS_FLOOR, WS_COUNT
 };
 
 struct DevBuf {
@@ -58,8 +58,8 @@ struct sr_ot_ctx {
     bool prof = false;
     std::vector<ProfPair> pending;
     std::vector<cudaEvent_t> event_pool;
-    double prof_ms[SR_OT_PROF_KINDS] = {0, 0, 0, 0, 0};
-    long long prof_groups[SR_OT_PROF_KINDS] = {0, 0, 0, 0, 0};
+    double prof_ms[SR_OT_PROF_KINDS] = {};
+    long long prof_groups[SR_OT_PROF_KINDS] = {};
     // batched solves: side streams for concurrent tile launches, the tile
     // chosen per size bucket by the autotuner, captured graphs per shape set
     cudaStream_t side[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -242,10 +242,11 @@ sr_ot_status check_opts(sr_ot_handle h, const sr_ot_options *o) {
     if ((o->variant == SR_OT_BCAFW || o->variant == SR_OT_BCPFW) && o->step != SR_OT_ELS)
         return fail(h, SR_OT_EINVAL, "away and pairwise steps need the exact line search (SR_OT_ELS)");
     if (o->trace && o->trace_capacity < 0) return fail(h, SR_OT_EINVAL, "trace_capacity must be >= 0");
-    if (o->epoch_kernel < SR_OT_EPOCH_AUTO || o->epoch_kernel > SR_OT_EPOCH_SPECULATIVE)
+    if (o->epoch_kernel < SR_OT_EPOCH_AUTO || o->epoch_kernel > SR_OT_EPOCH_SPECULATIVE_SPLIT)
         return fail(h, SR_OT_EINVAL, "unknown epoch_kernel %d", o->epoch_kernel);
     if (o->cost_kind != SR_OT_COST_SQUARED && o->cost_kind != SR_OT_COST_EUCLIDEAN)
         return fail(h, SR_OT_EINVAL, "unknown cost_kind %d", o->cost_kind);
+    if (o->spin_limit < 0) return fail(h, SR_OT_EINVAL, "spin_limit must be >= 0");
     return SR_OT_OK;
 }
 
@@ -434,6 +435,37 @@ sr_ot_status solve_impl(sr_ot_handle h, const sr_ot_options *o, int m, int n, in
     if (n > epoch_max_n(fp64))
         return fail(h, SR_OT_EUNSUPPORTED, "n = %d exceeds the single-instance limit %d for this precision",
                     n, epoch_max_n(fp64));
+    // FP64 BCFW on rows of width <= 512 runs on the single-warp kernel, which
+    // streams the cost row: d = 3 points are turned into C once (the same
+    // FP64 operations in the same order as the point cost, so the values are
+    // identical) and the whole solve, certificate included, reads C.
+    bool f64w = false;
+    float *c32 = nullptr;
+    if constexpr (std::is_same<Real, double>::value) {
+        if (o->variant == SR_OT_BCFW && !ga && n <= epoch_f64w_max_n() &&
+            (size_t)m * n * (sizeof(double) + sizeof(float)) <= ((size_t)1 << 30)) {
+            if (in.cost_mode == kCostPts3) {
+                double *Cw;
+                if ((st = ws_typed(h, WS_COST, (size_t)m * n, &Cw))) return st;
+                {
+                    ProfScope ps(h, SR_OT_PROF_COST);
+                    launch_cost_plain<double>(m, n, 3, in.X, in.Y, Cw, h->stream, false);
+                }
+                h->launches += 1;
+                CKL(h);
+                in.C = Cw;
+                in.cost_mode = kCostGiven;
+            }
+            if (in.cost_mode == kCostGiven) {
+                // its FP32 rounding, for the kernel's argmin screen
+                if ((st = ws_typed(h, WS_COST32, (size_t)m * n, &c32))) return st;
+                launch_round_cost(in.C, c32, (size_t)m * n, h->stream);
+                h->launches += 1;
+                CKL(h);
+                f64w = true;
+            }
+        }
+    }
     Real *T = static_cast<Real *>(T_inout);
     double *q;
     int *dstat_d;
@@ -508,6 +540,9 @@ sr_ot_status solve_impl(sr_ot_handle h, const sr_ot_options *o, int m, int n, in
     A.atoms = atoms;
     A.resume = nullptr;
     A.resume_in = nullptr;
+    A.spin_limit = o->spin_limit;
+    A.gate = o->start_gate;
+    A.C32 = c32;
     {
         const size_t rb = (size_t)n * sizeof(Real);
         bool v = (rb % 16 == 0) && ((uintptr_t)T % 16 == 0);
@@ -536,7 +571,12 @@ sr_ot_status solve_impl(sr_ot_handle h, const sr_ot_options *o, int m, int n, in
                     As.resume = dstat_d + 1;
                     const int ek = o->epoch_kernel;
                     bool ran = false;
-                    if (ek == SR_OT_EPOCH_AUTO || ek == SR_OT_EPOCH_SPECULATIVE) ran = launch_epoch_spec(As, h->stream);
+                    if (ek == SR_OT_EPOCH_AUTO || ek == SR_OT_EPOCH_SPECULATIVE)
+                        ran = launch_epoch_spec(As, h->stream, 3);
+                    else if (ek == SR_OT_EPOCH_SPECULATIVE_ONE_CHAIN)
+                        ran = launch_epoch_spec(As, h->stream, 1);
+                    else if (ek == SR_OT_EPOCH_SPECULATIVE_SPLIT)
+                        ran = launch_epoch_spec(As, h->stream, kSpecChainSplit);
                     if (!ran && ek != SR_OT_EPOCH_TWO_PHASE) ran = launch_epoch_pipe(As, h->stream);
                     if (!ran) launch_epoch_sparse(As, h->stream);
                     EpochArgs<float> Ad = A;
@@ -546,6 +586,8 @@ sr_ot_status solve_impl(sr_ot_handle h, const sr_ot_options *o, int m, int n, in
                 } else {
                     launch_epoch<Real>(A, h->stream);
                 }
+            } else if constexpr (std::is_same<Real, double>::value) {
+                if (!(f64w && launch_epoch_f64w(A, h->stream))) launch_epoch<Real>(A, h->stream);
             } else {
                 launch_epoch<Real>(A, h->stream);
             }
@@ -571,6 +613,11 @@ sr_ot_status solve_impl(sr_ot_handle h, const sr_ot_options *o, int m, int n, in
             }
             h->launches += 4;
             CKL(h);
+            // Without a tolerance nothing on the host depends on an
+            // intermediate certificate (an active-set solve still reads each
+            // one for a row that outgrew its record): the stream runs on and
+            // only the last one is read back.
+            if (!last && o->tol_rel_gap == 0.0 && !use_sparse) continue;
             int dstat = 0;
             if ((st = read_cert(h, w, dstat_d, &dstat))) return st;
             have_cert = true;
@@ -849,6 +896,7 @@ sr_ot_status solve_batched_impl(sr_ot_handle h, const sr_ot_options *o, int batc
     base.order = o->order;
     base.step = o->step;
     base.seed = o->seed;
+    base.warm = o->batch_warm_start ? 1 : 0;
     int sms = 152;
     {
         int dev = 0;
@@ -872,7 +920,9 @@ sr_ot_status solve_batched_impl(sr_ot_handle h, const sr_ot_options *o, int batc
         const long long key = bk * 64 + o->variant * 8 + o->step;
         if (h->tuned_tile.count(key)) continue;
         int best = kBucketTiles[bk][0];
-        if (kBucketTiles[bk].size() > 1) {
+        // the timing runs write the plans: not with a warm start (the first
+        // tile of the bucket is taken until a cold call has tuned it)
+        if (kBucketTiles[bk].size() > 1 && !base.warm) {
             double best_rate = -1.0;
             for (int tile : kBucketTiles[bk]) {
                 BatchArgs B = args_for(bk, tile);
@@ -897,7 +947,7 @@ sr_ot_status solve_batched_impl(sr_ot_handle h, const sr_ot_options *o, int batc
                 if (rate > best_rate) { best_rate = rate; best = tile; }
             }
         }
-        h->tuned_tile[key] = best;
+        if (!base.warm) h->tuned_tile[key] = best;
     }
     // ---- the solve: one graph per shape set ----------------------------------
     unsigned long long hsh = 1469598103934665603ULL;
@@ -914,6 +964,11 @@ sr_ot_status solve_batched_impl(sr_ot_handle h, const sr_ot_options *o, int batc
     unsigned long long ob[8];
     std::memcpy(ob, o, std::min(sizeof(ob), sizeof(*o)));
     for (unsigned long long w : ob) mix(w);
+    mix((unsigned long long)base.warm);
+    for (int bk = 0; bk < kNumBuckets; ++bk) {  // the tile each bucket runs with
+        auto tt = h->tuned_tile.find(bk * 64 + o->variant * 8 + o->step);
+        mix(tt == h->tuned_tile.end() ? 99ull : (unsigned long long)tt->second);
+    }
     cudaGraphExec_t exec = nullptr;
     auto it = h->graphs.find(hsh);
     if (it != h->graphs.end()) {
@@ -929,7 +984,8 @@ sr_ot_status solve_batched_impl(sr_ot_handle h, const sr_ot_options *o, int batc
         int used = 0;
         for (int bk = 0; bk < kNumBuckets; ++bk) {
             if (buckets[bk].empty()) continue;
-            const int tile = h->tuned_tile[bk * 64 + o->variant * 8 + o->step];
+            auto tt = h->tuned_tile.find(bk * 64 + o->variant * 8 + o->step);
+            const int tile = tt == h->tuned_tile.end() ? kBucketTiles[bk][0] : tt->second;
             cudaStream_t s = h->side[used];
             if (used > 0) cudaStreamWaitEvent(s, h->ev_fork, 0);
             launch_batched_tile(tile, args_for(bk, tile), grid_for(bk, tile), s);
@@ -990,8 +1046,10 @@ sr_ot_status solve_batched_impl(sr_ot_handle h, const sr_ot_options *o, int batc
         o1.dense_only = bucket_of(n[k]) >= 0 ? 1 : o->dense_only;
         o1.trace = nullptr;
         o1.trace_capacity = 0;
+        // from T0, or (warm start) from the plan in T, which the batched
+        // kernel left feasible wherever it stopped
         sr_ot_status s = solve_impl<float>(h, &o1, m[k], n[k], 3, nullptr, X + off_X[k], Y + off_Y[k],
-                                           a + off_a[k], b + off_b[k], T + off_T[k], 0, &res[k]);
+                                           a + off_a[k], b + off_b[k], T + off_T[k], base.warm, &res[k]);
         if (s < 0) res[k].status = s;
         account(s);
     }
@@ -1022,6 +1080,8 @@ void sr_ot_default_options(sr_ot_options *o) {
     o->seed = 0;
     o->trace = nullptr;
     o->trace_capacity = 0;
+    o->spin_limit = 0;
+    o->start_gate = nullptr;
 }
 
 sr_ot_status sr_ot_create(sr_ot_handle *out, int device, void *cuda_stream) {
@@ -1110,6 +1170,54 @@ sr_ot_status sr_ot_gap(sr_ot_handle h, const sr_ot_options *opts, int m, int n, 
     if (opts->precision == SR_OT_FP64)
         return gap_impl<double>(h, opts, m, n, d, C, X, Y, a, b, T, g_rows, res);
     return gap_impl<float>(h, opts, m, n, d, C, X, Y, a, b, T, g_rows, res);
+}
+
+sr_ot_status sr_ot_lp_metrics(sr_ot_handle h, const sr_ot_options *opts, int m, int n, int d, const void *C,
+                              const void *X, const void *Y, const void *T, const void *T_lp,
+                              sr_ot_lp_metrics_result *out) {
+    if (!h) return fail(nullptr, SR_OT_EINVAL, "handle is NULL");
+    h->err.clear();
+    sr_ot_status st;
+    if (!opts) return fail(h, SR_OT_EINVAL, "opts is NULL");
+    if ((st = check_sizes(h, m, n))) return st;
+    if (!T || !T_lp || !out) return fail(h, SR_OT_EINVAL, "T, T_lp and out must be non-NULL");
+    const bool have_c = C != nullptr, have_pts = X != nullptr || Y != nullptr;
+    if (have_c == have_pts) return fail(h, SR_OT_EINVAL, "pass exactly one of C or (X, Y)");
+    if (have_pts && (!X || !Y)) return fail(h, SR_OT_EINVAL, "points mode needs both X and Y");
+    if (have_pts && d != 3) return fail(h, SR_OT_EUNSUPPORTED, "the metrics take points with d = 3 (got %d); pass C", d);
+    if (opts->cost_kind != SR_OT_COST_SQUARED && opts->cost_kind != SR_OT_COST_EUCLIDEAN)
+        return fail(h, SR_OT_EINVAL, "unknown cost_kind %d", opts->cost_kind);
+    if ((st = check_stream_device(h))) return st;
+    const int nb = lp_metrics_blocks(m);
+    double *wk;
+    if ((st = ws_typed(h, WS_MET, (size_t)4 * nb + 4, &wk))) return st;
+    {
+        ProfScope ps(h, SR_OT_PROF_METRICS);
+        if (opts->precision == SR_OT_FP64) {
+            LpMetricsArgs<double> A{m, n, static_cast<const double *>(T), static_cast<const double *>(T_lp),
+                                    static_cast<const double *>(C), static_cast<const double *>(X),
+                                    static_cast<const double *>(Y), opts->cost_kind == SR_OT_COST_EUCLIDEAN};
+            launch_lp_metrics<double>(A, wk, wk + 4 * nb, h->stream);
+        } else {
+            LpMetricsArgs<float> A{m, n, static_cast<const float *>(T), static_cast<const float *>(T_lp),
+                                   static_cast<const float *>(C), static_cast<const float *>(X),
+                                   static_cast<const float *>(Y), opts->cost_kind == SR_OT_COST_EUCLIDEAN};
+            launch_lp_metrics<float>(A, wk, wk + 4 * nb, h->stream);
+        }
+    }
+    h->launches += 2;
+    CKL(h);
+    CK(h, cudaMemcpyAsync(h->h_check, wk + 4 * nb, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    prof_collect(h);
+    const double d2 = h->h_check[0], l2 = h->h_check[1], tc = h->h_check[2], lc = h->h_check[3];
+    out->diff_norm = std::sqrt(std::max(d2, 0.0));
+    out->lp_norm = std::sqrt(std::max(l2, 0.0));
+    out->value = tc;
+    out->lp_value = lc;
+    out->e_m = out->lp_norm > 0.0 ? out->diff_norm / out->lp_norm : 0.0;
+    out->e_v = lc != 0.0 ? std::fabs(tc - lc) / std::fabs(lc) : 0.0;
+    return SR_OT_OK;
 }
 
 sr_ot_status sr_ot_solve_batched(sr_ot_handle h, const sr_ot_options *opts, int batch, const int *m,
@@ -1221,6 +1329,33 @@ sr_ot_status sr_ot_transfer_batched(sr_ot_handle h, const sr_ot_options *opts, i
 }
 
 long long sr_ot_launch_count(sr_ot_handle h) { return h ? h->launches : 0; }
+
+sr_ot_status sr_ot_profile_chain_floor(sr_ot_handle h, int chain_warps, int updates, double *ns_per_update) {
+    if (!h) return fail(nullptr, SR_OT_EINVAL, "handle is NULL");
+    h->err.clear();
+    if (chain_warps != 1 && chain_warps != 3) return fail(h, SR_OT_EINVAL, "chain_warps must be 1 or 3");
+    if (updates < 1 || !ns_per_update) return fail(h, SR_OT_EINVAL, "updates must be >= 1 and the output non-NULL");
+    sr_ot_status st;
+    if ((st = check_stream_device(h))) return st;
+    int *wk;
+    if ((st = ws_typed(h, WS_FLOOR, 4, &wk))) return st;
+    CK(h, cudaMemsetAsync(wk, 0, sizeof(int), h->stream));
+    cudaEvent_t e0 = prof_event(h), e1 = prof_event(h);
+    CK(h, cudaEventRecord(e0, h->stream));
+    launch_chain_floor(chain_warps, updates, wk, reinterpret_cast<float *>(wk + 1), h->stream);
+    h->launches += 1;
+    CK(h, cudaEventRecord(e1, h->stream));
+    CKL(h);
+    CK(h, cudaMemcpyAsync(h->h_status, wk, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    h->event_pool.push_back(e0);
+    h->event_pool.push_back(e1);
+    if (h->h_status[0]) return dev_status_error(h, h->h_status[0]);
+    *ns_per_update = 1e6 * (double)ms / (double)updates;
+    return SR_OT_OK;
+}
 
 sr_ot_status sr_ot_profile_enable(sr_ot_handle h, int enable) {
     if (!h) return fail(nullptr, SR_OT_EINVAL, "handle is NULL");

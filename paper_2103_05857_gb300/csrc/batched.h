@@ -41,6 +41,7 @@ struct BatchArgs {
     int gap_every;
     int variant, order, step;
     unsigned long long seed;
+    int warm;             // 1: every instance starts from the plan in T
 };
 
 // Tile shapes of the batched kernel: ntc compute threads, g quads each, so

@@ -118,6 +118,9 @@ struct EpochArgs {
     int4 *atoms;             // sparse kernel: per-row atom records (m x kAtomRecord)
     int *resume;             // sparse kernel: set to the update index where it stopped
     const int *resume_in;    // dense kernel: start at *resume_in, or return if it is < 0
+    long long spin_limit;    // speculative kernel: probes before a wait gives up (0: default)
+    const int *gate;         // speculative kernel: wait for *gate != 0 before the first update
+    const float *C32;        // FP64 single-warp kernel: the FP32 rounding of C (argmin screen)
 };
 
 // Gap-adaptive epoch (Alg. A.4): rows drawn with probability proportional to
@@ -148,9 +151,19 @@ bool launch_epoch_sparse(const EpochArgs<float> &args, cudaStream_t st);
 // overlaps the current update). False unless BCPFW and n fits.
 bool launch_epoch_pipe(const EpochArgs<float> &args, cudaStream_t st);
 // Speculative pairwise epoch: the LMOs of the next rows are taken ahead
-// against an older residual and repaired at the columns changed since. False
-// unless BCPFW, d = 3 points, cyclic or permuted order and n <= 4096.
-bool launch_epoch_spec(const EpochArgs<float> &args, cudaStream_t st);
+// against an older residual and repaired at the columns changed since. chain:
+// 1 or 3 chain warps in rotation, or kSpecChainSplit (two preparer warps and
+// one decider). False unless BCPFW, d = 3 points, cyclic or permuted order
+// and n <= 4096.
+constexpr int kSpecChainSplit = 0;
+bool launch_epoch_spec(const EpochArgs<float> &args, cudaStream_t st, int chain);
+
+// FP64 BCFW epoch on one warp (n <= epoch_f64w_max_n(), cost given as C):
+// false if the arguments are outside what it takes.
+bool launch_epoch_f64w(const EpochArgs<double> &args, cudaStream_t st);
+int epoch_f64w_max_n();
+// C32[e] = fl32(C[e]) for the single-warp kernel's argmin screen.
+void launch_round_cost(const double *C, float *C32, size_t count, cudaStream_t st);
 
 // Atom records of a dense plan; *overflow becomes 1 if a row has > 63 atoms.
 void launch_build_atoms(int m, int n, const float *T, int4 *rec, int *overflow, cudaStream_t st);
@@ -160,6 +173,10 @@ template <typename Real>
 bool launch_epoch(const EpochArgs<Real> &args, cudaStream_t st);
 
 int epoch_max_n(bool fp64);
+
+// The speculative kernel's chain alone (chain_warps 1 or 3), `updates` times;
+// *status is set to kDevTimeout if a wait gave up; sink: one float.
+void launch_chain_floor(int chain_warps, int updates, int *status, float *sink, cudaStream_t st);
 
 // Message returned by sr_ot_last_error(NULL) on this thread (errors of calls
 // that have no handle).
@@ -203,6 +220,21 @@ struct AdjArgs {
     long long total_cols, total_rows;
     int total_fin;  // blocks of the finishing pass
 };
+
+// ---- evaluation metrics against a reference plan (Sec. 5, v and vi) ------
+template <typename Real>
+struct LpMetricsArgs {
+    int m, n;
+    const Real *T, *L;  // the plan and the reference plan T*_LP
+    const Real *C;      // given cost, or null: d = 3 points X, Y
+    const Real *X, *Y;
+    bool euclid;        // points: the Euclidean cost instead of the squared one
+};
+// Blocks of the metrics pass (4 doubles of partial sums each).
+int lp_metrics_blocks(int m);
+// out[0..3] = sum (t - l)^2, sum l^2, <T, C>, <L, C>; part: 4 doubles per block.
+template <typename Real>
+void launch_lp_metrics(const LpMetricsArgs<Real> &A, double *part, double *out, cudaStream_t st);
 
 // Padded width of the per-entry partial vector (x or y, then 1): 4, 8, 16 or 32.
 int adj_width(int d);

@@ -110,26 +110,55 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_batched(BatchArgs B) {
         float *T = B.T + I.off_T;
         int4 *grec = B.atoms + I.off_atoms;
 
-        // ---- initial plan T0 = (a_i e_0), atom records, residual ----------
-        for (size_t e = tid; e < (size_t)m * n; e += NT) {
-            const int i = (int)(e / n), j = (int)(e - (size_t)i * n);
-            T[e] = j == 0 ? a[i] : 0.f;
+        // ---- initial plan: T0 = (a_i e_0) (Thm 1), or the caller's plan -----
+        // (warm start); atom records; residual
+        if (tid == 0) sflag[0] = 0;
+        if (!B.warm) {
+            for (size_t e = tid; e < (size_t)m * n; e += NT) {
+                const int i = (int)(e / n), j = (int)(e - (size_t)i * n);
+                T[e] = j == 0 ? a[i] : 0.f;
+            }
+            for (int i = tid; i < m; i += NT) {
+                const float ai = a[i];
+                grec[(size_t)i * kAtomRecord] = make_int4(ai > 0.f ? 1 : 0, 0, 0, 0);
+                grec[(size_t)i * kAtomRecord + 1] = make_int4(0, __float_as_int(ai), 0, 0);
+            }
         }
-        for (int i = tid; i < m; i += NT) {
+        for (int i = tid; i < m && i < kRowMax; i += NT) {
             const float ai = a[i];
-            grec[(size_t)i * kAtomRecord] = make_int4(ai > 0.f ? 1 : 0, 0, 0, 0);
-            grec[(size_t)i * kAtomRecord + 1] = make_int4(0, __float_as_int(ai), 0, 0);
-            if (i < kRowMax)
-                arow[i] = make_float4(ai, ai > 0.f ? 1.f / ai : 0.f, ai > 0.f ? 1.f / (2.f * rho * ai) : 0.f, 0.f);
+            arow[i] = make_float4(ai, ai > 0.f ? 1.f / ai : 0.f, ai > 0.f ? 1.f / (2.f * rho * ai) : 0.f, 0.f);
         }
-        // s_0 = sum_i a_i in ascending order (one thread), r = s - b
+        // s_0 = sum_i a_i in ascending order (one thread): the plan's total mass
         if (tid == 0) {
             double s0 = 0.0;
             for (int i = 0; i < m; ++i) s0 += (double)a[i];
             cacc[0] = s0;
-            sflag[0] = 0;
         }
         __syncthreads();
+        if (B.warm) {
+            // the records of the caller's plan: each row's non-zero entries in
+            // column order (one warp per row); a row with more than 63 stops
+            // the instance for the dense path
+            for (int i = warp; i < m; i += NW) {
+                const float *trow = T + (size_t)i * n;
+                int4 *rec = grec + (size_t)i * kAtomRecord;
+                int cnt = 0;
+                for (int j0 = 0; j0 < n; j0 += kWarp) {
+                    const int j = j0 + lane;
+                    const float t = j < n ? trow[j] : 0.f;
+                    const unsigned mk = __ballot_sync(FULL, t > 0.f);
+                    const int pos = cnt + __popc(mk & ((1u << lane) - 1u));
+                    if (t > 0.f && pos < kAtomsMax) rec[1 + pos] = make_int4(j, __float_as_int(t), 0, 0);
+                    cnt += __popc(mk);
+                }
+                if (lane == 0) {
+                    rec[0] = make_int4(cnt <= kAtomsMax ? cnt : 0, 0, 0, 0);
+                    if (cnt > kAtomsMax) sflag[0] = kInstNeedsDense;
+                }
+            }
+            __syncthreads();
+        }
+        const int init_flag = sflag[0];
         // fixed-point exponent for the certificate's column sums (see there)
         int fx_exp;
         {
@@ -139,7 +168,12 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_batched(BatchArgs B) {
         }
         for (int j = tid; j < WID; j += NT) {
             if (j < n) {
-                const double qq = rho64 * ((j == 0 ? cacc[0] : 0.0) - (double)b[j]);
+                double sj = j == 0 ? cacc[0] : 0.0;
+                if (B.warm) {  // the plan's column sum, rows in ascending order
+                    sj = 0.0;
+                    for (int i = 0; i < m; ++i) sj += (double)T[(size_t)i * n + j];
+                }
+                const double qq = rho64 * (sj - (double)b[j]);
                 const float h = (float)qq;
                 qh[j] = h;
                 ql[j] = (float)((double)h - qq);
@@ -170,7 +204,8 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_batched(BatchArgs B) {
         long long next_cert = 0;  // epoch count at which the next certificate is due
         int status = kInstOk;
         int par = 0;
-        for (ep = 0; ep < B.max_epochs; ++ep) {
+        if (init_flag) status = init_flag;
+        for (ep = 0; !init_flag && ep < B.max_epochs; ++ep) {
             const long long k0 = ep * (long long)m;
             // ---- block order of this epoch --------------------------------
             if (B.order == SR_OT_PERMUTE) {

@@ -25,8 +25,9 @@
 // Warps 0..NWP-1 produce segment minima (their columns: quads tid + NTC g),
 // warps NWP, NWP+1 (atom warps, even and odd updates) stream the atom
 // records, take the away statistics and publish the row's data, warps
-// NWP+2 .. NWP+1+kChain are the chain (update u goes to warp u mod kChain):
-// while one warp decides and applies an update, the next prepares its own. They
+// NWP+2 .. NWP+1+CH are the chain (update u goes to warp u mod CH; with
+// CH = 3, while one warp decides and applies an update, the next prepares
+// its own; with CH = 1 one warp prepares, decides and applies). They
 // synchronise through mbarriers only (no polling): per slot a "full" barrier
 // on which the producers and the atom warp arrive (release) once their words
 // for update u are stored and on which the chain waits (acquire), and per
@@ -53,11 +54,14 @@ constexpr int kSpecLag = 4;        // producers run at most this many updates ah
 constexpr int kSpecSlots = 8;      // candidate / atom-warp slots (> kSpecLag)
 constexpr int kSpecRecAhead = 4;   // atom records are fetched this many updates early
 constexpr int kSpecRecSlots = 16;  // record slots (> kSpecLag + kSpecRecAhead)
-constexpr int kChain = 3;          // chain warps; warp c takes the updates u = c mod kChain (exactly
-                                   // 3: the hand-over takes the columns of u-2, then those of u-1)
-constexpr long long kSpecSpin = 1ll << 26;  // polls before a wait gives up
+constexpr int kSpecRecHead = 8;    // record entries fetched ahead: the count and 7 atoms (128 bytes);
+                                   // a row with more atoms has the rest copied when it is used
+// Chain warps CH: 3 (warp c takes the updates u = c mod 3, the hand-over
+// takes the columns of u-2, then those of u-1) or 1 (one warp takes every
+// update; it knows every column changed since the producers' residual
+// without waiting on another warp).
+constexpr long long kSpecSpin = 1ll << 26;  // default polls before a wait gives up
 static_assert(kSpecSlots > kSpecLag && kSpecRecSlots > kSpecLag + kSpecRecAhead, "slot rings too small");
-static_assert(kChain == 3 && kChain <= kSpecLag, "the hand-over takes the columns of u-2 and u-1");
 
 __device__ inline unsigned saddr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ inline int vload(const int *p) { return *reinterpret_cast<const volatile int *>(p); }
@@ -85,14 +89,17 @@ constexpr int kAtomWords = 3;  // atom warp output per update: int4 words
 
 }  // namespace
 
-template <int NWP, int G>
-__global__ void __launch_bounds__(NWP * kWarp + (2 + kChain) * kWarp, 1) k_epoch_spec(EpochArgs<float> A) {
+template <int NWP, int G, int CH, bool SPLIT>
+__global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, 1) k_epoch_spec(EpochArgs<float> A) {
     constexpr int NTC = NWP * kWarp;  // producer threads
     constexpr int AW = NWP;  // atom warps NWP, NWP + 1; chain warps NWP + 2 ...
-    constexpr int NT = NTC + (2 + kChain) * kWarp;
+    constexpr int NT = NTC + (2 + CH) * kWarp;
     constexpr int WID = NTC * 4 * G;
+    static_assert(CH == 1 || CH == 3, "one chain warp, or three in rotation");
+    static_assert(!SPLIT || CH == 3, "the split chain has two preparer warps and one decider");
+    static_assert(CH <= kSpecLag, "the changed columns are known for the updates ver .. u-1");
     static_assert(WID <= 8192, "column index must fit 13 bits");
-    static_assert(NWP + 2 * (kSpecLag - kChain + 1) <= kWarp, "candidates and changed columns must fit one warp");
+    static_assert(NWP + 2 * (kSpecLag - CH + 1) <= kWarp, "candidates and changed columns must fit one warp");
     extern __shared__ __align__(16) unsigned char smem[];
     float *qh = reinterpret_cast<float *>(smem);
     float *ql = qh + WID;
@@ -104,8 +111,10 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + kChain) * kWarp, 1) k_epoch
     uint64_t *full = reinterpret_cast<uint64_t *>(cand + kSpecSlots * NWP);  // kSpecSlots
     uint64_t *done = full + kSpecSlots;                                      // kSpecSlots
     uint64_t *decided = done + kSpecSlots;                                   // kSpecSlots
-    int2 *dec = reinterpret_cast<int2 *>(decided + kSpecSlots);              // columns update u changes
-    int *ctl = reinterpret_cast<int *>(dec + kSpecSlots);                    // [0] stop
+    uint64_t *prepd = decided + kSpecSlots;                                  // kSpecSlots (split chain)
+    int2 *dec = reinterpret_cast<int2 *>(prepd + kSpecSlots);                // columns update u changes
+    int4 *prep = reinterpret_cast<int4 *>(dec + kSpecSlots);                 // prepared words (split chain)
+    int *ctl = reinterpret_cast<int *>(prep + kSpecSlots);                   // [0] stop
 
     const int m = A.in.m, n = A.in.n;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -130,17 +139,31 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + kChain) * kWarp, 1) k_epoch
         }
         lastmod[j] = -1;
     }
+    const long long spin = A.spin_limit > 0 ? A.spin_limit : kSpecSpin;
     if (tid == 0) {
         for (int s = 0; s < kSpecSlots; ++s) {
             mbar_init(full + s, NWP + 1);
             mbar_init(done + s, 1);
             mbar_init(decided + s, 1);
+            mbar_init(prepd + s, 1);
             dec[s] = make_int2(-1, -1);
         }
         ctl[0] = 0;
         if (A.resume) *A.resume = -1;
+        if (A.gate) {  // the start gate: a bounded wait for a non-zero word
+            long long it = 0;
+            while (vload(A.gate) == 0) {
+                if (++it > spin) {
+                    atomicCAS(A.status, 0, (int)kDevTimeout);
+                    ctl[0] = 1;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
     }
     __syncthreads();
+    const bool gate_closed = ctl[0] != 0;  // every warp skips its loop
 
     auto row_of = [&](int u) -> int { return order == SR_OT_PERMUTE ? A.perm[u] : u; };
     // gradient of row x at column j with the residual as it is now
@@ -157,7 +180,7 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + kChain) * kWarp, 1) k_epoch
         long long it = 0;
         while (!mbar_try(done + p % kSpecSlots, (unsigned)(p / kSpecSlots) & 1u)) {
             if (vload(ctl)) return false;
-            if (++it > kSpecSpin) {
+            if (++it > spin) {
                 if (lane == 0) {
                     atomicCAS(A.status, 0, (int)kDevTimeout);
                     vstore(ctl, 1);
@@ -184,7 +207,9 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + kChain) * kWarp, 1) k_epoch
         for (int e = 0; e < 4; ++e) xa[0][e] = xa[1][e];
     };
 
-    if (warp < NWP) {
+    if (gate_closed) {
+        // the start gate timed out: no update is made, the residual is kept
+    } else if (warp < NWP) {
         // ================= producers: segment minima =====================
         float2 ny0[2 * G], ny1[2 * G], ny2[2 * G];
 #pragma unroll
@@ -247,11 +272,10 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + kChain) * kWarp, 1) k_epoch
         // ============ statistics, row data
         const int aw0 = warp - AW;
         auto fetch_record = [&](int t) {
-            if (t < m) {
+            if (t < m && lane < kSpecRecHead) {
                 const int i = row_of(t);
                 int4 *dst = aring + (size_t)(t % kSpecRecSlots) * kAtomRecord;
                 cp16(dst + lane, grec + (size_t)i * kAtomRecord + lane);
-                cp16(dst + 32 + lane, grec + (size_t)i * kAtomRecord + 32 + lane);
             }
             commit();
         };
@@ -261,10 +285,21 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + kChain) * kWarp, 1) k_epoch
         load_xa(1, aw0 + 2);
         for (int u = aw0; u < m; u += 2) {
             if (!gate(u)) break;
-            wait_groups<1>();  // the record of update u has landed (u + 2 may be in flight)
+            wait_groups<1>();  // the head of update u's record has landed (u + 2's may be in flight)
             __syncwarp();
+            int4 *rs = aring + (size_t)(u % kSpecRecSlots) * kAtomRecord;
+            {
+                const int cnt = rs[0].x;  // warp-uniform
+                if (cnt >= kSpecRecHead) {
+                    // more atoms than the head holds (rare): copy the rest now;
+                    // the row's record is not written again before update u
+                    const int4 *src = grec + (size_t)row_of(u) * kAtomRecord;
+                    for (int e = kSpecRecHead + lane; e <= cnt && e < kAtomRecord; e += kWarp) rs[e] = src[e];
+                    __syncwarp();
+                }
+            }
             const float x0 = xa[0][0], x1 = xa[0][1], x2 = xa[0][2], au = xa[0][3];
-            LaneAtoms at = load_atoms(aring + (size_t)(u % kSpecRecSlots) * kAtomRecord, lane);
+            LaneAtoms at = load_atoms(rs, lane);
             DF tvd{0.f, 0.f};
             auto grad = [&](int j) -> float { return grad_at(j, x0, x1, x2); };
             const AtomStats st = atom_stats(at, grad, au, false, &tvd);
@@ -284,10 +319,232 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + kChain) * kWarp, 1) k_epoch
             load_xa(1, u + 4);
         }
         wait_groups<0>();
+    } else if (SPLIT && warp < AW + 4) {
+        // ================= split chain: two preparer warps ================
+        // Preparer (u mod 2) takes everything of update u that does not need
+        // the residual of u-2 and u-1: once update u-3 is published, the
+        // segment minima (recomputed where their column changed since ver),
+        // the columns changed by updates ver..u-3, the record position of
+        // the likely vertex and whether an atom changed since ver. The
+        // decider merges the columns of u-2 and u-1 itself.
+        const int pw = warp - (NWP + 2);
+        auto wait_bar = [&](uint64_t *b, unsigned parity) -> bool {
+            long long it = 0;
+            while (!mbar_try(b, parity)) {
+                if (vload(ctl)) return false;
+                if (++it > spin) {
+                    if (lane == 0) {
+                        atomicCAS(A.status, 0, (int)kDevTimeout);
+                        vstore(ctl, 1);
+                    }
+                    return false;
+                }
+            }
+            return true;
+        };
+        for (int u = pw; u < m; u += 2) {
+            const int slot = u % kSpecSlots;
+            if (u >= 3) {
+                const int p3 = u - 3;
+                if (!wait_bar(done + p3 % kSpecSlots, (unsigned)(p3 / kSpecSlots) & 1u)) break;
+            }
+            if (!wait_bar(full + slot, (unsigned)(u / kSpecSlots) & 1u)) break;
+            const unsigned long long cw = lane < NWP ? cand[slot * NWP + lane] : 0ull;
+            const int4 w1 = aw[slot * kAtomWords + 1];
+            const int ver = u > kSpecLag ? u - kSpecLag : 0;
+            const float x0 = __int_as_float(w1.x), x1 = __int_as_float(w1.y), x2 = __int_as_float(w1.z);
+            LaneAtoms at = load_atoms(aring + (size_t)(u % kSpecRecSlots) * kAtomRecord, lane);
+            auto grad = [&](int j) -> float { return grad_at(j, x0, x1, x2); };
+            uint32_t key = 0xFFFFFFFFu;
+            int col = 0x7FFFFFFF;
+            bool stale = false;
+            if (lane < NWP) {
+                const int cj = (int)(cw >> 32);
+                stale = lastmod[cj] >= ver;
+                if (!stale) {
+                    key = (uint32_t)cw;
+                    col = cj;
+                }
+            } else if (lane < NWP + 2 * (kSpecLag - 2)) {
+                const int w = u - 3 - ((lane - NWP) >> 1);
+                if (w >= ver && w >= 0) {
+                    const int2 d = dec[w % kSpecSlots];
+                    const int c = ((lane - NWP) & 1) ? d.y : d.x;
+                    if (c >= 0) {
+                        key = f2key(grad(c));
+                        col = c;
+                    }
+                }
+            }
+            unsigned fb = __ballot_sync(FULL, stale);
+            while (fb) {
+                const int w = __ffs(fb) - 1;
+                fb &= fb - 1;
+                float bv = INF;
+                int bj = 0x7FFFFFFF;
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    const int j0 = 4 * (kWarp * w + lane + NTC * g);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float gv = grad(j0 + e);
+                        if (gv < bv) { bv = gv; bj = j0 + e; }
+                    }
+                }
+                const uint32_t kb = f2key(bv);
+                const uint32_t wk = __reduce_min_sync(FULL, kb);
+                const int wj = __reduce_min_sync(FULL, kb == wk ? bj : 0x7FFFFFFF);
+                if (lane == w) { key = wk; col = wj; }
+            }
+            const uint32_t pk = __reduce_min_sync(FULL, key);
+            const int pj = __reduce_min_sync(FULL, key == pk ? col : 0x7FFFFFFF);
+            const bool olddirty = __any_sync(FULL, (at.j[0] >= 0 && lastmod[at.j[0]] >= ver) ||
+                                                       (at.cnt > 32 && at.j[1] >= 0 && lastmod[at.j[1]] >= ver));
+            bool present = false;
+            int jpos = -1;
+            atom_weight(at, pj, &present, &jpos);
+            if (lane == 0) {
+                prep[slot] = make_int4((int)pk, pj, olddirty ? 1 : 0, jpos);
+                mbar_arrive(prepd + slot);
+            }
+        }
+    } else if (SPLIT) {
+        // ================= split chain: the decider =======================
+        // One warp decides and applies every update. It knows the columns
+        // the last two updates changed (its own), merges their exact keys
+        // into the prepared minimum (the full LMO instead when that minimum
+        // sits on one of them), takes the away statistics again when one of
+        // the row's atoms changed, decides, applies and publishes -- with no
+        // hand-over between warps on its chain.
+        bool aborted = false;
+        int c1[2] = {-1, -1}, c2[2] = {-1, -1};  // columns changed by updates u-1 and u-2
+        for (int u = 0; u < m; ++u) {
+            const long long k = A.k0 + u;
+            const int slot = u % kSpecSlots;
+            {
+                long long it = 0;
+                while (!mbar_try(prepd + slot, (unsigned)(u / kSpecSlots) & 1u)) {
+                    if (vload(ctl)) { aborted = true; break; }
+                    if (++it > spin) {
+                        if (lane == 0) {
+                            atomicCAS(A.status, 0, (int)kDevTimeout);
+                            vstore(ctl, 1);
+                        }
+                        aborted = true;
+                        break;
+                    }
+                }
+                if (aborted) break;
+            }
+            const int4 pr = prep[slot];
+            const uint32_t pk = (uint32_t)pr.x;
+            const int pj = pr.y;
+            const bool olddirty = pr.z != 0;
+            int jpos = pr.w;
+            bool present = jpos >= 0;
+            const int4 w0 = aw[slot * kAtomWords], w1 = aw[slot * kAtomWords + 1], w2 = aw[slot * kAtomWords + 2];
+            const int row = w2.z;
+            const float x0 = __int_as_float(w1.x), x1 = __int_as_float(w1.y), x2 = __int_as_float(w1.z);
+            const float ai = __int_as_float(w1.w), ra = __int_as_float(w2.x), ia = __int_as_float(w2.y);
+            LaneAtoms at = load_atoms(aring + (size_t)(u % kSpecRecSlots) * kAtomRecord, lane);
+            auto grad = [&](int j) -> float { return grad_at(j, x0, x1, x2); };
+            // update u-2: its two columns join the prepared minimum (a prepared
+            // minimum on one of them was stale: the full LMO is taken instead)
+            bool redo_lmo = pj >= 0 && (pj == c2[0] || pj == c2[1]);
+            uint32_t fk = pk;
+            int js = pj;
+            {
+                const int c = lane == 0 ? c2[0] : c2[1];
+                const uint32_t ke = (lane < 2 && c >= 0) ? f2key(grad(c)) : 0xFFFFFFFFu;
+                const uint32_t k0 = __shfl_sync(FULL, ke, 0), k1 = __shfl_sync(FULL, ke, 1);
+                if (c2[0] >= 0 && (k0 < fk || (k0 == fk && c2[0] < js))) { fk = k0; js = c2[0]; }
+                if (c2[1] >= 0 && (k1 < fk || (k1 == fk && c2[1] < js))) { fk = k1; js = c2[1]; }
+            }
+            const int pj2 = js;
+            if (pj2 != pj) atom_weight(at, pj2, &present, &jpos);
+            // update u-1
+            redo_lmo = redo_lmo || (pj2 >= 0 && (pj2 == c1[0] || pj2 == c1[1]));
+            auto hit = [&](int c) { return c >= 0 && (c == c1[0] || c == c1[1] || c == c2[0] || c == c2[1]); };
+            const bool redo_atoms = __any_sync(FULL, olddirty || hit(at.j[0]) || (at.cnt > 32 && hit(at.j[1])));
+            if (redo_lmo) {
+                float bv = INF;
+                int bj = 0x7FFFFFFF;
+                for (int q = lane; q < WID / 4; q += kWarp) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float gv = grad(4 * q + e);
+                        if (gv < bv) { bv = gv; bj = 4 * q + e; }
+                    }
+                }
+                const uint32_t kb = f2key(bv);
+                fk = __reduce_min_sync(FULL, kb);
+                js = __reduce_min_sync(FULL, kb == fk ? bj : 0x7FFFFFFF);
+            } else {
+                const int c = lane == 0 ? c1[0] : c1[1];
+                const uint32_t ke = (lane < 2 && c >= 0) ? f2key(grad(c)) : 0xFFFFFFFFu;
+                const uint32_t k0 = __shfl_sync(FULL, ke, 0), k1 = __shfl_sync(FULL, ke, 1);
+                if (c1[0] >= 0 && (k0 < fk || (k0 == fk && c1[0] < js))) { fk = k0; js = c1[0]; }
+                if (c1[1] >= 0 && (k1 < fk || (k1 == fk && c1[1] < js))) { fk = k1; js = c1[1]; }
+            }
+            const float gmin = key2f(fk);
+            DF tvd{__int_as_float(w0.y), __int_as_float(w0.z)};
+            AtomStats st;
+            if (redo_atoms) {
+                st = atom_stats(at, grad, ai, false, &tvd);
+            } else {
+                const int v13 = w0.w & 0x1FFF;
+                st.v = v13 == 0x1FFF ? 0x7FFFFFFF : v13;
+                st.vpos = (w0.w >> 13) - 1;
+                st.gmax = __int_as_float(w0.x);
+                st.t_v = tvd.hi;
+                st.nnz = at.cnt;
+                st.g_aw = st.s2 = st.dda = 0.f;
+            }
+            if (!isfinite(gmin)) {
+                if (lane == 0) atomicCAS(A.status, 0, (int)kDevNonFinite);
+                aborted = true;
+                break;
+            }
+            float gmx = 0.f, inv = 0.f;
+            if (ai > 0.f) {
+                gmx = st.t_v * ra;  // same rounding as the two-phase kernel
+                inv = ia;
+            }
+            if (js != pj2) atom_weight(at, js, &present, &jpos);
+            const Step<float> S = decide_pairwise(st, gmin, js, ai, rho, gmx, inv, n);
+            const bool moved = S.kind == 2 && S.v != S.js && st.vpos >= 0;
+            if (lane == 0) dec[slot] = moved ? make_int2(S.js, S.v) : make_int2(-1, -1);
+            auto publish = [&] {
+                if (lane == 0 && moved) {
+                    lastmod[S.js] = u;
+                    lastmod[S.v] = u;
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(done + slot);
+            };
+            const bool ok = apply_pairwise(S, at, jpos, st.vpos, tvd, rho, A.T + (size_t)row * n, qh, ql,
+                                           grec + (size_t)row * kAtomRecord, lane, publish);
+            if (!ok) {  // j* would be a 64th atom: the dense kernel takes over at u
+                if (lane == 0 && A.resume) *A.resume = u;
+                aborted = true;
+                break;
+            }
+            if (lane == 0 && A.trace && k < A.trace_cap) {
+                A.trace[4 * k] = row;
+                A.trace[4 * k + 1] = js;
+                A.trace[4 * k + 2] = (st.v >= 0 && st.v < n) ? st.v : -1;
+                A.trace[4 * k + 3] = __float_as_int(S.gamma);
+            }
+            c2[0] = c1[0];
+            c2[1] = c1[1];
+            c1[0] = moved ? S.js : -1;
+            c1[1] = moved ? S.v : -1;
+        }
+        if (aborted && lane == 0) vstore(ctl, 1);  // releases every other warp still waiting
     } else {
         // ================= chain warps ====================================
-        // Warp NWP + 2 + (u mod kChain) takes update u. It prepares u
-        // (segment minima, the columns changed by updates ver..u-kChain, the
+        // Warp NWP + 2 + (u mod CH) takes update u. It prepares u
+        // (segment minima, the columns changed by updates ver..u-CH, the
         // away statistics) while the other chain warps decide and apply the
         // updates before it; then it merges the columns that u-2 changed
         // (decided and stored an update earlier), takes the two that u-1
@@ -299,7 +556,7 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + kChain) * kWarp, 1) k_epoch
             long long it = 0;
             while (!mbar_try(b, parity)) {
                 if (vload(ctl)) return false;
-                if (++it > kSpecSpin) {
+                if (++it > spin) {
                     if (lane == 0) {
                         atomicCAS(A.status, 0, (int)kDevTimeout);
                         vstore(ctl, 1);
@@ -309,7 +566,7 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + kChain) * kWarp, 1) k_epoch
             }
             return true;
         };
-        for (int u = cwi; u < m; u += kChain) {
+        for (int u = cwi; u < m; u += CH) {
             const long long k = A.k0 + u;
             const int slot = u % kSpecSlots;
             const int ps = (u + kSpecSlots - 1) % kSpecSlots;  // slot of update u - 1
@@ -336,8 +593,8 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + kChain) * kWarp, 1) k_epoch
                     key = (uint32_t)cw;
                     col = cj;
                 }
-            } else if (lane < NWP + 2 * (kSpecLag - kChain + 1)) {
-                const int w = u - kChain - ((lane - NWP) >> 1);
+            } else if (lane < NWP + 2 * (kSpecLag - CH + 1)) {
+                const int w = u - CH - ((lane - NWP) >> 1);
                 if (w >= ver && w >= 0) {
                     const int2 d = dec[w % kSpecSlots];
                     const int c = ((lane - NWP) & 1) ? d.y : d.x;
@@ -380,7 +637,7 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + kChain) * kWarp, 1) k_epoch
             // minimum (a prepared minimum on one of them was stale: the full
             // LMO is taken instead)
             int c2[2] = {-1, -1}, c1[2] = {-1, -1};
-            if (u >= 2) {
+            if (CH > 1 && u >= 2) {
                 const int s2 = (u - 2) % kSpecSlots;
                 const unsigned p2 = (unsigned)((u - 2) / kSpecSlots) & 1u;
                 if (!wait_bar(decided + s2, p2) || !wait_bar(done + s2, p2)) { aborted = true; break; }
@@ -401,7 +658,7 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + kChain) * kWarp, 1) k_epoch
             const int pj2 = js;
             if (pj2 != pj) atom_weight(at, pj2, &present, &jpos);
             // ---- hand-over, 2: update u-1, its columns, then their residual
-            if (u >= 1) {
+            if (CH > 1 && u >= 1) {
                 if (!wait_bar(decided + ps, pp)) { aborted = true; break; }
                 const int2 d = dec[ps];
                 c1[0] = d.x;
@@ -419,7 +676,7 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + kChain) * kWarp, 1) k_epoch
                 const float d0 = x0 - y.x, d1 = x1 - y.y, d2 = x2 - y.z;
                 ce = fmaf(d2, d2, fmaf(d1, d1, __fmul_rn(d0, d0)));
             }
-            if (u >= 1 && !wait_bar(done + ps, pp)) { aborted = true; break; }
+            if (CH > 1 && u >= 1 && !wait_bar(done + ps, pp)) { aborted = true; break; }
             if (redo_lmo) {
                 // the prepared minimum sits on a column changed since: full LMO
                 float bv = INF;
@@ -470,7 +727,7 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + kChain) * kWarp, 1) k_epoch
             const bool moved = S.kind == 2 && S.v != S.js && st.vpos >= 0;
             if (lane == 0) dec[slot] = moved ? make_int2(S.js, S.v) : make_int2(-1, -1);
             __syncwarp();
-            if (lane == 0) mbar_arrive(decided + slot);
+            if (CH > 1 && lane == 0) mbar_arrive(decided + slot);
             // after the residual has changed: release of update u, before the
             // plan entries and the record are stored
             auto publish = [&] {
@@ -506,32 +763,38 @@ static size_t spec_smem() {
     constexpr int WID = NWP * kWarp * 4 * G;
     size_t b = (size_t)WID * (4 + 4 + 16 + 4);
     b += (size_t)kSpecRecSlots * kAtomRecord * 16;
-    b += (size_t)kSpecSlots * (kAtomWords * 16 + NWP * 8 + 3 * 8 + 8);
+    b += (size_t)kSpecSlots * (kAtomWords * 16 + NWP * 8 + 4 * 8 + 8 + 16);
     b += 16;
     return b;
 }
 
-template <int NWP, int G>
+template <int NWP, int G, int CH, bool SPLIT>
 static void launch_spec(const EpochArgs<float> &A, cudaStream_t st) {
-    auto kern = k_epoch_spec<NWP, G>;
+    auto kern = k_epoch_spec<NWP, G, CH, SPLIT>;
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
         attr_set = true;
     }
-    kern<<<1, NWP * kWarp + (2 + kChain) * kWarp, spec_smem<NWP, G>(), st>>>(A);
+    kern<<<1, NWP * kWarp + (2 + CH) * kWarp, spec_smem<NWP, G>(), st>>>(A);
 }
 
-bool launch_epoch_spec(const EpochArgs<float> &A, cudaStream_t st) {
-    if (A.variant != SR_OT_BCPFW || A.in.cost_mode != kCostPts3) return false;
-    if (A.order != SR_OT_CYCLIC && A.order != SR_OT_PERMUTE) return false;
+template <int CH, bool SPLIT>
+static bool launch_spec_ch(const EpochArgs<float> &A, cudaStream_t st) {
     const int n = A.in.n;
-    if (n <= 128 * 4) launch_spec<4, 1>(A, st);
-    else if (n <= 128 * 8) launch_spec<4, 2>(A, st);
-    else if (n <= 128 * 16) launch_spec<4, 4>(A, st);
-    else if (n <= 128 * 32) launch_spec<4, 8>(A, st);
+    if (n <= 128 * 4) launch_spec<4, 1, CH, SPLIT>(A, st);
+    else if (n <= 128 * 8) launch_spec<4, 2, CH, SPLIT>(A, st);
+    else if (n <= 128 * 16) launch_spec<4, 4, CH, SPLIT>(A, st);
+    else if (n <= 128 * 32) launch_spec<4, 8, CH, SPLIT>(A, st);
     else return false;
     return true;
+}
+
+bool launch_epoch_spec(const EpochArgs<float> &A, cudaStream_t st, int chain) {
+    if (A.variant != SR_OT_BCPFW || A.in.cost_mode != kCostPts3) return false;
+    if (A.order != SR_OT_CYCLIC && A.order != SR_OT_PERMUTE) return false;
+    if (chain == kSpecChainSplit) return launch_spec_ch<3, true>(A, st);
+    return chain == 1 ? launch_spec_ch<1, false>(A, st) : launch_spec_ch<3, false>(A, st);
 }
 
 }  // namespace srot

@@ -20,14 +20,16 @@ BCFW, BCAFW, BCPFW, FW = 0, 1, 2, 3
 CYCLIC, PERMUTE, UNIFORM, GAP_ADAPTIVE = 0, 1, 2, 3
 DEC, ELS = 0, 1
 FP64, FP32, FP32_BF16COST = 0, 1, 2
-EPOCH_AUTO, EPOCH_TWO_PHASE, EPOCH_PIPELINED, EPOCH_SPECULATIVE = 0, 1, 2, 3
+EPOCH_AUTO, EPOCH_TWO_PHASE, EPOCH_PIPELINED, EPOCH_SPECULATIVE, EPOCH_SPECULATIVE_ONE_CHAIN = 0, 1, 2, 3, 4
+EPOCH_SPECULATIVE_SPLIT = 5
 COST_SQUARED, COST_EUCLIDEAN = 0, 1
 
 EXPORTS = ["sr_ot_default_options", "sr_ot_create", "sr_ot_set_stream", "sr_ot_destroy",
            "sr_ot_last_error", "sr_ot_solve", "sr_ot_solve_batched", "sr_ot_grad",
            "sr_ot_grad_batched", "sr_ot_transfer", "sr_ot_transfer_batched", "sr_ot_gap", "sr_ot_cost_bf16", "sr_ot_launch_count",
-           "sr_ot_profile_enable", "sr_ot_profile_read", "sr_ot_gap_noalloc"]
-PROF_EPOCH, PROF_CERT, PROF_BATCH, PROF_GRAD, PROF_COST = 0, 1, 2, 3, 4
+           "sr_ot_profile_enable", "sr_ot_profile_read", "sr_ot_gap_noalloc", "sr_ot_lp_metrics",
+           "sr_ot_profile_chain_floor"]
+PROF_EPOCH, PROF_CERT, PROF_BATCH, PROF_GRAD, PROF_COST, PROF_METRICS = 0, 1, 2, 3, 4, 5
 
 
 class Options(ct.Structure):
@@ -37,12 +39,18 @@ class Options(ct.Structure):
         ("gap_every", ct.c_int), ("refresh_every", ct.c_int), ("ga_M", ct.c_int),
         ("ga_global_only", ct.c_int), ("seed", ct.c_ulonglong), ("trace", ct.c_void_p),
         ("trace_capacity", ct.c_longlong), ("dense_only", ct.c_int), ("epoch_kernel", ct.c_int), ("cost_kind", ct.c_int),
+        ("spin_limit", ct.c_longlong), ("batch_warm_start", ct.c_int), ("start_gate", ct.c_void_p),
     ]
 
 
 class TransferStats(ct.Structure):
     _fields_ = [("e_c", ct.c_double), ("row_err", ct.c_double), ("col_err", ct.c_double),
                 ("sparsity", ct.c_double)]
+
+
+class LpMetrics(ct.Structure):
+    _fields_ = [("e_m", ct.c_double), ("e_v", ct.c_double), ("diff_norm", ct.c_double),
+                ("lp_norm", ct.c_double), ("value", ct.c_double), ("lp_value", ct.c_double)]
 
 
 class Result(ct.Structure):
@@ -93,6 +101,8 @@ def _load():
     lib.sr_ot_cost_bf16.argtypes = [vp, i, i, i, vp, vp, vp]
     lib.sr_ot_gap_noalloc.argtypes = [i, vp, ct.POINTER(Options), i, i, i, vp, vp, vp, vp, vp, vp,
                                       vp, ct.POINTER(Result)]
+    lib.sr_ot_lp_metrics.argtypes = [vp, ct.POINTER(Options), i, i, i, vp, vp, vp, vp, vp, ct.POINTER(LpMetrics)]
+    lib.sr_ot_profile_chain_floor.argtypes = [vp, i, i, ct.POINTER(d)]
     lib.sr_ot_profile_enable.argtypes = [vp, i]
     lib.sr_ot_profile_read.argtypes = [vp, i, ct.POINTER(d), ct.POINTER(ll)]
     for name in EXPORTS:
@@ -111,8 +121,8 @@ def options(**kw) -> Options:
     o = Options()
     lib.sr_ot_default_options(ct.byref(o))
     for k, v in kw.items():
-        if k == "trace":
-            o.trace = None if v is None else v.data_ptr()
+        if k in ("trace", "start_gate"):
+            setattr(o, k, None if v is None else v.data_ptr())
             continue
         if not hasattr(o, k):
             raise KeyError(k)
@@ -173,6 +183,13 @@ class Handle:
     def profile(self, enable: bool = True):
         self._check(lib.sr_ot_profile_enable(self._h, int(bool(enable))), allow=(OK,))
 
+    def chain_floor(self, chain_warps: int = 3, updates: int = 1 << 16) -> float:
+        """sr_ot_profile_chain_floor: ns per update of the speculative kernel's
+        update chain alone."""
+        ns = ct.c_double()
+        self._check(lib.sr_ot_profile_chain_floor(self._h, int(chain_warps), int(updates), ct.byref(ns)), allow=(OK,))
+        return ns.value
+
     def profile_read(self, kind: int):
         ms, groups = ct.c_double(), ct.c_longlong()
         self._check(lib.sr_ot_profile_read(self._h, kind, ct.byref(ms), ct.byref(groups)), allow=(OK,))
@@ -216,6 +233,22 @@ class Handle:
                                      arrs[3], arrs[4], _ptr(X), _ptr(Y), _ptr(a), _ptr(b), _ptr(T),
                                      res)
         self._check(st)
+        return st, [r.asdict() for r in res]
+
+    def solve_batched_raw(self, X, Y, a, b, T, sizes, offsets, opts=None, **kw):
+        """sr_ot_solve_batched returning (status, list of result dicts) without
+        raising: each instance's own status is in its dict, the call returns
+        the worst of them."""
+        o = opts if opts is not None else options(**kw)
+        B = len(sizes)
+        mm = (ct.c_int * B)(*[int(s[0]) for s in sizes])
+        nn = (ct.c_int * B)(*[int(s[1]) for s in sizes])
+        cols = list(zip(*offsets))
+        arrs = [(ct.c_longlong * B)(*[int(v) for v in c]) for c in cols]
+        res = (Result * B)()
+        st = lib.sr_ot_solve_batched(self._h, ct.byref(o), B, mm, nn, 3, arrs[0], arrs[1], arrs[2],
+                                     arrs[3], arrs[4], _ptr(X), _ptr(Y), _ptr(a), _ptr(b), _ptr(T),
+                                     res)
         return st, [r.asdict() for r in res]
 
     def gap(self, a, b, T, C=None, X=None, Y=None, g_rows=None, opts=None, **kw):
@@ -309,6 +342,18 @@ class Handle:
                                     _ptr(out.get("dY")), _ptr(out.get("db")))
         self._check(st, allow=(OK,))
         return out
+
+    def lp_metrics(self, T, T_lp, C=None, X=None, Y=None, opts=None, **kw):
+        """sr_ot_lp_metrics: e_m, e_v (Sec. 5, metrics v and vi) of plan T
+        against the reference plan T_lp. Returns a dict."""
+        o = opts if opts is not None else options(**kw)
+        m, n = T.shape
+        d = 0 if X is None else X.shape[1]
+        r = LpMetrics()
+        st = lib.sr_ot_lp_metrics(self._h, ct.byref(o), m, n, d, _ptr(C), _ptr(X), _ptr(Y), _ptr(T), _ptr(T_lp),
+                                  ct.byref(r))
+        self._check(st, allow=(OK,))
+        return {f: getattr(r, f) for f, _ in LpMetrics._fields_}
 
     def cost_bf16(self, X, Y, C=None):
         """sr_ot_cost_bf16: C = |x~|^2 + |y~|^2 - 2 X~ Y~^T on the tensor cores

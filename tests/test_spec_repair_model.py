@@ -9,12 +9,15 @@ Alg. A.3, changes q in the two columns j*, v only):
   - producers take their segment minima for update u with every column at some
     version in [ver, u], ver = max(u - 4, 0) (they wait until update u - 5 is
     applied), each column independently (reads race with the chain's stores);
-  - the chain warp of u prepares after its own update u - 3 (so every column is
-    at version >= u - 2), with the updates u - 2, u - 1 possibly half applied;
-    the last-change marks of u - 4 and u - 3 are visible, those of u - 2 and
-    u - 1 may or may not be;
-  - after the hand-over of u - 2 every column is at version >= u - 1; after that
-    of u - 1 at version u.
+  - with three chain warps in rotation, the chain warp of u prepares after its
+    own update u - 3 (so every column is at version >= u - 2), with the updates
+    u - 2, u - 1 possibly half applied; the last-change marks of u - 4 and
+    u - 3 are visible, those of u - 2 and u - 1 may or may not be; after the
+    hand-over of u - 2 every column is at version >= u - 1; after that of
+    u - 1 at version u;
+  - with one chain warp, it prepares update u after applying u - 1 itself:
+    every column is at version u and every mark is visible; there is no
+    hand-over.
 The atom warp takes the away vertex (Alg. A.3: the atom with the largest
 gradient) at versions in [ver, u] as well; the chain takes it again when one of
 the row's atom columns changed since ver. The model draws all of these at
@@ -25,29 +28,33 @@ import os
 import re
 
 import numpy as np
+import pytest
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2103_05857_gb300",
                    "csrc", "solve_spec.cu")
 
 
-def _kernel_constant(name):
+def _kernel_source():
     with open(SRC) as fh:
-        return int(re.search(r"constexpr int %s = (\d+);" % name, fh.read()).group(1))
+        return fh.read()
 
 
-LAG = _kernel_constant("kSpecLag")      # producers run at most this many updates ahead
-CHAIN = _kernel_constant("kChain")      # chain warps in rotation
+LAG = int(re.search(r"constexpr int kSpecLag = (\d+);", _kernel_source()).group(1))  # producers' lead
+# the chain-warp counts the kernel is built for
+CHAINS = tuple(int(v) for v in re.search(r"static_assert\(CH == (\d+) \|\| CH == (\d+),",
+                                         _kernel_source()).groups())
 
 
 def _min(keys):
     return min(keys) if keys else (np.inf, 1 << 30)
 
 
-def _chain_lmo(rng, u, C, q0, dec, deltas, nseg, atoms, drop=None):
+def _chain_lmo(rng, u, C, q0, dec, deltas, nseg, atoms, CHAIN, drop=None):
     """The kernel's LMO and away vertex for update u under one random
-    interleaving. `drop` leaves one repair out (a planted mistake): "stale" (no
-    segment recompute), "history" (no columns of u-3, u-4), "c2" or "c1" (no
-    hand-over merge), "atoms" (the atom warp's away statistics always kept)."""
+    interleaving, with CHAIN chain warps. `drop` leaves one repair out (a
+    planted mistake): "stale" (no segment recompute), "history" (no columns
+    of u-CHAIN .. u-4), "c2" or "c1" (no hand-over merge), "atoms" (the atom
+    warp's away statistics always kept)."""
     n = len(C)
     seg_of = (np.arange(n) // 4) % nseg  # quads interleaved over the producer warps
 
@@ -94,7 +101,7 @@ def _chain_lmo(rng, u, C, q0, dec, deltas, nseg, atoms, drop=None):
     fk, js = _min(keys)
     pj = js
     # hand-over 1: update u-2 is applied, u-1 may be half applied
-    c2 = dec[u - 2] if u >= 2 and dec[u - 2] is not None and drop != "c2" else ()
+    c2 = dec[u - 2] if CHAIN == 3 and u >= 2 and dec[u - 2] is not None and drop != "c2" else ()
     redo = pj in c2
     for c in c2:
         k = value(c, int(rng.integers(max(u - 1, 0), u + 1)))
@@ -102,7 +109,7 @@ def _chain_lmo(rng, u, C, q0, dec, deltas, nseg, atoms, drop=None):
             fk, js = k, c
     pj2 = js
     # hand-over 2: update u-1 is applied, every column at version u
-    c1 = dec[u - 1] if u >= 1 and dec[u - 1] is not None and drop != "c1" else ()
+    c1 = dec[u - 1] if CHAIN == 3 and u >= 1 and dec[u - 1] is not None and drop != "c1" else ()
     redo = redo or pj2 in c1
     if redo:
         fk, js = min((value(j, u), j) for j in range(n))
@@ -118,7 +125,7 @@ def _chain_lmo(rng, u, C, q0, dec, deltas, nseg, atoms, drop=None):
     return js, away, value
 
 
-def _mismatches(seed, trials, drop=None):
+def _mismatches(seed, trials, chain, drop=None):
     rng = np.random.default_rng(seed)
     bad = 0
     for _ in range(trials):
@@ -141,7 +148,7 @@ def _mismatches(seed, trials, drop=None):
                 dec.append(None)
                 deltas.append(np.zeros(n))
         atoms = [int(j) for j in rng.choice(n, int(rng.integers(1, 6)), replace=False)]
-        js, away, value = _chain_lmo(rng, u, C, q0, dec, deltas, nseg, atoms, drop)
+        js, away, value = _chain_lmo(rng, u, C, q0, dec, deltas, nseg, atoms, chain, drop)
         exact = min((value(j, u), j) for j in range(n))[1]
         exact_away = min((-value(j, u), j) for j in atoms)[1]
         bad += (js != exact) or (away != exact_away)
@@ -149,17 +156,21 @@ def _mismatches(seed, trials, drop=None):
 
 
 def test_model_follows_the_kernel_constants():
-    """The hand-over takes the columns of u-2 and u-1 (three chain warps), the
-    other changed columns are the ones of u-CHAIN .. u-LAG."""
-    assert CHAIN == 3 and LAG >= CHAIN
+    """The kernel is built for one chain warp or three in rotation; with
+    three the hand-over takes the columns of u-2 and u-1, the other changed
+    columns are the ones of u-CHAIN .. u-LAG."""
+    assert CHAINS == (1, 3) and LAG >= max(CHAINS)
 
 
-def test_speculative_repair_gives_the_exact_lmo():
-    assert _mismatches(2103, 4000) == 0
+@pytest.mark.parametrize("chain", [1, 3])
+def test_speculative_repair_gives_the_exact_lmo(chain):
+    assert _mismatches(2103, 4000, chain) == 0
 
 
-def test_each_repair_is_needed():
+@pytest.mark.parametrize("chain", [1, 3])
+def test_each_repair_is_needed(chain):
     """Leaving out any one repair makes the model return wrong LMOs on the
     same kind of draws, so the test above has something to catch."""
-    for drop in ("stale", "history", "c2", "c1", "atoms"):
-        assert _mismatches(7, 1500, drop) > 0, drop
+    drops = ("stale", "history", "c2", "c1", "atoms") if chain == 3 else ("stale", "history", "atoms")
+    for drop in drops:
+        assert _mismatches(7, 1500, chain, drop) > 0, drop
