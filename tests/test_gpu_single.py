@@ -125,6 +125,58 @@ def test_fp64_dec_trajectory_bit_identical(S, h, oracle_mod, order, epochs):
     assert abs(res["gap"] - ro["g"]) <= 1e-12 * ro["f"]
 
 
+@pytest.mark.parametrize("m,n,order,mode", [(50, 97, "CYCLIC", "pts"), (64, 1, "CYCLIC", "pts"),
+                                             (33, 512, "UNIFORM", "pts"), (300, 65, "PERMUTE", "C"),
+                                             (7, 2, "UNIFORM", "C"), (120, 130, "CYCLIC", "C")])
+def test_fp64_dec_single_warp_kernel_edges(S, h, oracle_mod, m, n, order, mode):
+    """FP64 BCFW rows of width <= 512 run on the single-warp kernel: odd
+    widths (8-byte copies and padded columns), one column, the widest rows it
+    takes, repeated rows in uniform order, given or point costs. The argmin
+    sequence and the plan equal the oracle's bit for bit."""
+    inst = W.colour_instance(m * 7 + n, m, n, rho=10.0, b_dirichlet=True)
+    C = oracle_mod.cost(inst.X, inst.Y)
+    ep, seed = 12, 4
+    To, ro, ti, tj, _ = oracle_mod.solve(C, inst.a, inst.b, rho=inst.rho, variant=oracle_mod.BCFW,
+                                         step=oracle_mod.DEC, order=getattr(oracle_mod, order), seed=seed,
+                                         max_epochs=ep, trace=True)
+    cap = ep * m
+    tr = _trace_buf(cap)
+    T = torch.zeros((m, n), dtype=torch.float64, device="cuda")
+    kw = dict(C=dev(C, torch.float64)) if mode == "C" else dict(X=dev(inst.X, torch.float64),
+                                                                 Y=dev(inst.Y, torch.float64))
+    res = h.solve(dev(inst.a, torch.float64), dev(inst.b, torch.float64), T, precision=S.FP64, variant=S.BCFW,
+                  step=S.DEC, order=getattr(S, order), seed=seed, rho=inst.rho, max_epochs=ep, trace=tr,
+                  trace_capacity=cap, **kw)
+    trh = tr.cpu().numpy().reshape(-1, 4)
+    np.testing.assert_array_equal(trh[:, 0], ti)
+    np.testing.assert_array_equal(trh[:, 1], tj)
+    np.testing.assert_array_equal(host(T), To)
+    assert rel(res["objective"], ro["f"]) <= 1e-13
+
+
+@pytest.mark.parametrize("order", ["CYCLIC", "UNIFORM"])
+def test_fp64_line_search_single_warp_kernel(S, h, oracle_mod, order):
+    """FP64 BCFW with the exact line search (eq. 8) on the single-warp
+    kernel: the same trajectory as the oracle up to the order of the two dot
+    products."""
+    inst = W.colour_instance(15, 180, 300, rho=10.0, b_dirichlet=True)
+    C = oracle_mod.cost(inst.X, inst.Y)
+    ep = 15
+    To, ro, _, tj, _ = oracle_mod.solve(C, inst.a, inst.b, rho=inst.rho, variant=oracle_mod.BCFW,
+                                        step=oracle_mod.ELS, order=getattr(oracle_mod, order), seed=2,
+                                        max_epochs=ep, trace=True)
+    cap = ep * 180
+    tr = _trace_buf(cap)
+    T = torch.zeros((180, 300), dtype=torch.float64, device="cuda")
+    res = h.solve(dev(inst.a, torch.float64), dev(inst.b, torch.float64), T, X=dev(inst.X, torch.float64),
+                  Y=dev(inst.Y, torch.float64), precision=S.FP64, variant=S.BCFW, step=S.ELS,
+                  order=getattr(S, order), seed=2, rho=inst.rho, max_epochs=ep, trace=tr, trace_capacity=cap)
+    js = tr.cpu().numpy().reshape(-1, 4)[:, 1]
+    assert rel(res["objective"], ro["f"]) <= 1e-10
+    assert np.abs(host(T) - To).max() <= 1e-10
+    assert (js != tj).mean() <= 0.01
+
+
 @pytest.mark.parametrize("d,order", [(3, "CYCLIC"), (5, "PERMUTE")])
 def test_fp64_euclidean_cost_trajectory_bit_identical(S, h, oracle_mod, d, order):
     """The paper's cost ||x_i - y_j||_2 (Sec. 5.1) from points: the argmin
@@ -298,17 +350,82 @@ def near_tie(C, a, T, r, i, rho, variant, tol_rel=2e-6):
     return None
 
 
+def _gpu_direction(variant, tie, oracle_dir):
+    """The direction the GPU took at an update whose decision differed from
+    the oracle's at a near tie: BCFW always steps toward the LMO vertex and
+    BCPFW always moves mass pairwise; a BCAFW step changes direction only
+    when the tie was the choice between the FW and the away direction."""
+    if variant == "BCFW":
+        return 0
+    if variant == "BCPFW":
+        return 2
+    return (1 - oracle_dir) if (tie == "FW or away" and oracle_dir in (0, 1)) else oracle_dir
+
+
+EPS32 = 2.0 ** -24   # unit roundoff of binary32
+NEGLIGIBLE = 1e-6    # an atom lighter than this fraction of a_i is below what an FP32 step resolves
+
+
+def fp32_step_allowance(C, a, T, r, i, rho, direction, js, v, gam):
+    """How far an FP32 step size gamma may lie from the FP64 one for the same
+    decision: the line-search numerator (eq. 8 / eq. 10) is a difference of
+    sums of O(|supp| + 2) terms of size t_ij |grad_ij|, each carrying a few
+    FP32 roundings (cost, residual, product, sum), so its absolute error is
+    bounded by ~8 (|supp| + 4) eps32 times the sum of the magnitudes; gamma
+    inherits that error divided by the curvature, plus the same relative
+    error of the curvature itself."""
+    g = C[i] + rho * r
+    t = T[i]
+    ai = a[i]
+    supp = np.nonzero(t > 0)[0]
+    k = 8.0 * (len(supp) + 4) * EPS32
+    rel_gam = k
+    if direction == 2:  # pairwise: numerator a_i (g_v - g_js), curvature 2 a_i^2 rho
+        den = rho * 2.0 * ai * ai
+        mag = ai * (abs(g[v]) + abs(g[js]))
+    else:  # FW or away: numerator <t, g> - a_i g_js (or a_i g_v - <t, g>)
+        d = -t.copy() if direction == 0 else t.copy()
+        d[js if direction == 0 else v] += ai if direction == 0 else -ai
+        den = rho * float(d @ d)
+        mag = float(t @ np.abs(g)) + ai * abs(g[js if direction == 0 else v])
+        if direction == 1 and ai > t[v]:
+            # the away curvature holds (a_i - t_v)^2, which the dense FP32 kernel
+            # takes from the stored mass of the other atoms: its error -- a few
+            # roundings of the row's mass, plus the row's drift from a_i -- is
+            # relative to a_i - t_v
+            drift = abs(float(t.sum()) - ai)
+            rel_gam = k + 2.0 * (drift + k * ai) / (ai - t[v])
+    if not den > 0:
+        return np.inf
+    return k * mag / den + rel_gam * abs(gam)
+
+
 def replay_epochs(S, h, O, inst, C, kw, variant, step, order, epochs, prec=None, seed=3,
-                  dense_only=0, T0=None):
+                  dense_only=0, T0=None, max_tie_frac=0.05):
     """Run `epochs` epochs one at a time; before each, the oracle starts from
-    the GPU's current plan. Within an epoch the GPU's decisions (block i,
-    LMO vertex j*, away vertex v, step gamma; from the device trace) are
-    compared update by update with the oracle's block steps. They must agree
-    until the first update where a discrete decision is a near tie at the
-    oracle's state (which FP32 cannot order); the epoch is then accepted
-    without further comparison. Epochs without a tie must reproduce the
-    oracle's plan to 1e-6 and its objective to 1e-5. Returns the number of
-    epochs that ended at a tie."""
+    the GPU's current plan. Within an epoch every GPU decision (block i, LMO
+    vertex j*, away vertex v, step gamma; from the device trace) is compared
+    with the oracle's block step at the same state, update by update:
+      - the same vertices and gamma within 1e-7 + 1e-5 gamma (in units of
+        a_i): the oracle's step stands;
+      - the same vertices and gamma within what FP32 resolves for this step
+        (fp32_step_allowance: the line-search numerator cancels when the row
+        is nearly converged, the away curvature when alpha_v is near 1) -- an
+        "ill-conditioned step" (not a different decision, and not counted as
+        one);
+      - other vertices: the decision must be a near tie at the oracle's state
+        (one FP32 cannot order, see near_tie), or the vertex that differs is an
+        atom lighter than 1e-6 a_i on one side (a mass below FP32 resolution
+        that one run holds and the other rounded away).
+    In the last two cases the oracle adopts the GPU's decision for that update
+    (its own update arithmetic applied to the GPU's j*, v and gamma; a step
+    within FP32 rounding of gamma_max is taken as the drop it was, and atoms
+    below FP32 resolution in the row are cleared first), and the comparison
+    goes on with the next update, so no update of the epoch goes unchecked.
+    Every epoch must end with the oracle's plan within 1e-6 of the GPU's and
+    its objective within 1e-5. Adopted different decisions may not exceed
+    `max_tie_frac` of the updates (at least 2). Returns the per-epoch numbers
+    of adopted different decisions."""
     prec = S.FP32 if prec is None else prec
     dt = torch.float32 if prec != S.FP64 else torch.float64
     m, n = inst.m, inst.n
@@ -320,7 +437,9 @@ def replay_epochs(S, h, O, inst, C, kw, variant, step, order, epochs, prec=None,
         T = dev(T0, dt)
         start = host(T)
     var_o, step_o, order_o = getattr(O, variant), getattr(O, step), getattr(O, order)
-    ties = 0
+    ties = []
+    kinds = {}
+    steps_ill = 0
     for ep in range(epochs):
         tr = torch.full((4 * m,), -1, dtype=torch.int32, device="cuda")
         res = h.solve(dev(inst.a, dt), dev(inst.b, dt), T, warm_start=ep > 0 or T0 is not None,
@@ -334,29 +453,61 @@ def replay_epochs(S, h, O, inst, C, kw, variant, step, order, epochs, prec=None,
         np.testing.assert_array_equal(gi, ti)  # same block order
         assert Tg.min() >= 0.0
         np.testing.assert_allclose(Tg.sum(1), inst.a, rtol=2e-5, atol=0)
-        assert rel(res["objective"], ro["f"]) <= 1e-3  # gross check, holds across ties
+        assert rel(res["objective"], ro["f"]) <= 1e-3  # free-running oracle epoch: gross check
         Tr = start.copy()
         rr = Tr.sum(0) - inst.b
-        tie = None
+        nt = 0
         for p in range(m):
             i = int(ti[p])
+            ai = inst.a[i]
             row_before, r_before = Tr[i].copy(), rr.copy()
-            js, v, _, gam = O.block_step(C, inst.a, Tr, rr, i, p, variant=var_o, step=step_o,
-                                         rho=inst.rho)
-            same = gj[p] == js and (variant == "BCFW" or gv[p] == v or abs(gam) + abs(gg[p]) == 0)
-            same = same and abs(gg[p] - gam) * inst.a[i] <= 1e-7 + 1e-5 * abs(gam) * inst.a[i]
-            if not same:
-                Tpre = Tr.copy()
-                Tpre[i] = row_before
+            js, v, dr, gam = O.block_step(C, inst.a, Tr, rr, i, p, variant=var_o, step=step_o,
+                                          rho=inst.rho)
+            if gam == 0.0 and gg[p] == 0.0:
+                continue  # neither moved: the state is the same whatever vertex was named
+            same_vertices = gj[p] == js and (variant == "BCFW" or gv[p] == v)
+            if same_vertices and abs(gg[p] - gam) * ai <= 1e-7 + 1e-5 * abs(gam) * ai:
+                continue
+            Tpre = Tr.copy()
+            Tpre[i] = row_before
+            if same_vertices:
+                tie = "ill-conditioned step" if abs(gg[p] - gam) <= fp32_step_allowance(
+                    C, inst.a, Tpre, r_before, i, inst.rho, dr, js, v, gam) else None
+                tie = near_tie(C, inst.a, Tpre, r_before, i, inst.rho, variant) if tie is None else tie
+            else:
                 tie = near_tie(C, inst.a, Tpre, r_before, i, inst.rho, variant)
-                assert tie is not None, (ep, p, i, (gj[p], js), (gv[p], v), (gg[p], gam))
-                break
-        if tie is None:
-            assert np.abs(Tg - Tr).max() <= T_ATOL, ep
-            assert rel(res["objective"], ro["f"]) <= OBJ_RTOL, ep
-        else:
-            ties += 1
+                if tie is None and variant != "BCFW":
+                    light = lambda c: 0 <= c < n and row_before[c] <= NEGLIGIBLE * ai
+                    if light(int(gv[p])) or light(v):
+                        tie = "negligible atom"
+            assert tie is not None, (ep, p, i, (gj[p], js), (gv[p], v), (gg[p], gam))
+            kinds[tie] = kinds.get(tie, 0) + 1
+            if tie == "ill-conditioned step":
+                steps_ill += 1  # the same decision, a step FP32 resolves only this far
+            else:
+                nt += 1
+            # follow the GPU's decision from here on
+            Tr[i] = row_before
+            rr[:] = r_before
+            light = (Tr[i] > 0) & (Tr[i] <= NEGLIGIBLE * ai)
+            rr[light] -= Tr[i][light]
+            Tr[i][light] = 0.0
+            gdir, gam_g = _gpu_direction(variant, tie, dr), float(gg[p])
+            gvc = int(gv[p])
+            if gdir in (1, 2) and 0 <= gvc < n and Tr[i, gvc] > 0:
+                alpha = Tr[i, gvc] / ai
+                gmax = alpha if gdir == 2 else alpha / (1.0 - alpha)
+                if gam_g >= gmax * (1.0 - 1e-6):
+                    gam_g = gmax  # the GPU dropped the atom
+                elif tie == "drop" and gam >= gmax:
+                    gam_g = min(gam_g, float(np.nextafter(gmax, 0.0)))  # the GPU kept it
+            O.apply_step(inst.a, Tr, rr, i, gdir, int(gj[p]), gvc, gam_g)
+        ties.append(nt)
+        assert np.abs(Tg - Tr).max() <= T_ATOL, (ep, np.abs(Tg - Tr).max(), nt)
+        fr = O.certificate(C, inst.a, inst.b, inst.rho, Tr)["f"]
+        assert rel(res["objective"], fr) <= OBJ_RTOL, (ep, res["objective"], fr, nt)
         start = Tg
+    assert sum(ties) <= max(2, max_tie_frac * m * epochs), (ties, kinds)
     return ties
 
 
@@ -453,7 +604,8 @@ def test_pairwise_overflow_mid_epoch_all_kernels(S, h, oracle_mod, order):
     T0 = f32(T0)
     ep = 3
     out = []
-    for ek in (S.EPOCH_TWO_PHASE, S.EPOCH_PIPELINED, S.EPOCH_SPECULATIVE):
+    for ek in (S.EPOCH_TWO_PHASE, S.EPOCH_PIPELINED, S.EPOCH_SPECULATIVE, S.EPOCH_SPECULATIVE_ONE_CHAIN,
+               S.EPOCH_SPECULATIVE_SPLIT):
         cap = ep * m
         tr = torch.full((4 * cap,), -1, dtype=torch.int32, device="cuda")
         T = dev(T0, torch.float32).contiguous()
@@ -463,7 +615,7 @@ def test_pairwise_overflow_mid_epoch_all_kernels(S, h, oracle_mod, order):
                       trace=tr, trace_capacity=cap, epoch_kernel=ek)
         assert res["status"] in (S.OK, S.NOT_CONVERGED), res
         out.append((tr.cpu().numpy(), T.cpu().numpy()))
-    for k in (1, 2):
+    for k in (1, 2, 3, 4):
         np.testing.assert_array_equal(out[0][0], out[k][0])
         np.testing.assert_array_equal(out[0][1], out[k][1])
     tr0 = out[0][0].reshape(-1, 4)
@@ -492,7 +644,43 @@ def test_fp32_full_size_colour4096(S, h, oracle_mod, variant, step):
         assert rel(res["objective"], ro["f"]) <= OBJ_RTOL
         assert np.abs(host(T) - To).max() <= T_ATOL
     else:
-        replay_epochs(S, h, oracle_mod, inst, C, kw, variant, step, "CYCLIC", 3)
+        # from T0 the rows are far from converged: FP32 may flip at most 1% of
+        # the decisions
+        replay_epochs(S, h, oracle_mod, inst, C, kw, variant, step, "CYCLIC", 3, max_tie_frac=0.01)
+
+
+def _optima():
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "colour4096_fp32_optima.json")) as fh:
+        return json.load(fh)["optima"]
+
+
+@pytest.mark.parametrize("rho", [1.0, 10.0, 100.0])
+def test_fp32_headline_converged_to_oracle_optimum(S, h, oracle_mod, rho):
+    """colour4096_fp32 solved as the benchmark solves it (BCPFW-ELS, cyclic,
+    FP32 with FP64 certificate, default kernel, rel. gap 1e-6), for rho = 1,
+    10, 100. The returned plan is certified again by the oracle: its gap
+    (Thm 2) is at most 1.2e-6 of its objective, and that objective is within
+    1.2e-6 of the optimal value f* the oracle reached on the same inputs
+    (stored by tests/golden/make_optima.py; f* is unique). The library's own
+    objective agrees with the oracle's evaluation of its plan to the FP32
+    rounding of the cost entries."""
+    opt = _optima()[f"{rho:g}"]
+    inst = W.workload("colour4096_fp32").rounded()
+    C = oracle_mod.cost(inst.X, inst.Y)
+    T = torch.zeros((inst.m, inst.n), dtype=torch.float32, device="cuda")
+    res = h.solve(dev(inst.a, torch.float32), dev(inst.b, torch.float32), T, X=dev(inst.X, torch.float32),
+                  Y=dev(inst.Y, torch.float32), precision=S.FP32, variant=S.BCPFW, step=S.ELS, order=S.CYCLIC,
+                  rho=rho, tol_rel_gap=1e-6, max_epochs=6000, gap_every=1, refresh_every=1)
+    assert res["status"] == S.OK and res["rel_gap"] <= 1e-6, res
+    cert = oracle_mod.certificate(C, inst.a, inst.b, rho, host(T))
+    assert cert["g"] <= 1.2e-6 * cert["f"], (cert["g"] / cert["f"], res)
+    # below f* only by what the FP32 row sums' rounding allows (the plan is
+    # feasible to ~1e-7 of a_i)
+    assert opt["f_lower"] * (1 - 2e-7) <= cert["f"] <= opt["f"] * (1 + 1.2e-6), (cert["f"], opt)
+    assert rel(res["objective"], cert["f"]) <= 2e-7
+    assert abs(res["gap"] - cert["g"]) <= 2e-7 * cert["f"]
 
 
 def test_fp32_reaches_relative_gap(S, h, oracle_mod):
@@ -592,6 +780,61 @@ def test_errors(S, h):
     assert res["status"] == S.OK
 
 
+def test_bounded_wait_times_out_and_handle_stays_usable(S, h):
+    """The speculative epoch kernel's waits are bounded. With a start gate
+    that nothing opens and a limit of 2000 probes, its first wait runs out:
+    the kernel stops without making an update, the call returns
+    SR_OT_ETIMEOUT, and the same handle and stream then solve normally -- the
+    result equal, bit for bit, to a solve on a fresh handle and to a solve
+    through an opened gate."""
+    inst = W.colour_instance(61, 300, 500, rho=10.0, b_dirichlet=True).rounded()
+    a, b = dev(inst.a, torch.float32), dev(inst.b, torch.float32)
+    X, Y = dev(inst.X, torch.float32), dev(inst.Y, torch.float32)
+    kw = dict(precision=S.FP32, variant=S.BCPFW, step=S.ELS, rho=10.0, max_epochs=4,
+              epoch_kernel=S.EPOCH_SPECULATIVE)
+    gate = torch.zeros(1, dtype=torch.int32, device="cuda")
+    T = torch.zeros((inst.m, inst.n), dtype=torch.float32, device="cuda")
+    st, _ = h.solve_raw(a, b, T, X=X, Y=Y, start_gate=gate, spin_limit=2000, **kw)
+    assert st == S.ETIMEOUT and "bounded device wait" in h.last_error()
+    Tz = host(T)
+    assert np.all(Tz[:, 1:] == 0.0) and np.allclose(Tz[:, 0], inst.a)  # no update was made
+    res = h.solve(a, b, T, X=X, Y=Y, **kw)
+    h2 = S.Handle(0)
+    T2 = torch.zeros_like(T)
+    res2 = h2.solve(a, b, T2, X=X, Y=Y, **kw)
+    h2.close()
+    assert torch.equal(T, T2) and res["objective"] == res2["objective"]
+    gate.fill_(1)
+    T3 = torch.zeros_like(T)
+    res3 = h.solve(a, b, T3, X=X, Y=Y, start_gate=gate, spin_limit=2000, **kw)
+    assert torch.equal(T, T3) and res3["objective"] == res["objective"]
+    st, _ = h.solve_raw(a, b, T3, X=X, Y=Y, spin_limit=-1, **kw)
+    assert st == S.EINVAL
+
+
+def test_reading_b_lambda_as_inverse_weight(S, h, oracle_mod):
+    """The paper's weight is 1/(2 lambda) (Sec. 3, eq. 5): read literally, the
+    workload's "lambda = 10" is rho = 1/10. colour256_fp64 at rho = 0.1,
+    BCFW-DEC, 200 epochs: argmin sequence and plan bit-identical to the
+    oracle, as for rho = 10."""
+    inst = W.workload("colour256_fp64")
+    m, n, rho = inst.m, inst.n, 0.1
+    C = oracle_mod.cost(inst.X, inst.Y)
+    To, ro, ti, tj, _ = oracle_mod.solve(C, inst.a, inst.b, rho=rho, variant=oracle_mod.BCFW,
+                                         step=oracle_mod.DEC, max_epochs=200, trace=True)
+    cap = 200 * m
+    tr = _trace_buf(cap)
+    T = torch.zeros((m, n), dtype=torch.float64, device="cuda")
+    res = h.solve(dev(inst.a, torch.float64), dev(inst.b, torch.float64), T, X=dev(inst.X, torch.float64),
+                  Y=dev(inst.Y, torch.float64), precision=S.FP64, variant=S.BCFW, step=S.DEC, rho=rho,
+                  max_epochs=200, trace=tr, trace_capacity=cap)
+    trh = tr.cpu().numpy().reshape(-1, 4)
+    np.testing.assert_array_equal(trh[:, 0], ti)
+    np.testing.assert_array_equal(trh[:, 1], tj)
+    np.testing.assert_array_equal(host(T), To)
+    assert rel(res["objective"], ro["f"]) <= 1e-13
+
+
 def test_not_converged_status(S, h):
     m, n = 64, 64
     inst = W.colour_instance(1, m, n)
@@ -642,7 +885,8 @@ def test_pairwise_kernels_match_two_phase(S, h, oracle_mod, order, m, n, ep, mod
     inst = W.colour_instance(17 + m, m, n, rho=10.0, b_dirichlet=True).rounded()
     C = dev(oracle_mod.cost(inst.X, inst.Y), torch.float32) if mode == "cost" else None
     out = []
-    for ek in (S.EPOCH_TWO_PHASE, S.EPOCH_PIPELINED, S.EPOCH_SPECULATIVE):
+    for ek in (S.EPOCH_TWO_PHASE, S.EPOCH_PIPELINED, S.EPOCH_SPECULATIVE, S.EPOCH_SPECULATIVE_ONE_CHAIN,
+               S.EPOCH_SPECULATIVE_SPLIT):
         cap = ep * m
         tr = torch.full((4 * cap,), -1, dtype=torch.int32, device="cuda")
         T = torch.zeros((m, n), dtype=torch.float32, device="cuda")
@@ -652,7 +896,19 @@ def test_pairwise_kernels_match_two_phase(S, h, oracle_mod, order, m, n, ep, mod
                       max_epochs=ep, trace=tr, trace_capacity=cap, epoch_kernel=ek, **kw)
         assert res["status"] in (S.OK, S.NOT_CONVERGED), res
         out.append((tr.cpu().numpy(), T.cpu().numpy(), res))
-    for k in (1, 2):
+    for k in (1, 2, 3, 4):
         np.testing.assert_array_equal(out[0][0], out[k][0])
         np.testing.assert_array_equal(out[0][1], out[k][1])
         assert out[0][2]["objective"] == out[k][2]["objective"]
+
+
+def test_chain_floor_probe(S, h):
+    """The chain-floor probe (observability) runs its dependent hand-overs
+    to the end for one and three chain warps and reports a positive time per
+    update below that of any real block update; bad arguments are refused."""
+    for cw in (1, 3):
+        ns = h.chain_floor(cw, 1 << 14)
+        assert 1.0 < ns < 5000.0, (cw, ns)
+    r = S.ct.c_double()
+    assert S.lib.sr_ot_profile_chain_floor(h._h, 2, 100, S.ct.byref(r)) == S.EINVAL
+    assert S.lib.sr_ot_profile_chain_floor(h._h, 3, 0, S.ct.byref(r)) == S.EINVAL
