@@ -93,6 +93,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--instances", type=int, default=None,
                     help="batched workloads: use only the first K instances (small profiling cases)")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="colour4096_fp32: skip the variant x rho grid")
+    ap.add_argument("--no-protocol", action="store_true",
+                    help="colour_batch64_2048: skip the 100-step gradient descent on X")
     return ap.parse_args()
 
 
@@ -290,6 +294,130 @@ def config_for(args, s, insts, ws):
 
 
 # ---------------------------------------------------------------------------
+# CPU-baseline leg, second part: the FP64 oracle certifies plans the GPU
+# returned (outside every timed region; rank 0 only; skipped with
+# --no-cpu-baseline). The oracle's certificate (Thm 2) of a plan bounds its
+# distance to the optimum, and the stored optimal values (written by
+# tests/golden/make_optima.py from the oracle alone) give f* itself.
+# ---------------------------------------------------------------------------
+def golden_optima(workload):
+    p = os.path.join(ROOT, "tests", "golden", f"{workload}_optima.json")
+    if not os.path.exists(p):
+        return {}
+    with open(p) as fh:
+        return json.load(fh)["optima"]
+
+
+class OracleCheck:
+    def __init__(self, inst, workload):
+        from oracle import oracle as O
+        O.build()
+        self.O = O
+        self.inst = inst
+        self.C = O.cost(inst.X, inst.Y)
+        self.optima = golden_optima(workload)
+
+    def __call__(self, T_dev, rho, reported):
+        Th = T_dev.detach().to("cpu").double().numpy()
+        c = self.O.certificate(self.C, self.inst.a, self.inst.b, rho, Th)
+        out = {"rel_gap": c["g"] / c["f"], "objective": c["f"],
+               "library_objective_rel_err": abs(reported["objective"] - c["f"]) / abs(c["f"])}
+        opt = self.optima.get(f"{rho:g}")
+        if opt:
+            out["f_star"] = opt["f"]
+            out["objective_vs_f_star"] = (c["f"] - opt["f"]) / opt["f"]
+        return out
+
+
+def colour256_checks(h, S, inst, s, T, X, Y, reported):
+    """colour256_fp64: the oracle's own run of the same solve (BCFW with the
+    decay rule, cyclic, FP64) must give the GPU's plan bit for bit; and the
+    paper's metrics (v) and (vi) of that plan against the exact LP plan T*_LP
+    (the oracle's LP solve), computed on the GPU by sr_ot_lp_metrics and
+    checked against the oracle's own evaluation."""
+    import torch
+    from oracle import oracle as O
+    O.build()
+    C = O.cost(inst.X, inst.Y)
+    To, ro, *_ = O.solve(C, inst.a, inst.b, rho=inst.rho, variant=VARIANTS[s["variant"]],
+                         step=1 if s["step"] == "ELS" else 0, max_epochs=s["max_epochs"])
+    Tg = T.detach().cpu().numpy()
+    out = {"plan_bit_identical": bool(np.array_equal(Tg, To)), "max_abs_plan_diff": float(np.abs(Tg - To).max()),
+           "objective_rel_err": abs(reported["objective"] - ro["f"]) / abs(ro["f"])}
+    L = O.transport_lp(C, inst.a, inst.b)
+    g = h.lp_metrics(T, torch.as_tensor(L, dtype=torch.float64, device=T.device), X=X, Y=Y, precision=S.FP64)
+    o = O.lp_metrics(C, Tg, L)
+    out["lp_metrics"] = {"e_m": g["e_m"], "e_v": g["e_v"], "lp_value": g["lp_value"],
+                         "e_m_rel_err_vs_oracle": abs(g["e_m"] - o["e_m"]) / o["e_m"],
+                         "e_v_abs_err_vs_oracle": abs(g["e_v"] - o["e_v"]),
+                         "reference": "T*_LP of the unrelaxed problem, oracle LP solve (Sec. 5, metrics v, vi)"}
+    return out
+
+
+def feature_checks(inst, T, reported):
+    """feature8192_d128: the oracle's certificate (Thm 2, FP64) of the GPU's
+    plan under the cost the library approximates -- the squared distances of
+    the BF16-rounded points -- and under the exact inputs' cost (the error of
+    the mixed-precision form against the FP64 problem)."""
+    from oracle import oracle as O
+    from paper_2103_05857_gb300 import workloads as W
+    O.build()
+    Tg = T.detach().to("cpu").double().numpy()
+    exact = W.workload("feature8192_d128")
+    out = {}
+    for key, X, Y in (("bf16_rounded_inputs", W.bf16_round(inst.X), W.bf16_round(inst.Y)),
+                      ("exact_inputs", exact.X, exact.Y)):
+        C = O.cost(X, Y)
+        c = O.certificate(C, inst.a, inst.b, inst.rho, Tg)
+        out[key] = {"rel_gap": c["g"] / c["f"], "objective": c["f"],
+                    "library_objective_rel_err": abs(reported["objective"] - c["f"]) / abs(c["f"])}
+        del C
+    return out
+
+
+# The variant grid on colour4096_fp32: plain BCFW and the paper's three fast
+# variants (Sec. 4: away steps, pairwise steps, gap-adaptive sampling), each
+# with the exact line search, plus pairwise steps in the paper's default
+# uniform order, for rho in {1, 10, 100}; each run to rel. gap 1e-6 or its
+# epoch cap (then the gap reached is reported).
+VARIANT_GRID = [  # label, variant, order, extra options, epoch cap
+    ("BCFW-ELS", "BCFW", "CYCLIC", {}, 600),
+    ("BCAFW-ELS", "BCAFW", "CYCLIC", {}, 3000),
+    ("BCPFW-ELS", "BCPFW", "CYCLIC", {}, 6000),
+    ("BCFW-GAS-ELS", "BCFW", "GAP_ADAPTIVE", {"ga_global_only": 1}, 600),
+    ("BCPFW-U-ELS", "BCPFW", "UNIFORM", {}, 6000),
+]
+GRID_RHOS = (1.0, 10.0, 100.0)
+
+
+def variant_grid(h, S, inst, X, Y, a, b, T, stream, flush, check):
+    import torch
+    cells = []
+    for label, var, order, extra, cap in VARIANT_GRID:
+        for rho in GRID_RHOS:
+            opts = S.options(variant=VARIANTS[var], step=S.ELS, order=getattr(S, order), precision=S.FP32,
+                             rho=rho, tol_rel_gap=1e-6, max_epochs=cap, gap_every=1, refresh_every=1,
+                             seed=7, **extra)
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = h.solve(a, b, T, X=X, Y=Y, opts=opts)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3
+            cell = {"variant": label, "rho": rho, "converged": r["status"] == S.OK, "seconds": sec,
+                    "epochs": r["epochs"], "rel_gap": r["rel_gap"],
+                    "block_updates_per_s": r["block_updates"] / sec}
+            if check is not None:
+                cell["oracle_check"] = check(T, rho, r)
+            cells.append(cell)
+    return {"workload": "colour4096_fp32", "tol_rel_gap": 1e-6, "step": "ELS", "seed": 7,
+            "note": "seconds = time to the tolerance when converged, else to the epoch cap (rel_gap then "
+                    "is the gap reached)", "cells": cells}
+
+
+# ---------------------------------------------------------------------------
 def bench_reference(args, ws, rank):
     """The oracle timed on the host cores: K steps, each a bounded sample."""
     if rank != 0:
@@ -392,7 +520,7 @@ def hbm_roofline(nbytes, avg_ms, peaks, peak_src, kernel, extra=None):
     return r
 
 
-def bench_single(args, s, ws, rank, local):
+def bench_single(args, s, ws, rank, local, cpu_leg):
     """One instance per rank (replicas): colour4096_fp32, colour256_fp64,
     feature8192_d128."""
     import torch
@@ -450,6 +578,11 @@ def bench_single(args, s, ws, rank, local):
     extra = {"launches": ep_n, "chain_ns_per_update": 1e6 * avg / m, "cert_avg_ms": ce_ms / max(ce_n, 1),
              "hbm_bytes_per_update": 8 * supp, "mean_support": supp}
     kname = epoch_kernel_name(s, n)
+    if kname.startswith("k_epoch_spec"):
+        # the chain alone, with the same hand-over (and with one warp, none)
+        floor3 = h.chain_floor(3)
+        extra.update(chain_floor_ns=floor3, chain_floor_ns_one_warp=h.chain_floor(1),
+                     chain_frac=floor3 / extra["chain_ns_per_update"])
     roof = alu_roofline(FLOPS_PER_GRAD * n * m, avg, peaks, peak_src, kname, extra)
     cfg = config_for(args, s, inst, ws)
     line = {"metric": metric_for(s),
@@ -462,6 +595,16 @@ def bench_single(args, s, ws, rank, local):
             "converged": all(r["status"] == 0 for r in out),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "roofline": roof, "clocks": clk}
+    check = None
+    if cpu_leg and args.workload == "colour4096_fp32":
+        check = OracleCheck(inst, args.workload)
+        line["oracle_check"] = check(T, inst.rho, out[-1])
+    elif cpu_leg and args.workload == "colour256_fp64":
+        line["oracle_check"] = colour256_checks(h, S, inst, s, T, X, Y, out[-1])
+    elif cpu_leg and args.workload == "feature8192_d128":
+        line["oracle_check"] = feature_checks(inst, T, out[-1])
+    if args.workload == "colour4096_fp32" and ws == 1 and not args.no_variants:
+        line["variants"] = variant_grid(h, S, inst, X, Y, a, b, T, stream, H.flush, check)
     if co_n:
         co_avg = co_ms / co_n
         line["roofline_cost"] = hbm_roofline(4.0 * m * n + 4.0 * (m + n) * d + 2.0 * (m + n) * d, co_avg,
@@ -469,6 +612,44 @@ def bench_single(args, s, ws, rank, local):
                                              {"tflops_bf16": 2.0 * m * n * d / (co_avg / 1e3) / 1e12})
     h.close()
     return line, inst
+
+
+def gd_protocol(h, S, pb, insts, kw, stream, steps=100):
+    """The differentiable form in use: 100 steps of gradient descent on the
+    source points X of the whole batch, X <- X - lr dX with dX the envelope
+    gradient (sr_ot_grad_batched) at the current plans, each step followed by
+    a batched solve warm-started from the previous plans (batch_warm_start).
+    lr = 0.025 m moves every x_i 5 % of the way to its barycentric projection
+    (dX_i = 2 a_i (x_i - x^_i), a_i = 1/m), i.e. gradient descent on the sum
+    of the instances' optimal values, which must not increase."""
+    import torch
+    m = insts[0].m
+    lr = 0.025 * m
+    X = pb.X.clone()
+    T = pb.T  # converged plans of the timed solves
+    _, res0 = h.solve_batched(X, pb.Y, pb.a, pb.b, T, pb.sizes, pb.offsets, batch_warm_start=1, **kw)
+    vals = [sum(r["objective"] for r in res0)]
+    epochs, conv = [], True
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        g = h.grad_batched(X, pb.Y, pb.b, T, pb.sizes, pb.offsets, want=("dX",), rho=insts[0].rho,
+                           precision=S.FP32)
+        X.sub_(lr * g["dX"])
+        _, res = h.solve_batched(X, pb.Y, pb.a, pb.b, T, pb.sizes, pb.offsets, batch_warm_start=1, **kw)
+        vals.append(sum(r["objective"] for r in res))
+        epochs.append(float(np.median([r["epochs"] for r in res])))
+        conv = conv and all(r["status"] == 0 for r in res)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    incr = [b - a for a, b in zip(vals, vals[1:])]
+    return {"steps": steps, "lr": lr, "objective_sum_start": vals[0], "objective_sum_end": vals[-1],
+            "non_increasing_steps": sum(d <= 1e-6 * abs(vals[0]) for d in incr), "seconds": sec,
+            "ms_per_step": 1e3 * sec / steps, "warm_solve_epochs_median": float(np.median(epochs)),
+            "all_converged": conv,
+            "note": "each step: adjoint at the current plans, X update, batched solve warm-started from them"}
 
 
 def bench_batch(args, s, ws, rank, local):
@@ -523,9 +704,16 @@ def bench_batch(args, s, ws, rank, local):
     peaks, peak_src = measured_peaks()
     b_ms, b_n = prof[S.PROF_BATCH]
     flops = FLOPS_PER_GRAD * sum(r["block_updates"] * insts[k].n for res in out for k, r in enumerate(res))
-    roof = alu_roofline(flops / max(len(out), 1), b_ms / max(b_n, 1), peaks, peak_src,
+    # the makespan is set by the instance with the most block updates: its
+    # mean time per update if it ran from the first to the last moment
+    longest = max(r["block_updates"] for r in out[-1])
+    batch_ms = b_ms / max(b_n, 1)
+    floor3 = h.chain_floor(3)
+    roof = alu_roofline(flops / max(len(out), 1), batch_ms, peaks, peak_src,
                         "k_batched (persistent, one CTA per instance at a time)",
-                        {"launches": b_n, "instances": len(insts)})
+                        {"launches": b_n, "instances": len(insts), "longest_chain_updates": longest,
+                         "longest_chain_ns_per_update": 1e6 * batch_ms / longest,
+                         "chain_floor_ns": floor3, "chain_frac": floor3 / (1e6 * batch_ms / longest)})
     res0 = out[-1]
     line = {"metric": metric_for(s),
             "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -537,11 +725,13 @@ def bench_batch(args, s, ws, rank, local):
             "epochs_max": max(r["epochs"] for r in res0), "epochs_median": float(np.median([r["epochs"] for r in res0])),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "roofline": roof, "clocks": clk}
-    # the same instances solved one after another on the single-instance path
-    # (sr_ot_solve, same rule and tolerance): 32 evenly spaced instances,
+    # the plain GPU form: the same instances solved one after another on the
+    # single-instance path (sr_ot_solve, same rule and tolerance; with the
+    # backward pass, sr_ot_grad after each): evenly spaced instances,
     # extrapolated to the whole share by their block updates
-    if not backward:
-        sample = list(range(0, len(insts), max(1, len(insts) // 32)))[:32]
+    if True:
+        nsamp = 8 if backward else 32
+        sample = list(range(0, len(insts), max(1, len(insts) // nsamp)))[:nsamp]
         seq_upd, seq_ms = 0, 0.0
         for k in sample:
             inst = insts[k]
@@ -553,6 +743,8 @@ def bench_batch(args, s, ws, rank, local):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             r = h.solve(as_, bs, Ts, X=Xs, Y=Ys, precision=S.FP32, **kw)
+            if backward:
+                h.grad(Ts, X=Xs, Y=Ys, b=bs, precision=S.FP32, rho=insts[0].rho)
             e1.record(stream)
             torch.cuda.synchronize(dev)
             seq_ms += e0.elapsed_time(e1)
@@ -560,10 +752,13 @@ def bench_batch(args, s, ws, rank, local):
         seq_rate = seq_upd / (seq_ms / 1e3)
         line["sequential_baseline"] = {
             "value": seq_rate, "unit": UNIT,
-            "sample": f"{len(sample)} of {len(insts)} instances solved one after another with sr_ot_solve "
-                      f"({s['variant']}-{s['step']}, same tolerance), {seq_ms / 1e3:.2f} s for {seq_upd} block updates",
+            "sample": f"{len(sample)} of {len(insts)} instances solved one after another with sr_ot_solve"
+                      f"{' and sr_ot_grad' if backward else ''} ({s['variant']}-{s['step']}, same tolerance), "
+                      f"{seq_ms / 1e3:.2f} s for {seq_upd} block updates",
             "extrapolated_s": (updates / len(out)) / seq_rate,
             "batched_speedup": value / seq_rate}
+    if backward and ws == 1 and not args.no_protocol:
+        line["gd_100"] = gd_protocol(h, S, pb, insts, kw, stream)
     g_ms, g_n = prof[S.PROF_GRAD]
     if g_n:
         tbytes = 4.0 * pb.total_T + 4.0 * sum(3 * (i.m + i.n) * 2 + i.n * 2 for i in insts)
@@ -590,10 +785,11 @@ def bench_batch(args, s, ws, rank, local):
 
 def bench_ours(args, ws, rank, local):
     s = settings(args)
+    cpu_leg = rank == 0 and not args.no_cpu_baseline
     if args.workload in BATCH_WORKLOADS:
         line, insts = bench_batch(args, s, ws, rank, local)
     else:
-        line, insts = bench_single(args, s, ws, rank, local)
+        line, insts = bench_single(args, s, ws, rank, local, cpu_leg)
     for key in ("roofline", "roofline_cost", "roofline_adjoint", "roofline_transfer"):
         if key in line:
             line[key]["traffic"] = captured_traffic(args.workload, key)
