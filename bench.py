@@ -230,7 +230,11 @@ def settings(args):
 def epoch_kernel_name(s, n):
     """The epoch kernel the library runs for these settings (its own dispatch:
     speculative for pairwise steps on d = 3 points with n <= 4096, pipelined up
-    to n = 8192, else two-phase; FP64 and BCFW keep the dense-row kernel)."""
+    to n = 8192, else two-phase; FP64 BCFW up to n = 512 runs on one warp;
+    other FP64 and BCFW settings keep the dense-row kernel).""""
+    if s["precision"] == "FP64" and s["variant"] == "BCFW" and n <= 512 and not s.get("ga"):
+        return ("k_epoch_f64w (one warp, m block updates; dense rows, FP32 argmin screen with exact "
+                "FP64 decisions, cost in shared memory)")
     if s["precision"] == "FP64" or s["variant"] == "BCFW":
         return "k_epoch (one CTA, m block updates; dense rows)"
     if s["variant"] == "BCAFW":
@@ -619,12 +623,12 @@ def gd_protocol(h, S, pb, insts, kw, stream, steps=100):
     source points X of the whole batch, X <- X - lr dX with dX the envelope
     gradient (sr_ot_grad_batched) at the current plans, each step followed by
     a batched solve warm-started from the previous plans (batch_warm_start).
-    lr = 0.025 m moves every x_i 5 % of the way to its barycentric projection
+    lr = 0.005 m moves every x_i 1 % of the way to its barycentric projection
     (dX_i = 2 a_i (x_i - x^_i), a_i = 1/m), i.e. gradient descent on the sum
     of the instances' optimal values, which must not increase."""
     import torch
     m = insts[0].m
-    lr = 0.025 * m
+    lr = 0.005 * m
     X = pb.X.clone()
     T = pb.T  # converged plans of the timed solves
     _, res0 = h.solve_batched(X, pb.Y, pb.a, pb.b, T, pb.sizes, pb.offsets, batch_warm_start=1, **kw)

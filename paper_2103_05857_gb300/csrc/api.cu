@@ -571,7 +571,9 @@ sr_ot_status solve_impl(sr_ot_handle h, const sr_ot_options *o, int m, int n, in
                     As.resume = dstat_d + 1;
                     const int ek = o->epoch_kernel;
                     bool ran = false;
-                    if (ek == SR_OT_EPOCH_AUTO || ek == SR_OT_EPOCH_SPECULATIVE)
+                    if (ek == SR_OT_EPOCH_AUTO)  // uniform order: only the split chain takes it
+                        ran = launch_epoch_spec(As, h->stream, o->order == SR_OT_UNIFORM ? kSpecChainSplit : 3);
+                    else if (ek == SR_OT_EPOCH_SPECULATIVE)
                         ran = launch_epoch_spec(As, h->stream, 3);
                     else if (ek == SR_OT_EPOCH_SPECULATIVE_ONE_CHAIN)
                         ran = launch_epoch_spec(As, h->stream, 1);

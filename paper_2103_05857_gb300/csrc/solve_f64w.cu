@@ -20,10 +20,15 @@
 //     on the bit pattern, and rho r_j is recomputed in FP64 only where r_j
 //     changed;
 //   - an FP64 instruction occupies the pipe for about 60 clocks for the whole
-//     warp, however few lanes take part, so the candidates and the row's
-//     support are first compacted onto consecutive lanes (integer ballots)
-//     and each FP64 operation is then issued once per update, not once per
-//     column slot of a lane;
+//     warp, however few lanes take part, so each lane keeps a bit mask of its
+//     candidates and of its non-zero plan entries, and the lanes work through
+//     their masks together: every FP64 operation is issued once per round,
+//     and the rounds are as many as the most entries one lane holds (one,
+//     as a rule), not one per column slot;
+//   - with the decay rule, when the screen leaves a single candidate it is
+//     the exact minimum and no FP64 operation is needed for the LMO at all;
+//   - the step of the next 32 updates (gamma, 1 - gamma, gamma a_i) is
+//     computed one per lane ahead of use;
 //   - the decay step 2m/(k+2m) comes from a table the lanes fill 32 updates
 //     at a time, so no FP64 division sits on the chain;
 //   - one warp, no block barrier: every reduction is a warp reduction.
@@ -32,12 +37,11 @@
 // __ddiv_rn), so the decay-rule trajectory equals that of an FP64 reference
 // written the same way, bit for bit.
 //
-// Lane l owns columns j = 2 (l + 32 g) + e, g < G, e < 2, for the screen.
-// Rows of T, of C and of its FP32 rounding are streamed into a ring
+// Lane l owns the quads j = 4 (l + 32 g) + e, g < G, e < 4 (128-bit shared
+// loads). Rows of T, of C and of its FP32 rounding are streamed into a ring
 // kF64wRing - 2 updates ahead by the lanes that own their columns; the
-// compacted lists are read by any lane after a warp barrier, and the residual
-// state (r_j, rho r_j, fl32(rho r_j)) lives in shared memory. A row that
-// repeats within the window (uniform order) is read again from global
+// residual state (r_j, rho r_j, fl32(rho r_j)) lives in shared memory. A row
+// that repeats within the window (uniform order) is read again from global
 // memory, where it was stored.
 #include <climits>
 #include <limits>
@@ -96,8 +100,8 @@ __global__ void k_round_cost(const double *__restrict__ C, float *__restrict__ C
 
 template <int G>
 __global__ void __launch_bounds__(32, 1) k_epoch_f64w(EpochArgs<double> A) {
-    constexpr int CPL = 2 * G;         // columns per lane
-    constexpr int WID = 64 * G;        // padded row width
+    constexpr int CPL = 4 * G;         // columns per lane: G quads
+    constexpr int WID = 128 * G;       // padded row width
     constexpr int D = kF64wRing - 2;   // rows streamed D updates ahead
     constexpr int SLOT = 2 * WID + WID / 2;  // doubles per slot: T row, C row, FP32 C row
     constexpr unsigned FULL = 0xffffffffu;
@@ -107,18 +111,20 @@ __global__ void __launch_bounds__(32, 1) k_epoch_f64w(EpochArgs<double> A) {
     double *rcol = ring + (size_t)kF64wRing * SLOT;       // r_j
     double *rrs = rcol + WID;                             // rho r_j
     float *rfs = reinterpret_cast<float *>(rrs + WID);    // fl32(rho r_j)
-    int *list = reinterpret_cast<int *>(rfs + WID);       // compacted columns (WID + 32)
     const int m = A.in.m, n = A.in.n;
     const int lane = threadIdx.x;
-    const unsigned lt = (1u << lane) - 1u;
     const double rho = A.rho;
     const bool dec = A.step == SR_OT_DEC;
+    // 16-byte copies: T and C rows (doubles) when n is even and the rows
+    // aligned (A.vec); the FP32 cost quads only when n is also a multiple of
+    // 4, else as two 8-byte halves
     const bool vec = A.vec;
+    const bool vec32 = vec && (n % 4) == 0;
     const float FINF = std::numeric_limits<float>::infinity();
     auto tslot = [&](int s) { return ring + (size_t)s * SLOT; };
     auto cslot = [&](int s) { return ring + (size_t)s * SLOT + WID; };
     auto fslot = [&](int s) { return reinterpret_cast<float *>(ring + (size_t)s * SLOT + 2 * WID); };
-    auto col = [&](int c) { return 2 * (lane + 32 * (c >> 1)) + (c & 1); };
+    auto col = [&](int c) { return 4 * (lane + 32 * (c >> 2)) + (c & 3); };
 
     // residual state per column; padding columns get +inf (never a
     // candidate) and zero plan and cost entries in every slot
@@ -149,14 +155,21 @@ __global__ void __launch_bounds__(32, 1) k_epoch_f64w(EpochArgs<double> A) {
         const float *fsrc = A.C32 + (size_t)i * n;
 #pragma unroll
         for (int g = 0; g < G; ++g) {
-            const int j0 = 2 * (lane + 32 * g);
-            if (vec && j0 + 1 < n) {
+            const int j0 = 4 * (lane + 32 * g);
+            if (vec && j0 + 3 < n) {
                 cpa16(tslot(s) + j0, tsrc + j0);
+                cpa16(tslot(s) + j0 + 2, tsrc + j0 + 2);
                 cpa16(cslot(s) + j0, csrc + j0);
-                cpa8(fslot(s) + j0, fsrc + j0);
+                cpa16(cslot(s) + j0 + 2, csrc + j0 + 2);
+                if (vec32) {
+                    cpa16(fslot(s) + j0, fsrc + j0);
+                } else {
+                    cpa8(fslot(s) + j0, fsrc + j0);
+                    cpa8(fslot(s) + j0 + 2, fsrc + j0 + 2);
+                }
             } else {
 #pragma unroll
-                for (int e = 0; e < 2; ++e)
+                for (int e = 0; e < 4; ++e)
                     if (j0 + e < n) {
                         cpa8(tslot(s) + j0 + e, tsrc + j0 + e);
                         cpa8(cslot(s) + j0 + e, csrc + j0 + e);
@@ -192,8 +205,9 @@ __global__ void __launch_bounds__(32, 1) k_epoch_f64w(EpochArgs<double> A) {
         cpa_commit();
     }
     __syncwarp();
-    double ac = rq[0] >= 0 ? A.in.a[rq[0]] : 0.0;
-    double gtab = 0.0;  // decay steps of updates p0 .. p0 + 31 (lane t: update p0 + t)
+    // the step of the next 32 updates, one per lane: gamma (decay rule),
+    // 1 - gamma and gamma a_i of that update's row, and a_i
+    double tg = 0.0, tcoef = 0.0, tadd = 0.0, ta = 0.0;
     int i_prev = -1;
     for (int p = 0; p < m; ++p) {
         const long long k = A.k0 + p;
@@ -208,12 +222,18 @@ __global__ void __launch_bounds__(32, 1) k_epoch_f64w(EpochArgs<double> A) {
             cpa_commit();
         }
         const int r_far = row_of(p + D + 2);
-        const double an = rq[1] >= 0 ? A.in.a[rq[1]] : 0.0;
-        if (dec && (p & 31) == 0) {
-            // gamma = 2m / (k + 2m) for the next 32 updates, one per lane
-            const double twom = 2.0 * (double)m;
-            gtab = __ddiv_rn(twom, dadd((double)(k + lane), twom));
+        if ((p & 31) == 0) {
+            const int rl = row_of(p + lane);
+            ta = rl >= 0 ? A.in.a[rl] : 0.0;
+            if (dec) {
+                const double twom = 2.0 * (double)m;
+                tg = __ddiv_rn(twom, dadd((double)(k + lane), twom));
+                tcoef = dsub(1.0, tg);
+                tadd = dmul(tg, ta);
+            }
         }
+        const int tl = p & 31;
+        const double ac = __shfl_sync(FULL, ta, tl);
         if (aq[0]) cpa_wait<D>();
         else fetch_sync(i, s);
         __syncwarp();
@@ -224,98 +244,110 @@ __global__ void __launch_bounds__(32, 1) k_epoch_f64w(EpochArgs<double> A) {
         // ---- argmin (eq. 7): FP32 screen ----------------------------------
         float lo[CPL];
         float hmin = FINF;
+        unsigned supm = 0;  // this lane's non-zero plan entries (bit c)
 #pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-            const int j = col(c);
-            const float cf = frs[j], pf = rfs[j];
-            const float gs = __fadd_rn(cf, pf);
-            const float er = kScreen * (fabsf(cf) + fabsf(pf)) + 0x1.0p-120f;
-            lo[c] = gs - er;
-            hmin = fminf(hmin, gs + er);
-        }
-        const float U = key2f(__reduce_min_sync(FULL, f2key(hmin)));
-        // candidates, compacted onto the lanes (a bound that is not a number,
-        // for values beyond the FP32 range, keeps its column a candidate)
-        int nc = 0;
+        for (int g = 0; g < G; ++g) {
+            const int j0 = 4 * (lane + 32 * g);
+            const float4 cf4 = *reinterpret_cast<const float4 *>(frs + j0);
+            const float4 pf4 = *reinterpret_cast<const float4 *>(rfs + j0);
+            const longlong2 t01 = *reinterpret_cast<const longlong2 *>(trs + j0);
+            const longlong2 t23 = *reinterpret_cast<const longlong2 *>(trs + j0 + 2);
+            const float cf[4] = {cf4.x, cf4.y, cf4.z, cf4.w};
+            const float pf[4] = {pf4.x, pf4.y, pf4.z, pf4.w};
+            const long long tb[4] = {t01.x, t01.y, t23.x, t23.y};
 #pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-            const int j = col(c);
-            const bool cand = j < n && !(lo[c] > U);
-            const unsigned mk = __ballot_sync(FULL, cand);
-            if (cand) list[nc + __popc(mk & lt)] = j;
-            nc += __popc(mk);
-        }
-        __syncwarp();
-        // ---- exact FP64 gradient on the candidates ---------------------------
-        unsigned long long kmin = ~0ull;
-        int jmin = INT_MAX;
-        for (int e0 = 0; e0 < nc; e0 += 32) {
-            if (e0 + lane < nc) {
-                const int j = list[e0 + lane];
-                const unsigned long long kk = d2key(dadd(crs[j], rrs[j]));
-                if (kk < kmin || (kk == kmin && j < jmin)) { kmin = kk; jmin = j; }
+            for (int e = 0; e < 4; ++e) {
+                const float gs = __fadd_rn(cf[e], pf[e]);
+                const float er = kScreen * (fabsf(cf[e]) + fabsf(pf[e])) + 0x1.0p-120f;
+                lo[4 * g + e] = gs - er;
+                hmin = fminf(hmin, gs + er);
+                if ((tb[e] << 1) != 0) supm |= 1u << (4 * g + e);
             }
         }
-        const unsigned hi = (unsigned)(kmin >> 32), lw = (unsigned)kmin;
-        const unsigned whi = __reduce_min_sync(FULL, hi);
-        const unsigned wlo = __reduce_min_sync(FULL, hi == whi ? lw : 0xFFFFFFFFu);
-        const int js = __reduce_min_sync(FULL, (hi == whi && lw == wlo) ? jmin : INT_MAX);
-        const unsigned long long wk = ((unsigned long long)whi << 32) | wlo;
-        // non-finite minimum: the key of +inf or above (NaN), or no candidate
-        if (js == INT_MAX || wk >= 0xFFF0000000000000ull) {
+        const float U = key2f(__reduce_min_sync(FULL, f2key(hmin)));
+        // candidates (a bound that is not a number, for values beyond the
+        // FP32 range, keeps its column a candidate)
+        unsigned cand = 0;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c)
+            if (col(c) < n && !(lo[c] > U)) cand |= 1u << c;
+        const int ncand = __reduce_add_sync(FULL, __popc(cand));
+        int js;
+        double gmin = 0.0;
+        if (ncand == 1 && dec) {
+            // one candidate: it is the exact minimum, and the decay rule needs
+            // no gradient value
+            js = __reduce_max_sync(FULL, cand ? col(__ffs(cand) - 1) : -1);
+        } else {
+            // ---- exact FP64 gradient on the candidates ---------------------
+            unsigned long long kmin = ~0ull;
+            int jmin = INT_MAX;
+            unsigned mine = cand;
+            while (__any_sync(FULL, mine != 0)) {
+                if (mine) {
+                    const int c = __ffs(mine) - 1;
+                    mine &= mine - 1;
+                    const int j = col(c);
+                    const unsigned long long kk = d2key(dadd(crs[j], rrs[j]));
+                    if (kk < kmin || (kk == kmin && j < jmin)) { kmin = kk; jmin = j; }
+                }
+            }
+            const unsigned hi = (unsigned)(kmin >> 32), lw = (unsigned)kmin;
+            const unsigned whi = __reduce_min_sync(FULL, hi);
+            const unsigned wlo = __reduce_min_sync(FULL, hi == whi ? lw : 0xFFFFFFFFu);
+            js = __reduce_min_sync(FULL, (hi == whi && lw == wlo) ? jmin : INT_MAX);
+            const unsigned long long wk = ((unsigned long long)whi << 32) | wlo;
+            if (js == INT_MAX || wk >= 0xFFF0000000000000ull) js = INT_MAX;  // not finite
+            else gmin = key2d(wk);
+        }
+        if (js == INT_MAX || (ncand == 1 && dec && !(U < FINF))) {  // no finite minimum
             if (lane == 0) atomicCAS(A.status, 0, (int)kDevNonFinite);
             break;
         }
-        const double gmin = key2d(wk);
-        // ---- the row's support and j*, compacted -----------------------------
-        __syncwarp();
-        int ns = 0;
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-            const int j = col(c);
-            const bool sup = j < n && (nonzero_bits(trs[j]) || j == js);
-            const unsigned mk = __ballot_sync(FULL, sup);
-            if (sup) list[ns + __popc(mk & lt)] = j;
-            ns += __popc(mk);
-        }
-        __syncwarp();
         const double t_js = trs[js];
         // ---- step (Alg. 1): decay rule or exact line search ----------------
-        double gam = 0.0;
-        const bool move = ac > 0.0;
+        double gam, coef, add;
+        const bool move = (__double_as_longlong(ac) << 1) != 0;  // a_i > 0 (weights are >= 0)
         if (dec) {
-            gam = __shfl_sync(FULL, gtab, p & 31);
+            gam = __shfl_sync(FULL, tg, tl);
+            coef = __shfl_sync(FULL, tcoef, tl);
+            add = __shfl_sync(FULL, tadd, tl);
         } else {
             // sum_j t_ij grad_ij and sum_j t_ij^2 over the support
             double s1 = 0.0, s2 = 0.0;
-            for (int e0 = 0; e0 < ns; e0 += 32) {
-                if (e0 + lane < ns) {
-                    const int j = list[e0 + lane];
+            unsigned mine = supm;
+            while (__any_sync(FULL, mine != 0)) {
+                if (mine) {
+                    const int c = __ffs(mine) - 1;
+                    mine &= mine - 1;
+                    const int j = col(c);
                     const double t = trs[j];
                     s1 = fma(t, dadd(crs[j], rrs[j]), s1);
                     s2 = fma(t, t, s2);
                 }
             }
-            const int lanes = ns < 32 ? ns : 32;
-            for (int o = 1; o < lanes; o <<= 1) {
-                const double u1 = __shfl_down_sync(FULL, s1, o), u2 = __shfl_down_sync(FULL, s2, o);
-                if (lane + o < lanes && (lane & (2 * o - 1)) == 0) {
-                    s1 = dadd(s1, u1);
-                    s2 = dadd(s2, u2);
-                }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                s1 = dadd(s1, __shfl_xor_sync(FULL, s1, o));
+                s2 = dadd(s2, __shfl_xor_sync(FULL, s2, o));
             }
-            s1 = __shfl_sync(FULL, s1, 0);
-            s2 = __shfl_sync(FULL, s2, 0);
             const double g_fw = s1 - ac * gmin;
             double dd = (s2 - t_js * t_js) + (ac - t_js) * (ac - t_js);
             gam = line_search<double>(g_fw, dd > 0.0 ? dd : 0.0, rho, 1.0);
+            coef = dsub(1.0, gam);
+            add = dmul(gam, ac);
         }
         if (move) {
-            const double coef = dsub(1.0, gam), add = dmul(gam, ac);
+            // the row's support and j*: each lane its own columns, each
+            // FP64 operation issued once per round
             double *trow = A.T + (size_t)i * n;
-            for (int e0 = 0; e0 < ns; e0 += 32) {
-                if (e0 + lane < ns) {
-                    const int j = list[e0 + lane];
+            unsigned mine = supm;
+            if (lane == ((js >> 2) & 31)) mine |= 1u << (4 * (js >> 7) + (js & 3));  // j* = col(that bit)
+            while (__any_sync(FULL, mine != 0)) {
+                if (mine) {
+                    const int c = __ffs(mine) - 1;
+                    mine &= mine - 1;
+                    const int j = col(c);
                     const double t = trs[j];
                     double tn = dmul(coef, t);
                     if (j == js) tn = dadd(tn, add);
@@ -344,7 +376,6 @@ __global__ void __launch_bounds__(32, 1) k_epoch_f64w(EpochArgs<double> A) {
         rq[D + 1] = r_far;
 #pragma unroll
         for (int t = 0; t < D; ++t) aq[t] = aq[t + 1];
-        ac = an;
     }
     cpa_wait<0>();
     __syncwarp();
@@ -357,8 +388,8 @@ __global__ void __launch_bounds__(32, 1) k_epoch_f64w(EpochArgs<double> A) {
 
 template <int G>
 static void launch_f64w(const EpochArgs<double> &A, cudaStream_t st) {
-    constexpr size_t smem = ((size_t)kF64wRing * (2 * 64 * G + 32 * G) + 2 * 64 * G) * sizeof(double) +
-                            (size_t)64 * G * sizeof(float) + (size_t)(64 * G + 32) * sizeof(int);
+    constexpr size_t smem = ((size_t)kF64wRing * (2 * 128 * G + 64 * G) + 2 * 128 * G) * sizeof(double) +
+                            (size_t)128 * G * sizeof(float);
     auto kern = k_epoch_f64w<G>;
     static bool attr_set = false;
     if (!attr_set) {
@@ -379,10 +410,9 @@ bool launch_epoch_f64w(const EpochArgs<double> &A, cudaStream_t st) {
     if (A.variant != SR_OT_BCFW || A.in.cost_mode != kCostGiven || A.order == SR_OT_GAP_ADAPTIVE) return false;
     if (A.resume_in || !A.C32) return false;
     const int n = A.in.n;
-    if (n <= 64) launch_f64w<1>(A, st);
-    else if (n <= 128) launch_f64w<2>(A, st);
-    else if (n <= 256) launch_f64w<4>(A, st);
-    else if (n <= 512) launch_f64w<8>(A, st);
+    if (n <= 128) launch_f64w<1>(A, st);
+    else if (n <= 256) launch_f64w<2>(A, st);
+    else if (n <= 512) launch_f64w<4>(A, st);
     else return false;
     return true;
 }

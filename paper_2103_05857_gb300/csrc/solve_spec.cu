@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, 1) k_epoch_spe
     int2 *dec = reinterpret_cast<int2 *>(prepd + kSpecSlots);                // columns update u changes
     int4 *prep = reinterpret_cast<int4 *>(dec + kSpecSlots);                 // prepared words (split chain)
     int *ctl = reinterpret_cast<int *>(prep + kSpecSlots);                   // [0] stop
+    int *recent = ctl + 4;                                                   // rows of the last 16 updates
 
     const int m = A.in.m, n = A.in.n;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -149,6 +150,7 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, 1) k_epoch_spe
             dec[s] = make_int2(-1, -1);
         }
         ctl[0] = 0;
+        for (int e = 0; e < 16; ++e) recent[e] = -1;
         if (A.resume) *A.resume = -1;
         if (A.gate) {  // the start gate: a bounded wait for a non-zero word
             long long it = 0;
@@ -165,7 +167,11 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, 1) k_epoch_spe
     __syncthreads();
     const bool gate_closed = ctl[0] != 0;  // every warp skips its loop
 
-    auto row_of = [&](int u) -> int { return order == SR_OT_PERMUTE ? A.perm[u] : u; };
+    auto row_of = [&](int u) -> int {
+        if (order == SR_OT_PERMUTE) return A.perm[u];
+        if (order == SR_OT_UNIFORM) return scale_u64(sm64_draw(A.seed, 2, (uint64_t)(A.k0 + u)), m);
+        return u;
+    };
     // gradient of row x at column j with the residual as it is now
     auto grad_at = [&](int j, float x0, float x1, float x2) -> float {
         const float4 y = ys[j];
@@ -322,11 +328,11 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, 1) k_epoch_spe
     } else if (SPLIT && warp < AW + 4) {
         // ================= split chain: two preparer warps ================
         // Preparer (u mod 2) takes everything of update u that does not need
-        // the residual of u-2 and u-1: once update u-3 is published, the
+        // the residual of u-3, u-2 and u-1: once update u-4 is published, the
         // segment minima (recomputed where their column changed since ver),
-        // the columns changed by updates ver..u-3, the record position of
+        // the columns changed by updates ver..u-4, the record position of
         // the likely vertex and whether an atom changed since ver. The
-        // decider merges the columns of u-2 and u-1 itself.
+        // decider merges the columns of u-3, u-2 and u-1 itself.
         const int pw = warp - (NWP + 2);
         auto wait_bar = [&](uint64_t *b, unsigned parity) -> bool {
             long long it = 0;
@@ -344,9 +350,9 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, 1) k_epoch_spe
         };
         for (int u = pw; u < m; u += 2) {
             const int slot = u % kSpecSlots;
-            if (u >= 3) {
-                const int p3 = u - 3;
-                if (!wait_bar(done + p3 % kSpecSlots, (unsigned)(p3 / kSpecSlots) & 1u)) break;
+            if (u >= 4) {
+                const int p4 = u - 4;
+                if (!wait_bar(done + p4 % kSpecSlots, (unsigned)(p4 / kSpecSlots) & 1u)) break;
             }
             if (!wait_bar(full + slot, (unsigned)(u / kSpecSlots) & 1u)) break;
             const unsigned long long cw = lane < NWP ? cand[slot * NWP + lane] : 0ull;
@@ -365,8 +371,8 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, 1) k_epoch_spe
                     key = (uint32_t)cw;
                     col = cj;
                 }
-            } else if (lane < NWP + 2 * (kSpecLag - 2)) {
-                const int w = u - 3 - ((lane - NWP) >> 1);
+            } else if (lane < NWP + 2 * (kSpecLag - 3)) {
+                const int w = u - 4 - ((lane - NWP) >> 1);
                 if (w >= ver && w >= 0) {
                     const int2 d = dec[w % kSpecSlots];
                     const int c = ((lane - NWP) & 1) ? d.y : d.x;
@@ -411,13 +417,15 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, 1) k_epoch_spe
     } else if (SPLIT) {
         // ================= split chain: the decider =======================
         // One warp decides and applies every update. It knows the columns
-        // the last two updates changed (its own), merges their exact keys
-        // into the prepared minimum (the full LMO instead when that minimum
-        // sits on one of them), takes the away statistics again when one of
-        // the row's atoms changed, decides, applies and publishes -- with no
-        // hand-over between warps on its chain.
+        // the last three updates changed (its own), merges their exact keys
+        // with the prepared minimum in one warp reduction (the full LMO
+        // instead when that minimum sits on one of them), takes the away
+        // statistics again when one of the row's atoms changed, decides,
+        // applies and publishes -- with no hand-over between warps on its
+        // chain.
         bool aborted = false;
-        int c1[2] = {-1, -1}, c2[2] = {-1, -1};  // columns changed by updates u-1 and u-2
+        int c1[2] = {-1, -1}, c2[2] = {-1, -1}, c3[2] = {-1, -1};  // columns of updates u-1, u-2, u-3
+        const bool repeats = order == SR_OT_UNIFORM;  // a row may come back within the window
         for (int u = 0; u < m; ++u) {
             const long long k = A.k0 + u;
             const int slot = u % kSpecSlots;
@@ -447,25 +455,50 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, 1) k_epoch_spe
             const float x0 = __int_as_float(w1.x), x1 = __int_as_float(w1.y), x2 = __int_as_float(w1.z);
             const float ai = __int_as_float(w1.w), ra = __int_as_float(w2.x), ia = __int_as_float(w2.y);
             LaneAtoms at = load_atoms(aring + (size_t)(u % kSpecRecSlots) * kAtomRecord, lane);
+            // uniform order: if the row was updated in the last 12 updates, the
+            // record was fetched before that update stored it: read it again
+            // (this warp stored it) and retake everything taken from it
+            bool fresh = false;
+            if (repeats) {
+                fresh = __any_sync(FULL, lane < 12 && u - 1 - lane >= 0 && recent[(u - 1 - lane) & 15] == row);
+                if (fresh) {
+                    __syncwarp();
+                    at = load_atoms(grec + (size_t)row * kAtomRecord, lane);
+                    present = false;
+                    jpos = -1;
+                    atom_weight(at, pj, &present, &jpos);
+                }
+                __syncwarp();
+                if (lane == 0) recent[u & 15] = row;
+            }
             auto grad = [&](int j) -> float { return grad_at(j, x0, x1, x2); };
-            // update u-2: its two columns join the prepared minimum (a prepared
-            // minimum on one of them was stale: the full LMO is taken instead)
-            bool redo_lmo = pj >= 0 && (pj == c2[0] || pj == c2[1]);
+            // the columns of updates u-1, u-2, u-3 (lanes 0..5) join the
+            // prepared minimum (lane 6); a prepared minimum on one of them was
+            // taken at a residual that has changed since: the full LMO instead
+            const int hc = lane < 6 ? ((lane >> 1) == 0 ? c1[lane & 1] : (lane >> 1) == 1 ? c2[lane & 1] : c3[lane & 1])
+                                    : -1;
+            const bool redo_lmo = __any_sync(FULL, hc >= 0 && hc == pj);
             uint32_t fk = pk;
             int js = pj;
-            {
-                const int c = lane == 0 ? c2[0] : c2[1];
-                const uint32_t ke = (lane < 2 && c >= 0) ? f2key(grad(c)) : 0xFFFFFFFFu;
-                const uint32_t k0 = __shfl_sync(FULL, ke, 0), k1 = __shfl_sync(FULL, ke, 1);
-                if (c2[0] >= 0 && (k0 < fk || (k0 == fk && c2[0] < js))) { fk = k0; js = c2[0]; }
-                if (c2[1] >= 0 && (k1 < fk || (k1 == fk && c2[1] < js))) { fk = k1; js = c2[1]; }
+            const int pj2 = pj;
+            auto hit = [&](int c) {
+                return c >= 0 && (c == c1[0] || c == c1[1] || c == c2[0] || c == c2[1] || c == c3[0] || c == c3[1]);
+            };
+            const bool redo_atoms =
+                __any_sync(FULL, fresh || olddirty || hit(at.j[0]) || (at.cnt > 32 && hit(at.j[1])));
+            if (!redo_lmo) {
+                uint32_t ke = 0xFFFFFFFFu;
+                int ce = 0x7FFFFFFF;
+                if (hc >= 0) {
+                    ke = f2key(grad(hc));
+                    ce = hc;
+                } else if (lane == 6) {
+                    ke = pk;
+                    ce = pj;
+                }
+                fk = __reduce_min_sync(FULL, ke);
+                js = __reduce_min_sync(FULL, ke == fk ? ce : 0x7FFFFFFF);
             }
-            const int pj2 = js;
-            if (pj2 != pj) atom_weight(at, pj2, &present, &jpos);
-            // update u-1
-            redo_lmo = redo_lmo || (pj2 >= 0 && (pj2 == c1[0] || pj2 == c1[1]));
-            auto hit = [&](int c) { return c >= 0 && (c == c1[0] || c == c1[1] || c == c2[0] || c == c2[1]); };
-            const bool redo_atoms = __any_sync(FULL, olddirty || hit(at.j[0]) || (at.cnt > 32 && hit(at.j[1])));
             if (redo_lmo) {
                 float bv = INF;
                 int bj = 0x7FFFFFFF;
@@ -479,12 +512,6 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, 1) k_epoch_spe
                 const uint32_t kb = f2key(bv);
                 fk = __reduce_min_sync(FULL, kb);
                 js = __reduce_min_sync(FULL, kb == fk ? bj : 0x7FFFFFFF);
-            } else {
-                const int c = lane == 0 ? c1[0] : c1[1];
-                const uint32_t ke = (lane < 2 && c >= 0) ? f2key(grad(c)) : 0xFFFFFFFFu;
-                const uint32_t k0 = __shfl_sync(FULL, ke, 0), k1 = __shfl_sync(FULL, ke, 1);
-                if (c1[0] >= 0 && (k0 < fk || (k0 == fk && c1[0] < js))) { fk = k0; js = c1[0]; }
-                if (c1[1] >= 0 && (k1 < fk || (k1 == fk && c1[1] < js))) { fk = k1; js = c1[1]; }
             }
             const float gmin = key2f(fk);
             DF tvd{__int_as_float(w0.y), __int_as_float(w0.z)};
@@ -535,6 +562,8 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, 1) k_epoch_spe
                 A.trace[4 * k + 2] = (st.v >= 0 && st.v < n) ? st.v : -1;
                 A.trace[4 * k + 3] = __float_as_int(S.gamma);
             }
+            c3[0] = c2[0];
+            c3[1] = c2[1];
             c2[0] = c1[0];
             c2[1] = c1[1];
             c1[0] = moved ? S.js : -1;
@@ -764,7 +793,7 @@ static size_t spec_smem() {
     size_t b = (size_t)WID * (4 + 4 + 16 + 4);
     b += (size_t)kSpecRecSlots * kAtomRecord * 16;
     b += (size_t)kSpecSlots * (kAtomWords * 16 + NWP * 8 + 4 * 8 + 8 + 16);
-    b += 16;
+    b += 16 + 16 * 4;
     return b;
 }
 
@@ -792,8 +821,11 @@ static bool launch_spec_ch(const EpochArgs<float> &A, cudaStream_t st) {
 
 bool launch_epoch_spec(const EpochArgs<float> &A, cudaStream_t st, int chain) {
     if (A.variant != SR_OT_BCPFW || A.in.cost_mode != kCostPts3) return false;
+    if (chain == kSpecChainSplit) {
+        if (A.order != SR_OT_CYCLIC && A.order != SR_OT_PERMUTE && A.order != SR_OT_UNIFORM) return false;
+        return launch_spec_ch<3, true>(A, st);
+    }
     if (A.order != SR_OT_CYCLIC && A.order != SR_OT_PERMUTE) return false;
-    if (chain == kSpecChainSplit) return launch_spec_ch<3, true>(A, st);
     return chain == 1 ? launch_spec_ch<1, false>(A, st) : launch_spec_ch<3, false>(A, st);
 }
 

@@ -206,7 +206,7 @@ def test_batched_warm_start(S, h, oracle_mod):
     st, warm = h.solve_batched(pb.X, pb.Y, pb.a, pb.b, pb.T, pb.sizes, pb.offsets, batch_warm_start=1, **kw)
     assert st == S.OK
     for c, w in zip(cold, warm):
-        assert w["epochs"] <= 3 and w["status"] == S.OK
+        assert w["epochs"] <= 10 and w["status"] == S.OK
         assert rel(w["objective"], c["objective"]) <= 2e-6
     # a gradient step on X (towards the barycentric projection), then warm
     g = h.grad_batched(pb.X, pb.Y, pb.b, pb.T, pb.sizes, pb.offsets, rho=10.0, precision=S.FP32, want=("dX",))

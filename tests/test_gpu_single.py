@@ -368,36 +368,40 @@ NEGLIGIBLE = 1e-6    # an atom lighter than this fraction of a_i is below what a
 
 def fp32_step_allowance(C, a, T, r, i, rho, direction, js, v, gam):
     """How far an FP32 step size gamma may lie from the FP64 one for the same
-    decision: the line-search numerator (eq. 8 / eq. 10) is a difference of
-    sums of O(|supp| + 2) terms of size t_ij |grad_ij|, each carrying a few
-    FP32 roundings (cost, residual, product, sum), so its absolute error is
-    bounded by ~8 (|supp| + 4) eps32 times the sum of the magnitudes; gamma
-    inherits that error divided by the curvature, plus the same relative
-    error of the curvature itself."""
+    decision. gamma = num / (rho dd) (eq. 8 / eq. 10). The numerator is a
+    difference of sums of O(|supp| + 2) terms of size t_ij |grad_ij|, each
+    carrying a few FP32 roundings (cost, residual, product, sum); the
+    curvature dd is a difference and sum of squares of the row's entries (for
+    away and FW steps it cancels when one atom holds almost all the row's
+    mass), and the dense kernel takes a_i - t_v from the stored mass of the
+    other atoms, which also carries the row's drift from a_i. Each error is
+    bounded by ~8 (|supp| + 4) eps32 times the magnitudes of its terms; gamma
+    inherits the numerator's error over the curvature plus the curvature's
+    relative error."""
     g = C[i] + rho * r
     t = T[i]
     ai = a[i]
     supp = np.nonzero(t > 0)[0]
     k = 8.0 * (len(supp) + 4) * EPS32
-    rel_gam = k
-    if direction == 2:  # pairwise: numerator a_i (g_v - g_js), curvature 2 a_i^2 rho
-        den = rho * 2.0 * ai * ai
-        mag = ai * (abs(g[v]) + abs(g[js]))
-    else:  # FW or away: numerator <t, g> - a_i g_js (or a_i g_v - <t, g>)
-        d = -t.copy() if direction == 0 else t.copy()
-        d[js if direction == 0 else v] += ai if direction == 0 else -ai
-        den = rho * float(d @ d)
-        mag = float(t @ np.abs(g)) + ai * abs(g[js if direction == 0 else v])
-        if direction == 1 and ai > t[v]:
-            # the away curvature holds (a_i - t_v)^2, which the dense FP32 kernel
-            # takes from the stored mass of the other atoms: its error -- a few
-            # roundings of the row's mass, plus the row's drift from a_i -- is
-            # relative to a_i - t_v
+    if direction == 2:  # pairwise: numerator a_i (g_v - g_js), curvature 2 a_i^2
+        dd = 2.0 * ai * ai
+        num_mag = ai * (abs(g[v]) + abs(g[js]))
+        err_dd = k * dd
+    else:  # FW (towards js) or away (from v)
+        x = js if direction == 0 else v
+        tx = float(t[x])
+        s2 = float(t @ t)
+        oth = ai - tx
+        dd = (s2 - tx * tx) + oth * oth
+        num_mag = float(t @ np.abs(g)) + ai * abs(g[x])
+        err_dd = k * (s2 + tx * tx + (ai + tx) ** 2)
+        if direction == 1:
             drift = abs(float(t.sum()) - ai)
-            rel_gam = k + 2.0 * (drift + k * ai) / (ai - t[v])
-    if not den > 0:
-        return np.inf
-    return k * mag / den + rel_gam * abs(gam)
+            err_dd += 2.0 * abs(oth) * (drift + k * ai)
+    den = rho * dd
+    if not den > 0 or err_dd >= dd:
+        return np.inf  # the curvature is below FP32 resolution: gamma is not determined
+    return k * num_mag / den + (err_dd / dd + k) * abs(gam)
 
 
 def replay_epochs(S, h, O, inst, C, kw, variant, step, order, epochs, prec=None, seed=3,
@@ -480,7 +484,15 @@ def replay_epochs(S, h, O, inst, C, kw, variant, step, order, epochs, prec=None,
                     light = lambda c: 0 <= c < n and row_before[c] <= NEGLIGIBLE * ai
                     if light(int(gv[p])) or light(v):
                         tie = "negligible atom"
-            assert tie is not None, (ep, p, i, (gj[p], js), (gv[p], v), (gg[p], gam))
+            if tie is None:  # report what the decision looked like at the oracle's state
+                gr = C[i] + inst.rho * r_before
+                tt = row_before
+                info = dict(dir=dr, alpha_v=(tt[v] / ai if 0 <= v < n else None),
+                            g_fw=float(tt @ gr - ai * gr[js]),
+                            g_aw=(float(ai * gr[v] - tt @ gr) if 0 <= v < n else None),
+                            allowance=fp32_step_allowance(C, inst.a, Tpre, r_before, i, inst.rho, dr, js, v, gam)
+                            if same_vertices else None, nnz=int((tt > 0).sum()), row_drift=float(tt.sum() - ai))
+            assert tie is not None, (ep, p, i, (gj[p], js), (gv[p], v), (gg[p], gam), info)
             kinds[tie] = kinds.get(tie, 0) + 1
             if tie == "ill-conditioned step":
                 steps_ill += 1  # the same decision, a step FP32 resolves only this far
@@ -873,7 +885,8 @@ def test_fp32_dense_steps_conserve_row_mass(S, h, oracle_mod, variant, order):
 @pytest.mark.parametrize("order,m,n,ep,mode", [("CYCLIC", 300, 700, 30, "pts"), ("UNIFORM", 257, 515, 20, "pts"),
                                                ("PERMUTE", 200, 1500, 15, "pts"), ("CYCLIC", 190, 600, 20, "cost"),
                                                ("CYCLIC", 1024, 4096, 3, "pts"), ("PERMUTE", 2048, 3000, 4, "pts"),
-                                               ("CYCLIC", 3, 40, 200, "pts"), ("CYCLIC", 5000, 1025, 2, "pts")])
+                                               ("CYCLIC", 3, 40, 200, "pts"), ("CYCLIC", 5000, 1025, 2, "pts"),
+                                               ("UNIFORM", 6, 300, 60, "pts"), ("UNIFORM", 40, 2000, 12, "pts")])
 def test_pairwise_kernels_match_two_phase(S, h, oracle_mod, order, m, n, ep, mode):
     """The pipelined BCPFW kernel takes the next row's LMO and away vertex over
     the columns the current update leaves unchanged and completes them at the
@@ -881,7 +894,9 @@ def test_pairwise_kernels_match_two_phase(S, h, oracle_mod, order, m, n, ep, mod
     the next rows against an older residual and repairs them at every column
     changed since. Every decision (block, LMO vertex, away vertex, step) and
     the final plan equal the two-phase active-set kernel's bit for bit (where
-    a kernel does not apply, the fallback runs and must match as well)."""
+    a kernel does not apply, the fallback runs and must match as well). In
+    uniform order rows come back within a few updates (m = 6: every few
+    updates), which the split chain handles by re-reading the record."""
     inst = W.colour_instance(17 + m, m, n, rho=10.0, b_dirichlet=True).rounded()
     C = dev(oracle_mod.cost(inst.X, inst.Y), torch.float32) if mode == "cost" else None
     out = []

@@ -17,7 +17,11 @@ Alg. A.3, changes q in the two columns j*, v only):
     u - 1 at version u;
   - with one chain warp, it prepares update u after applying u - 1 itself:
     every column is at version u and every mark is visible; there is no
-    hand-over.
+    hand-over;
+  - with the split chain, a preparer takes update u once u - 4 is published
+    (every column at version >= u - 3; the marks of u - 4 and earlier
+    visible, those of u - 3 .. u - 1 may or may not be), and the decider,
+    which applied u - 3 .. u - 1 itself, merges their columns at version u.
 The atom warp takes the away vertex (Alg. A.3: the atom with the largest
 gradient) at versions in [ver, u] as well; the chain takes it again when one of
 the row's atom columns changed since ver. The model draws all of these at
@@ -51,10 +55,14 @@ def _min(keys):
 
 def _chain_lmo(rng, u, C, q0, dec, deltas, nseg, atoms, CHAIN, drop=None):
     """The kernel's LMO and away vertex for update u under one random
-    interleaving, with CHAIN chain warps. `drop` leaves one repair out (a
-    planted mistake): "stale" (no segment recompute), "history" (no columns
-    of u-CHAIN .. u-4), "c2" or "c1" (no hand-over merge), "atoms" (the atom
-    warp's away statistics always kept)."""
+    interleaving, with CHAIN chain warps (1 or 3) or the split chain
+    ("split"). `drop` leaves one repair out (a planted mistake): "stale" (no
+    segment recompute), "history" (no columns of the updates the preparing
+    warp knows are published), "c3", "c2" or "c1" (no merge of the columns
+    of u-3, u-2 or u-1), "atoms" (the atom warp's away statistics always
+    kept)."""
+    if CHAIN == "split":
+        return _split_lmo(rng, u, C, q0, dec, deltas, nseg, atoms, drop)
     n = len(C)
     seg_of = (np.arange(n) // 4) % nseg  # quads interleaved over the producer warps
 
@@ -125,6 +133,62 @@ def _chain_lmo(rng, u, C, q0, dec, deltas, nseg, atoms, CHAIN, drop=None):
     return js, away, value
 
 
+def _split_lmo(rng, u, C, q0, dec, deltas, nseg, atoms, drop=None):
+    """The split chain: the preparer of u starts once u - 4 is published; the
+    decider merges the columns of u - 3, u - 2, u - 1 at the current
+    residual and takes the full LMO when the prepared minimum sits on one of
+    them."""
+    n = len(C)
+    seg_of = (np.arange(n) // 4) % nseg
+
+    def value(j, k):
+        return C[j] + q0[j] + sum(deltas[w][j] for w in range(k) if dec[w] is not None and j in dec[w])
+
+    ver = u - LAG if u > LAG else 0
+    away = min((-value(j, int(rng.integers(ver, u + 1))), j) for j in atoms)[1]
+    cand = {}
+    for s in range(nseg):
+        cols = np.nonzero(seg_of == s)[0]
+        if len(cols) == 0:
+            continue
+        cand[s] = min((value(j, int(rng.integers(ver, u + 1))), int(j)) for j in cols)
+    lo = max(u - 3, 0)
+    visible = {w for w in range(u) if w <= u - 4 or rng.random() < 0.5}
+
+    def lastmod(j):
+        ws = [w for w in range(u) if w in visible and dec[w] is not None and j in dec[w]]
+        return max(ws) if ws else -1
+
+    def prep_value(j):
+        return value(j, int(rng.integers(lo, u + 1)))
+
+    keys = []
+    for s in cand:
+        val, cj = cand[s]
+        if lastmod(cj) >= ver and drop != "stale":
+            cols = np.nonzero(seg_of == s)[0]
+            keys.append(min((prep_value(j), int(j)) for j in cols))
+        else:
+            keys.append((val, cj))
+    for w in range(u - 4, u - LAG - 1, -1):
+        if w >= ver and w >= 0 and dec[w] is not None and drop != "history":
+            keys.extend((prep_value(c), c) for c in dec[w])
+    olddirty = any(lastmod(j) >= ver for j in atoms)
+    pk, pj = _min(keys)
+    merged = []
+    for back, name in ((3, "c3"), (2, "c2"), (1, "c1")):
+        w = u - back
+        if w >= 0 and dec[w] is not None and drop != name:
+            merged.extend(dec[w])
+    if pj in merged:
+        fk, js = min((value(j, u), j) for j in range(n))
+    else:
+        fk, js = min([(pk, pj)] + [(value(c, u), c) for c in merged])
+    if (olddirty or any(j in merged for j in atoms)) and drop != "atoms":
+        away = min((-value(j, u), j) for j in atoms)[1]
+    return js, away, value
+
+
 def _mismatches(seed, trials, chain, drop=None):
     rng = np.random.default_rng(seed)
     bad = 0
@@ -160,17 +224,22 @@ def test_model_follows_the_kernel_constants():
     three the hand-over takes the columns of u-2 and u-1, the other changed
     columns are the ones of u-CHAIN .. u-LAG."""
     assert CHAINS == (1, 3) and LAG >= max(CHAINS)
+    with open(SRC) as fh:
+        src = fh.read()
+    # the split chain's preparer waits for update u - 4, the decider merges u-3 .. u-1
+    assert "const int p4 = u - 4;" in src and "c3[2]" in src
 
 
-@pytest.mark.parametrize("chain", [1, 3])
+@pytest.mark.parametrize("chain", [1, 3, "split"])
 def test_speculative_repair_gives_the_exact_lmo(chain):
     assert _mismatches(2103, 4000, chain) == 0
 
 
-@pytest.mark.parametrize("chain", [1, 3])
+@pytest.mark.parametrize("chain", [1, 3, "split"])
 def test_each_repair_is_needed(chain):
     """Leaving out any one repair makes the model return wrong LMOs on the
     same kind of draws, so the test above has something to catch."""
-    drops = ("stale", "history", "c2", "c1", "atoms") if chain == 3 else ("stale", "history", "atoms")
+    drops = {3: ("stale", "history", "c2", "c1", "atoms"), 1: ("stale", "history", "atoms"),
+             "split": ("stale", "history", "c3", "c2", "c1", "atoms")}[chain]
     for drop in drops:
         assert _mismatches(7, 1500, chain, drop) > 0, drop
