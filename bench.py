@@ -94,7 +94,7 @@ def parse():
     ap.add_argument("--instances", type=int, default=None,
                     help="batched workloads: use only the first K instances (small profiling cases)")
     ap.add_argument("--no-variants", action="store_true",
-                    help="colour4096_fp32: skip the variant x rho grid")
+                    help="colour4096_fp32: skip the variant x rho grid; feature8192_d128: skip the plain-form runs")
     ap.add_argument("--no-protocol", action="store_true",
                     help="colour_batch64_2048: skip the 100-step gradient descent on X")
     return ap.parse_args()
@@ -231,7 +231,7 @@ def epoch_kernel_name(s, n):
     """The epoch kernel the library runs for these settings (its own dispatch:
     speculative for pairwise steps on d = 3 points with n <= 4096, pipelined up
     to n = 8192, else two-phase; FP64 BCFW up to n = 512 runs on one warp;
-    other FP64 and BCFW settings keep the dense-row kernel).""""
+    other FP64 and BCFW settings keep the dense-row kernel)."""
     if s["precision"] == "FP64" and s["variant"] == "BCFW" and n <= 512 and not s.get("ga"):
         return ("k_epoch_f64w (one warp, m block updates; dense rows, FP32 argmin screen with exact "
                 "FP64 decisions, cost in shared memory)")
@@ -392,6 +392,36 @@ VARIANT_GRID = [  # label, variant, order, extra options, epoch cap
     ("BCPFW-U-ELS", "BCPFW", "UNIFORM", {}, 6000),
 ]
 GRID_RHOS = (1.0, 10.0, 100.0)
+
+
+def plain_forms(h, S, inst, X, Y, a, b, stream, flush, mixed_s):
+    """feature8192_d128: the plain GPU form beside the mixed-precision one --
+    the FP32 cost built on the CUDA cores (no tensor cores, no BF16 rounding)
+    with plain BCFW (exact line search), to rel. gap 1e-6 or its epoch cap;
+    and, to separate the two effects, the same FP32 cost with pairwise steps.
+    Time to the tolerance (or to the cap) with CUDA events, outside the timed
+    region of the line."""
+    import torch
+    out = {"mixed_form_s": mixed_s}
+    for label, var, cap in (("plain_bcfw_fp32_cost", "BCFW", 300), ("bcpfw_fp32_cost", "BCPFW", 2000)):
+        T = torch.zeros((inst.m, inst.n), dtype=torch.float32, device=X.device)
+        opts = S.options(variant=VARIANTS[var], step=S.ELS, order=S.CYCLIC, precision=S.FP32, rho=inst.rho,
+                         tol_rel_gap=1e-6, max_epochs=cap, gap_every=1, refresh_every=1)
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = h.solve(a, b, T, X=X, Y=Y, opts=opts)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        out[label] = {"converged": r["status"] == S.OK, "seconds": sec, "epochs": r["epochs"],
+                      "rel_gap": r["rel_gap"], "epoch_cap": cap,
+                      "mixed_form_speedup": sec / mixed_s if mixed_s > 0 else None}
+        del T
+    out["note"] = ("seconds = time to rel. gap 1e-6 when converged, else to the epoch cap; the mixed form: BF16 "
+                   "tensor-core cost (FP32 accumulation, exact norms) + BCPFW-ELS, the timed step of this line")
+    return out
 
 
 def variant_grid(h, S, inst, X, Y, a, b, T, stream, flush, check):
@@ -609,6 +639,8 @@ def bench_single(args, s, ws, rank, local, cpu_leg):
         line["oracle_check"] = feature_checks(inst, T, out[-1])
     if args.workload == "colour4096_fp32" and ws == 1 and not args.no_variants:
         line["variants"] = variant_grid(h, S, inst, X, Y, a, b, T, stream, H.flush, check)
+    if args.workload == "feature8192_d128" and ws == 1 and not args.no_variants:
+        line["vs_plain_gpu"] = plain_forms(h, S, inst, X, Y, a, b, stream, H.flush, line["time_to_gap_s"])
     if co_n:
         co_avg = co_ms / co_n
         line["roofline_cost"] = hbm_roofline(4.0 * m * n + 4.0 * (m + n) * d + 2.0 * (m + n) * d, co_avg,
@@ -713,8 +745,10 @@ def bench_batch(args, s, ws, rank, local):
     longest = max(r["block_updates"] for r in out[-1])
     batch_ms = b_ms / max(b_n, 1)
     floor3 = h.chain_floor(3)
-    roof = alu_roofline(flops / max(len(out), 1), batch_ms, peaks, peak_src,
-                        "k_batched (persistent, one CTA per instance at a time)",
+    kname = ("k_spec_batch_init + k_epoch_spec in batch mode (one CTA per instance for the whole solve: "
+             "speculative epochs, certificate inside the CTA)" if s["variant"] == "BCPFW"
+             else "k_batched (persistent, one CTA per instance at a time)")
+    roof = alu_roofline(flops / max(len(out), 1), batch_ms, peaks, peak_src, kname,
                         {"launches": b_n, "instances": len(insts), "longest_chain_updates": longest,
                          "longest_chain_ns_per_update": 1e6 * batch_ms / longest,
                          "chain_floor_ns": floor3, "chain_frac": floor3 / (1e6 * batch_ms / longest)})

@@ -113,8 +113,11 @@ typedef struct {
     unsigned long long seed;  /* block-order random stream                         */
     int *trace;               /* optional DEVICE int32[4*trace_capacity]: per block
                                  update k, trace[4k..4k+3] = block i, LMO vertex
-                                 j*, away vertex v (-1 if none), step gamma as
-                                 IEEE-754 binary32 bits                           */
+                                 j*, v | dir << 29 (away vertex v in bits 0..28,
+                                 all ones if none; the step's direction dir in
+                                 bits 29..30: 0 toward j*, 1 away from v, 2
+                                 pairwise, 3 no step), step gamma as IEEE-754
+                                 binary32 bits                                    */
     long long trace_capacity;
     int dense_only;           /* 1: FP32 away/pairwise solves keep the dense row
                                  kernel instead of the active-set kernel          */

@@ -24,7 +24,7 @@ namespace {
 enum WsSlot {
     WS_Q = 0, WS_PARTIAL, WS_R64, WS_RQ32, WS_COLPART, WS_ROWPART, WS_CERT, WS_PERM, WS_PERMKEY,
     WS_PERMIDX, WS_GSTORE, WS_STATUS, WS_COST, WS_CHECK, WS_SCRATCH, WS_ATOMS, WS_B_INST,
-    WS_B_QUEUE, WS_B_HEAD, WS_B_RES, WS_B_ATOMS, WS_B_BAD, WS_ADJ_INST, WS_ADJ_CP, WS_ADJ_RP, WS_TR_PART, WS_TR_ZERO, WS_TR_STATS, WS_FW_JS, WS_FW_UPART, WS_BF16, WS_BF16_ERR, WS_MET, WS_COST32, WS_FLOOR, WS_COUNT
+    WS_B_QUEUE, WS_B_HEAD, WS_B_RES, WS_B_ATOMS, WS_B_BAD, WS_ADJ_INST, WS_ADJ_CP, WS_ADJ_RP, WS_TR_PART, WS_TR_ZERO, WS_TR_STATS, WS_FW_JS, WS_FW_UPART, WS_BF16, WS_BF16_ERR, WS_MET, WS_COST32, WS_FLOOR, WS_SB_STATE, WS_SB_Q, WS_SB_LIST, WS_COUNT
 };
 
 struct DevBuf {
@@ -811,6 +811,109 @@ sr_ot_status ensure_side_streams(sr_ot_handle h) {
     return SR_OT_OK;
 }
 
+// The batched speculative form (see solve_spec_batch.cu): instances with
+// n <= 4096 in width buckets; one set-up launch, then one launch per bucket
+// (each on its own side stream) in which every CTA solves one instance to
+// its stopping rule. Instances it does not take (n above the widths, or a
+// row that outgrew its record) are appended to `solo`.
+sr_ot_status solve_batched_spec(sr_ot_handle h, const sr_ot_options *o, int batch, const int *m, const int *n,
+                                const std::vector<BatchInst> &inst, const BatchInst *d_inst, int4 *d_atoms,
+                                const float *X, const float *Y, const float *a, const float *b, float *T,
+                                sr_ot_result *res, std::vector<int> &solo) {
+    sr_ot_status st;
+    std::vector<std::vector<int>> bq(kSpecBatchBuckets);
+    long long qlen = 1;
+    for (int k = 0; k < batch; ++k) {
+        const int bk = spec_batch_bucket(n[k]);
+        if (bk < 0) { solo.push_back(k); continue; }
+        bq[bk].push_back(k);
+        qlen = std::max(qlen, inst[k].off_b + n[k]);
+    }
+    // largest first within a bucket: the hardware starts CTAs in index order
+    auto by_size = [&](int x, int y) { return (long long)m[x] * n[x] > (long long)m[y] * n[y]; };
+    for (auto &v : bq) std::stable_sort(v.begin(), v.end(), by_size);
+    std::vector<int> hlist, lstart(kSpecBatchBuckets + 1, 0);
+    for (int bk = 0; bk < kSpecBatchBuckets; ++bk) {
+        lstart[bk] = (int)hlist.size();
+        hlist.insert(hlist.end(), bq[bk].begin(), bq[bk].end());
+    }
+    lstart[kSpecBatchBuckets] = (int)hlist.size();
+    if (hlist.empty()) return SR_OT_OK;
+    SpecInstState *d_state;
+    double *d_q;
+    int *d_list;
+    if ((st = ws_typed(h, WS_SB_STATE, (size_t)batch, &d_state))) return st;
+    if ((st = ws_typed(h, WS_SB_Q, (size_t)qlen, &d_q))) return st;
+    if ((st = ws_typed(h, WS_SB_LIST, (size_t)batch, &d_list))) return st;
+    CK(h, cudaMemcpyAsync(d_list, hlist.data(), sizeof(int) * hlist.size(), cudaMemcpyHostToDevice, h->stream));
+    SpecBatchArgs B{};
+    B.inst = d_inst;
+    B.list = d_list;
+    B.state = d_state;
+    B.q = d_q;
+    B.X = X;
+    B.Y = Y;
+    B.a = a;
+    B.b = b;
+    B.T = T;
+    B.atoms = d_atoms;
+    B.rho = o->rho;
+    B.tol = o->tol_rel_gap;
+    B.max_epochs = o->max_epochs;
+    B.gap_every = o->gap_every;
+    B.warm = o->batch_warm_start ? 1 : 0;
+    const bool uniform = o->order == SR_OT_UNIFORM;
+    {
+        ProfScope ps(h, SR_OT_PROF_BATCH);
+        launch_spec_batch_init(B, (int)hlist.size(), h->stream);
+        h->launches += 1;
+        CKL(h);
+        CK(h, cudaEventRecord(h->ev_fork, h->stream));
+        int used = 0;
+        // widest bucket first: its CTAs are dispatched first and its (larger)
+        // instances start at once
+        for (int bk = kSpecBatchBuckets - 1; bk >= 0; --bk) {
+            const int cnt = lstart[bk + 1] - lstart[bk];
+            if (cnt == 0) continue;
+            cudaStream_t s = h->side[used];
+            CK(h, cudaStreamWaitEvent(s, h->ev_fork, 0));
+            SpecBatchArgs Bb = B;
+            Bb.list = d_list + lstart[bk];
+            if (!launch_spec_batch_solve(bk, uniform, Bb, cnt, o->seed, o->spin_limit, s))
+                return fail(h, SR_OT_EUNSUPPORTED, "no speculative kernel for width bucket %d", bk);
+            h->launches += 1;
+            CKL(h);
+            CK(h, cudaEventRecord(h->ev_join[used], s));
+            CK(h, cudaStreamWaitEvent(h->stream, h->ev_join[used], 0));
+            ++used;
+        }
+    }
+    std::vector<SpecInstState> hs(batch);
+    CK(h, cudaMemcpyAsync(hs.data(), d_state, sizeof(SpecInstState) * batch, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    prof_collect(h);
+    for (int k = 0; k < batch; ++k) {
+        if (spec_batch_bucket(n[k]) < 0) continue;
+        const SpecInstState &r = hs[k];
+        if (r.active) return fail(h, SR_OT_ECUDA, "instance %d still running after its solve", k);
+        sr_ot_result &o2 = res[k];
+        o2.objective = r.f;
+        o2.gap = r.g;
+        o2.rel_gap = r.f != 0.0 ? r.g / r.f : 0.0;
+        o2.dual = r.f - r.g;
+        o2.row_err = r.feas;
+        o2.epochs = r.ep;
+        o2.block_updates = r.updates;
+        o2.reserved = 0;
+        o2.status = r.status == kInstOk ? SR_OT_OK
+                  : r.status == kInstNotConverged ? SR_OT_NOT_CONVERGED
+                  : r.status == kInstNonFinite ? SR_OT_ENUMERIC
+                  : r.status == kInstTimeout ? SR_OT_ETIMEOUT : SR_OT_OK;
+        if (r.status == kInstNeedsDense) solo.push_back(k);
+    }
+    return SR_OT_OK;
+}
+
 sr_ot_status solve_batched_impl(sr_ot_handle h, const sr_ot_options *o, int batch, const int *m,
                                 const int *n, int d, const long long *off_X, const long long *off_Y,
                                 const long long *off_a, const long long *off_b,
@@ -880,6 +983,42 @@ sr_ot_status solve_batched_impl(sr_ot_handle h, const sr_ot_options *o, int batc
             if (bad[k]) return fail(h, SR_OT_EINVAL, "instance %d: %d negative or non-finite entries in a, b, X or Y", k, bad[k]);
     }
     if ((st = ensure_side_streams(h))) return st;
+
+    sr_ot_status worst = SR_OT_OK;
+    auto account = [&](sr_ot_status s) {
+        if (s < 0 && (worst >= 0 || s < worst)) worst = s;
+        else if (s == SR_OT_NOT_CONVERGED && worst == SR_OT_OK) worst = s;
+    };
+    // dense or oversize instances one at a time: from T0, or (warm start)
+    // from the plan in T, which the batched kernels left feasible wherever
+    // they stopped
+    auto solve_solo = [&](const std::vector<int> &list, auto in_batch_width) {
+        for (int k : list) {
+            sr_ot_options o1 = *o;
+            o1.dense_only = in_batch_width(k) ? 1 : o->dense_only;
+            o1.trace = nullptr;
+            o1.trace_capacity = 0;
+            sr_ot_status s = solve_impl<float>(h, &o1, m[k], n[k], 3, nullptr, X + off_X[k], Y + off_Y[k],
+                                               a + off_a[k], b + off_b[k], T + off_T[k],
+                                               o->batch_warm_start ? 1 : 0, &res[k]);
+            if (s < 0) res[k].status = s;
+            account(s);
+        }
+    };
+    // pairwise steps in cyclic or uniform order: the batched speculative form
+    // (SR_OT_EPOCH_TWO_PHASE keeps the persistent two-phase kernel below)
+    if (o->variant == SR_OT_BCPFW && (o->order == SR_OT_CYCLIC || o->order == SR_OT_UNIFORM) &&
+        o->epoch_kernel != SR_OT_EPOCH_TWO_PHASE) {
+        std::vector<int> rest;
+        if ((st = solve_batched_spec(h, o, batch, m, n, inst, d_inst, d_atoms, X, Y, a, b, T, res, rest)))
+            return st;
+        std::vector<char> again(batch, 0);
+        for (int k : rest) again[k] = 1;
+        for (int k = 0; k < batch; ++k)
+            if (!again[k]) account((sr_ot_status)res[k].status);
+        solve_solo(rest, [&](int k) { return spec_batch_bucket(n[k]) >= 0; });
+        return worst;
+    }
 
     BatchArgs base;
     base.inst = d_inst;
@@ -1020,11 +1159,6 @@ sr_ot_status solve_batched_impl(sr_ot_handle h, const sr_ot_options *o, int batc
     CK(h, cudaStreamSynchronize(h->stream));
     prof_collect(h);
     // ---- fill results; dense or oversize instances one at a time ------------
-    sr_ot_status worst = SR_OT_OK;
-    auto account = [&](sr_ot_status s) {
-        if (s < 0 && (worst >= 0 || s < worst)) worst = s;
-        else if (s == SR_OT_NOT_CONVERGED && worst == SR_OT_OK) worst = s;
-    };
     for (int k = 0; k < batch; ++k) {
         if (bucket_of(n[k]) < 0) continue;
         const BatchResult &r = hres[k];
@@ -1043,18 +1177,7 @@ sr_ot_status solve_batched_impl(sr_ot_handle h, const sr_ot_options *o, int batc
         if (r.status == kInstNeedsDense) solo.push_back(k);
         else account((sr_ot_status)o2.status);
     }
-    for (int k : solo) {
-        sr_ot_options o1 = *o;
-        o1.dense_only = bucket_of(n[k]) >= 0 ? 1 : o->dense_only;
-        o1.trace = nullptr;
-        o1.trace_capacity = 0;
-        // from T0, or (warm start) from the plan in T, which the batched
-        // kernel left feasible wherever it stopped
-        sr_ot_status s = solve_impl<float>(h, &o1, m[k], n[k], 3, nullptr, X + off_X[k], Y + off_Y[k],
-                                           a + off_a[k], b + off_b[k], T + off_T[k], base.warm, &res[k]);
-        if (s < 0) res[k].status = s;
-        account(s);
-    }
+    solve_solo(solo, [&](int k) { return bucket_of(n[k]) >= 0; });
     return worst;
 }
 

@@ -78,6 +78,15 @@ struct Kahan32 {
     __device__ inline double value() const { return (double)s - (double)c; }
 };
 
+// Trace word 2 of a block update: the away vertex v in bits 0..28 (all ones
+// when there is none) and the step's direction in bits 29..30 (0 toward the
+// LMO vertex, 1 away from v, 2 pairwise, 3 no step).
+__device__ inline int trace_vdir(int v, int kind) {
+    const unsigned vv = v >= 0 ? ((unsigned)v & 0x1FFFFFFFu) : 0x1FFFFFFFu;
+    const unsigned k = (kind >= 0 && kind <= 2) ? (unsigned)kind : 3u;
+    return (int)(vv | (k << 29));
+}
+
 template <typename T>
 __device__ inline T warp_sum(T v) {
 #pragma unroll

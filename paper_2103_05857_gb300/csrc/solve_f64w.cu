@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(32, 1) k_epoch_f64w(EpochArgs<double> A) {
         if (lane == 0 && A.trace && k < A.trace_cap) {
             A.trace[4 * k] = i;
             A.trace[4 * k + 1] = js;
-            A.trace[4 * k + 2] = -1;
+            A.trace[4 * k + 2] = trace_vdir(-1, 0);  // BCFW: toward the LMO vertex
             A.trace[4 * k + 3] = __float_as_int(move ? (float)gam : 0.f);
         }
         // ---- advance the pipeline -------------------------------------------

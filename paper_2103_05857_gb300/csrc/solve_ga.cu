@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(NT, 1) k_epoch_ga(EpochArgs<Real> A) {
             if (tid == 0 && A.trace && k < A.trace_cap) {
                 A.trace[4 * k] = i;
                 A.trace[4 * k + 1] = R.jmin;
-                A.trace[4 * k + 2] = (AWAY && R.jmax >= 0 && R.jmax < n) ? R.jmax : -1;
+                A.trace[4 * k + 2] = trace_vdir((AWAY && R.jmax >= 0 && R.jmax < n) ? R.jmax : -1, S.kind);
                 A.trace[4 * k + 3] = __float_as_int(S.gamma);
             }
         } else {
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(NT, 1) k_epoch_ga(EpochArgs<Real> A) {
             if (tid == 0 && A.trace && k < A.trace_cap) {
                 A.trace[4 * k] = i;
                 A.trace[4 * k + 1] = R.jmin;
-                A.trace[4 * k + 2] = (AWAY && R.jmax >= 0 && R.jmax < n) ? R.jmax : -1;
+                A.trace[4 * k + 2] = trace_vdir((AWAY && R.jmax >= 0 && R.jmax < n) ? R.jmax : -1, S.kind);
                 A.trace[4 * k + 3] = __float_as_int((float)S.gamma);
             }
         }

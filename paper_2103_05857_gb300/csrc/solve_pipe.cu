@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(NTC + 2 * kWarp, 1) k_epoch_pipe(EpochArgs<flo
             if (lane == 0 && A.trace && k < A.trace_cap) {
                 A.trace[4 * k] = row;
                 A.trace[4 * k + 1] = js;
-                A.trace[4 * k + 2] = (st.v >= 0 && st.v < n) ? st.v : -1;
+                A.trace[4 * k + 2] = trace_vdir((st.v >= 0 && st.v < n) ? st.v : -1, S.kind);
                 A.trace[4 * k + 3] = __float_as_int(S.gamma);
             }
             if (!ok) {

@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(NT, 1) k_epoch(EpochArgs<Real> A) {
             if (tid == 0 && A.trace && k < A.trace_cap) {
                 A.trace[4 * k] = i;
                 A.trace[4 * k + 1] = R.jmin;
-                A.trace[4 * k + 2] = (AWAY && R.jmax >= 0 && R.jmax < n) ? R.jmax : -1;
+                A.trace[4 * k + 2] = trace_vdir((AWAY && R.jmax >= 0 && R.jmax < n) ? R.jmax : -1, S.kind);
                 A.trace[4 * k + 3] = __float_as_int((float)S.gamma);
             }
         } else {
@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(NT, 1) k_epoch(EpochArgs<Real> A) {
             if (tid == 0 && A.trace && k < A.trace_cap) {
                 A.trace[4 * k] = i;
                 A.trace[4 * k + 1] = R.jmin;
-                A.trace[4 * k + 2] = (AWAY && R.jmax >= 0 && R.jmax < n) ? R.jmax : -1;
+                A.trace[4 * k + 2] = trace_vdir((AWAY && R.jmax >= 0 && R.jmax < n) ? R.jmax : -1, S.kind);
                 A.trace[4 * k + 3] = __float_as_int((float)S.gamma);
             }
         }

@@ -40,6 +40,8 @@
 #include <limits>
 
 #include "atoms.cuh"
+#include "batched.h"
+#include "cert_records.cuh"
 #include "common.cuh"
 #include "cpasync.cuh"
 #include "internal.h"
@@ -62,12 +64,16 @@ constexpr int kSpecRecHead = 8;    // record entries fetched ahead: the count an
 // without waiting on another warp).
 constexpr long long kSpecSpin = 1ll << 26;  // default polls before a wait gives up
 static_assert(kSpecSlots > kSpecLag && kSpecRecSlots > kSpecLag + kSpecRecAhead, "slot rings too small");
+static_assert(kSpecRecSlots * kAtomRecord * 4 >= kRecRowChunk, "the certificate's row chunk lives in the record ring");
 
 __device__ inline unsigned saddr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ inline int vload(const int *p) { return *reinterpret_cast<const volatile int *>(p); }
 __device__ inline void vstore(int *p, int v) { *reinterpret_cast<volatile int *>(p) = v; }
 __device__ inline void mbar_init(uint64_t *b, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(saddr(b)), "r"(count) : "memory");
+}
+__device__ inline void mbar_inval(uint64_t *b) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(saddr(b)) : "memory");
 }
 __device__ inline void mbar_arrive(uint64_t *b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(saddr(b)) : "memory");
@@ -89,8 +95,13 @@ constexpr int kAtomWords = 3;  // atom warp output per update: int4 words
 
 }  // namespace
 
-template <int NWP, int G, int CH, bool SPLIT>
-__global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, 1) k_epoch_spec(EpochArgs<float> A) {
+// BATCH: CTA c solves instance Bt.list[c] of a batch (its sizes and arrays
+// from the batch descriptors, the other settings from A0): epoch after epoch,
+// the barriers re-initialised between them, the certificate of Thm 2 taken
+// inside the CTA when it is due, until the instance stops.
+template <int NWP, int G, int CH, bool SPLIT, bool BATCH>
+__global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <= 4) ? 2 : 1)
+    k_epoch_spec(EpochArgs<float> A0, SpecBatchArgs Bt) {
     constexpr int NTC = NWP * kWarp;  // producer threads
     constexpr int AW = NWP;  // atom warps NWP, NWP + 1; chain warps NWP + 2 ...
     constexpr int NT = NTC + (2 + CH) * kWarp;
@@ -116,7 +127,28 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, 1) k_epoch_spe
     int4 *prep = reinterpret_cast<int4 *>(dec + kSpecSlots);                 // prepared words (split chain)
     int *ctl = reinterpret_cast<int *>(prep + kSpecSlots);                   // [0] stop
     int *recent = ctl + 4;                                                   // rows of the last 16 updates
+    double *cred = reinterpret_cast<double *>(recent + 16);                  // certificate partials (BATCH)
 
+    EpochArgs<float> A = A0;
+    int inst = -1;
+    const float *bvec = nullptr;
+    if constexpr (BATCH) {
+        inst = Bt.list[blockIdx.x];
+        if (!Bt.state[inst].active) return;  // uniform over the CTA
+        const BatchInst I = Bt.inst[inst];
+        A.in.m = I.m;
+        A.in.n = I.n;
+        A.in.X = Bt.X + I.off_X;
+        A.in.Y = Bt.Y + I.off_Y;
+        A.in.a = Bt.a + I.off_a;
+        A.T = Bt.T + I.off_T;
+        A.q = Bt.q + I.off_b;
+        A.atoms = Bt.atoms + I.off_atoms;
+        A.status = &Bt.state[inst].devstat;
+        A.resume = &Bt.state[inst].resume;
+        A.k0 = Bt.state[inst].ep * (long long)I.m;
+        bvec = Bt.b + I.off_b;
+    }
     const int m = A.in.m, n = A.in.n;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned FULL = 0xffffffffu;
@@ -124,8 +156,53 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, 1) k_epoch_spe
     const int order = A.order;
     int4 *grec = A.atoms;
     const float INF = std::numeric_limits<float>::infinity();
+    int fx = 0;  // BATCH: fixed-point scale of the certificate's column sums
+    if constexpr (BATCH) fx = rec_fixed_exp(rec_total_mass(A.in.a, m, cred));
+    // BATCH: the certificate of the current plan (all threads); q refreshed
+    // in global memory; the instance's state updated; true to stop
+    auto certify = [&](long long E) -> bool {
+        unsigned long long *csum = reinterpret_cast<unsigned long long *>(qh);  // WID words over qh, ql
+        float *qf = reinterpret_cast<float *>(lastmod);  // reset before the next epoch
+        int *jrow = reinterpret_cast<int *>(aring);        // kSpecRecSlots x 1 KiB = kRecRowChunk ints
+        const RecCert c = rec_certificate(grec, m, n, A.in.X, ys, A.in.a, bvec, Bt.rho, fx, csum, qf, jrow, cred);
+        const double *qd = reinterpret_cast<const double *>(csum);
+        for (int j = tid; j < n; j += NT) A.q[j] = qd[j];
+        if (tid == 0) {
+            SpecInstState &S = Bt.state[inst];
+            S.f = c.f;
+            S.g = c.g;
+            S.feas = c.feas;
+            const bool conv = Bt.tol > 0.0 && c.g <= Bt.tol * c.f && c.feas <= kFeasTol;
+            int stop = 0;
+            if (conv || E >= Bt.max_epochs) {
+                S.status = (conv || Bt.tol <= 0.0) ? kInstOk : kInstNotConverged;
+                S.active = 0;
+                stop = 1;
+            } else if (Bt.tol > 0.0) {
+                // far above the tolerance the next certificate comes later
+                const double rel = c.f > 0.0 ? c.g / c.f : 0.0;
+                const long long skip =
+                    rel > 1000.0 * Bt.tol ? 8 : (rel > 100.0 * Bt.tol ? 4 : (rel > 10.0 * Bt.tol ? 2 : 1));
+                S.next_cert = E + skip * Bt.gap_every;
+            }
+            ctl[1] = stop;
+        }
+        __syncthreads();
+        return ctl[1] != 0;
+    };
+    bool finished = false;
+    if constexpr (BATCH) {
+        if (Bt.max_epochs <= 0) {  // the certificate of the initial plan only
+            for (int j = tid; j < n; j += NT)
+                ys[j] = make_float4(A.in.Y[(size_t)j * 3], A.in.Y[(size_t)j * 3 + 1], A.in.Y[(size_t)j * 3 + 2], 0.f);
+            __syncthreads();
+            finished = certify(0);
+            finished = true;
+        }
+    }
 
-    // ---- one-time set-up ------------------------------------------------
+    // ---- epochs: one per launch, or (BATCH) until the instance stops -----
+    for (int epoch_in_launch = 0; !finished; ++epoch_in_launch) {
     for (int j = tid; j < WID; j += NT) {
         if (j < n) {
             const double qq = A.q[j];
@@ -143,6 +220,12 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, 1) k_epoch_spe
     const long long spin = A.spin_limit > 0 ? A.spin_limit : kSpecSpin;
     if (tid == 0) {
         for (int s = 0; s < kSpecSlots; ++s) {
+            if (epoch_in_launch > 0) {  // every wait and arrival of the last epoch is over
+                mbar_inval(full + s);
+                mbar_inval(done + s);
+                mbar_inval(decided + s);
+                mbar_inval(prepd + s);
+            }
             mbar_init(full + s, NWP + 1);
             mbar_init(done + s, 1);
             mbar_init(decided + s, 1);
@@ -150,7 +233,8 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, 1) k_epoch_spe
             dec[s] = make_int2(-1, -1);
         }
         ctl[0] = 0;
-        for (int e = 0; e < 16; ++e) recent[e] = -1;
+        if (SPLIT)
+            for (int e = 0; e < 16; ++e) recent[e] = -1;
         if (A.resume) *A.resume = -1;
         if (A.gate) {  // the start gate: a bounded wait for a non-zero word
             long long it = 0;
@@ -169,7 +253,8 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, 1) k_epoch_spe
 
     auto row_of = [&](int u) -> int {
         if (order == SR_OT_PERMUTE) return A.perm[u];
-        if (order == SR_OT_UNIFORM) return scale_u64(sm64_draw(A.seed, 2, (uint64_t)(A.k0 + u)), m);
+        // uniform order runs on the split chain only
+        if (SPLIT && order == SR_OT_UNIFORM) return scale_u64(sm64_draw(A.seed, 2, (uint64_t)(A.k0 + u)), m);
         return u;
     };
     // gradient of row x at column j with the residual as it is now
@@ -559,7 +644,7 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, 1) k_epoch_spe
             if (lane == 0 && A.trace && k < A.trace_cap) {
                 A.trace[4 * k] = row;
                 A.trace[4 * k + 1] = js;
-                A.trace[4 * k + 2] = (st.v >= 0 && st.v < n) ? st.v : -1;
+                A.trace[4 * k + 2] = trace_vdir((st.v >= 0 && st.v < n) ? st.v : -1, S.kind);
                 A.trace[4 * k + 3] = __float_as_int(S.gamma);
             }
             c3[0] = c2[0];
@@ -777,7 +862,7 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, 1) k_epoch_spe
             if (lane == 0 && A.trace && k < A.trace_cap) {
                 A.trace[4 * k] = row;
                 A.trace[4 * k + 1] = js;
-                A.trace[4 * k + 2] = (st.v >= 0 && st.v < n) ? st.v : -1;
+                A.trace[4 * k + 2] = trace_vdir((st.v >= 0 && st.v < n) ? st.v : -1, S.kind);
                 A.trace[4 * k + 3] = __float_as_int(S.gamma);
             }
         }
@@ -785,6 +870,35 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, 1) k_epoch_spe
     }
     __syncthreads();
     for (int j = tid; j < n; j += NT) A.q[j] = (double)qh[j] - (double)ql[j];
+    if constexpr (!BATCH) {
+        break;
+    } else {
+        // count the epoch; stop on a record overflow, a non-finite value or
+        // a wait that gave up; else take the certificate when it is due
+        if (tid == 0) {
+            SpecInstState &S = Bt.state[inst];
+            const int rs = *A.resume, ds = *A.status;
+            S.ep += 1;
+            S.updates += rs >= 0 ? rs : m;
+            int stop = 0, due = 0;
+            if (rs >= 0 || ds != 0) {
+                S.status = rs >= 0 ? kInstNeedsDense : (ds == kDevTimeout ? kInstTimeout : kInstNonFinite);
+                S.active = 0;
+                stop = 1;
+            } else {
+                const long long E = S.ep;
+                due = (E % Bt.gap_every == 0 && E >= S.next_cert) || E >= Bt.max_epochs;
+            }
+            ctl[1] = stop;
+            ctl[2] = due;
+            ctl[3] = (int)(S.ep & 0x7FFFFFFF);
+        }
+        __syncthreads();
+        if (ctl[1]) break;
+        if (ctl[2] && certify(Bt.state[inst].ep)) break;
+        A.k0 += m;
+    }
+    }  // epochs
 }
 
 template <int NWP, int G>
@@ -793,19 +907,21 @@ static size_t spec_smem() {
     size_t b = (size_t)WID * (4 + 4 + 16 + 4);
     b += (size_t)kSpecRecSlots * kAtomRecord * 16;
     b += (size_t)kSpecSlots * (kAtomWords * 16 + NWP * 8 + 4 * 8 + 8 + 16);
-    b += 16 + 16 * 4;
+    b += 16 + 16 * 4 + 6 * 16 * sizeof(double);
     return b;
 }
 
-template <int NWP, int G, int CH, bool SPLIT>
-static void launch_spec(const EpochArgs<float> &A, cudaStream_t st) {
-    auto kern = k_epoch_spec<NWP, G, CH, SPLIT>;
+template <int NWP, int G, int CH, bool SPLIT, bool BATCH = false>
+static void launch_spec(const EpochArgs<float> &A, cudaStream_t st, const SpecBatchArgs *B = nullptr,
+                        int grid = 1) {
+    auto kern = k_epoch_spec<NWP, G, CH, SPLIT, BATCH>;
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
         attr_set = true;
     }
-    kern<<<1, NWP * kWarp + (2 + CH) * kWarp, spec_smem<NWP, G>(), st>>>(A);
+    SpecBatchArgs none{};
+    kern<<<grid, NWP * kWarp + (2 + CH) * kWarp, spec_smem<NWP, G>(), st>>>(A, B ? *B : none);
 }
 
 template <int CH, bool SPLIT>
@@ -817,6 +933,39 @@ static bool launch_spec_ch(const EpochArgs<float> &A, cudaStream_t st) {
     else if (n <= 128 * 32) launch_spec<4, 8, CH, SPLIT>(A, st);
     else return false;
     return true;
+}
+
+int spec_batch_bucket(int n) {
+    for (int b = 0; b < kSpecBatchBuckets; ++b)
+        if (n <= 512 << b) return b;
+    return -1;
+}
+
+template <bool SPLIT>
+static bool launch_spec_batch_b(int bucket, const EpochArgs<float> &A, const SpecBatchArgs &B, int count,
+                                cudaStream_t st) {
+    switch (bucket) {
+        case 0: launch_spec<4, 1, 3, SPLIT, true>(A, st, &B, count); return true;
+        case 1: launch_spec<4, 2, 3, SPLIT, true>(A, st, &B, count); return true;
+        case 2: launch_spec<4, 4, 3, SPLIT, true>(A, st, &B, count); return true;
+        case 3: launch_spec<4, 8, 3, SPLIT, true>(A, st, &B, count); return true;
+        default: return false;
+    }
+}
+
+bool launch_spec_batch_solve(int bucket, bool uniform, const SpecBatchArgs &B, int count,
+                             unsigned long long seed, long long spin_limit, cudaStream_t st) {
+    if (count <= 0) return true;
+    EpochArgs<float> A{};
+    A.in.cost_mode = kCostPts3;
+    A.rho = B.rho;
+    A.variant = SR_OT_BCPFW;
+    A.step = SR_OT_ELS;
+    A.order = uniform ? SR_OT_UNIFORM : SR_OT_CYCLIC;
+    A.seed = seed;
+    A.spin_limit = spin_limit;
+    return uniform ? launch_spec_batch_b<true>(bucket, A, B, count, st)
+                   : launch_spec_batch_b<false>(bucket, A, B, count, st);
 }
 
 bool launch_epoch_spec(const EpochArgs<float> &A, cudaStream_t st, int chain) {

@@ -40,14 +40,19 @@ def make_batch(seed, count, lo, hi, rho=10.0):
     return insts
 
 
-@pytest.mark.parametrize("variant,order", [("BCPFW", "CYCLIC"), ("BCAFW", "UNIFORM"), ("BCPFW", "PERMUTE")])
-def test_batched_converges_to_oracle_optimum(S, h, oracle_mod, variant, order):
+# kernels: AUTO takes the batched speculative form for pairwise steps in
+# cyclic or uniform order; TWO_PHASE keeps the persistent two-phase kernel
+@pytest.mark.parametrize("variant,order,kernel", [("BCPFW", "CYCLIC", "AUTO"), ("BCPFW", "CYCLIC", "TWO_PHASE"),
+                                                  ("BCPFW", "UNIFORM", "AUTO"), ("BCAFW", "UNIFORM", "AUTO"),
+                                                  ("BCPFW", "PERMUTE", "AUTO")])
+def test_batched_converges_to_oracle_optimum(S, h, oracle_mod, variant, order, kernel):
     from paper_2103_05857_gb300.batch import PackedBatch
     insts = make_batch(7, 9, 20, 300)
     pb = PackedBatch(insts)
     st, res = h.solve_batched(pb.X, pb.Y, pb.a, pb.b, pb.T, pb.sizes, pb.offsets,
                               variant=getattr(S, variant), step=S.ELS, order=getattr(S, order),
-                              seed=5, rho=10.0, tol_rel_gap=1e-6, max_epochs=20000)
+                              seed=5, rho=10.0, tol_rel_gap=1e-6, max_epochs=20000,
+                              epoch_kernel=getattr(S, "EPOCH_" + kernel))
     assert st == S.OK
     for k, inst in enumerate(insts):
         r = res[k]
@@ -87,14 +92,17 @@ def test_batched_decay_rule_trajectory(S, h, oracle_mod):
         assert np.abs(host(pb.plan(k)) - To).max() <= 1e-6
 
 
-def test_batched_oversize_and_replay(S, h, oracle_mod):
-    """An instance wider than the batched tiles is solved on the single-
-    instance path; a second call with the same shapes replays the captured
-    graph and gives the same results."""
+@pytest.mark.parametrize("kernel", ["AUTO", "TWO_PHASE"])
+def test_batched_oversize_and_replay(S, h, oracle_mod, kernel):
+    """An instance wider than the batched widths (n = 2600 > 2048 for the
+    two-phase kernel, n = 5000 > 4096 for the speculative form) is solved on
+    the single-instance path; a second call with the same shapes (replaying
+    the captured graph of the two-phase kernel) gives the same results."""
     from paper_2103_05857_gb300.batch import PackedBatch
-    insts = make_batch(3, 4, 50, 150) + [W.colour_instance(99, 40, 2600, rho=10.0).rounded()]
+    wide = 2600 if kernel == "TWO_PHASE" else 5000
+    insts = make_batch(3, 4, 50, 150) + [W.colour_instance(99, 40, wide, rho=10.0).rounded()]
     pb = PackedBatch(insts)
-    kw = dict(variant=S.BCPFW, step=S.ELS, rho=10.0, max_epochs=25)
+    kw = dict(variant=S.BCPFW, step=S.ELS, rho=10.0, max_epochs=25, epoch_kernel=getattr(S, "EPOCH_" + kernel))
     st1, r1 = h.solve_batched(pb.X, pb.Y, pb.a, pb.b, pb.T, pb.sizes, pb.offsets, **kw)
     T1 = pb.T.clone()
     st2, r2 = h.solve_batched(pb.X, pb.Y, pb.a, pb.b, pb.T, pb.sizes, pb.offsets, **kw)
@@ -156,7 +164,8 @@ FULL_SIZES = [(300, 250), (1900, 256), (700, 500), (2048, 511), (1500, 1000), (4
               (2048, 2048), (1200, 1900)]
 
 
-def test_batched_every_bucket_at_workload_sizes(S, h, oracle_mod):
+@pytest.mark.parametrize("kernel", ["AUTO", "TWO_PHASE"])
+def test_batched_every_bucket_at_workload_sizes(S, h, oracle_mod, kernel):
     """Instances in every size bucket up to n = 2048 (the sizes of the
     colour_batch512 workload), solved in one batched call to rel. gap 1e-6.
     Each returned plan is certified by the oracle (FP64, Thm 2): its gap is at
@@ -168,7 +177,8 @@ def test_batched_every_bucket_at_workload_sizes(S, h, oracle_mod):
              for k, (m, n) in enumerate(FULL_SIZES)]
     pb = PackedBatch(insts)
     st, res = h.solve_batched(pb.X, pb.Y, pb.a, pb.b, pb.T, pb.sizes, pb.offsets, variant=S.BCPFW,
-                              step=S.ELS, rho=10.0, tol_rel_gap=1e-6, max_epochs=20000)
+                              step=S.ELS, rho=10.0, tol_rel_gap=1e-6, max_epochs=20000,
+                              epoch_kernel=getattr(S, "EPOCH_" + kernel))
     assert st == S.OK
     for k, inst in enumerate(insts):
         r = res[k]
@@ -238,3 +248,32 @@ def test_batched_warm_start(S, h, oracle_mod):
     C0 = oracle_mod.cost(inst0.X, inst0.Y)
     cert = oracle_mod.certificate(C0, inst0.a, inst0.b, inst0.rho, host(T3[oT:oT + inst0.m * inst0.n].view(inst0.m, inst0.n)))
     assert cert["g"] <= 1.5e-6 * cert["f"]
+
+
+def test_batched_speculative_fixed_epochs_and_zero_epochs(S, h, oracle_mod):
+    """Without a tolerance the batched speculative form runs exactly
+    max_epochs epochs of every instance (uniform order here), and the
+    reported certificate is the oracle's certificate of the returned plan;
+    with max_epochs = 0 the plans stay at T0 = (a_i e_0) (Thm 1) and the
+    certificate is that of T0."""
+    from paper_2103_05857_gb300.batch import PackedBatch
+    insts = make_batch(23, 7, 30, 700)
+    for epochs in (0, 13):
+        pb = PackedBatch(insts)
+        st, res = h.solve_batched(pb.X, pb.Y, pb.a, pb.b, pb.T, pb.sizes, pb.offsets, variant=S.BCPFW,
+                                  step=S.ELS, order=S.UNIFORM, seed=9, rho=10.0, max_epochs=epochs)
+        assert st == S.OK
+        for k, inst in enumerate(insts):
+            r = res[k]
+            assert r["epochs"] == epochs and r["block_updates"] == epochs * inst.m
+            Tg = host(pb.plan(k))
+            if epochs == 0:
+                T0 = np.zeros((inst.m, inst.n))
+                T0[:, 0] = inst.a
+                assert np.array_equal(Tg, T0)
+            C = oracle_mod.cost(inst.X, inst.Y)
+            cert = oracle_mod.certificate(C, inst.a, inst.b, inst.rho, Tg)
+            assert rel(r["objective"], cert["f"]) <= 2e-7
+            assert abs(r["gap"] - cert["g"]) <= 2e-7 * cert["f"]
+            assert Tg.min() >= 0.0
+            np.testing.assert_allclose(Tg.sum(1), inst.a, rtol=2e-5)

@@ -295,9 +295,19 @@ def test_fp64_line_search_variants(S, h, oracle_mod, variant, order):
 # Epoch replay: from one state, one GPU epoch against one oracle epoch
 # ---------------------------------------------------------------------------
 def _trace_rows(tr):
-    """Per update (i, j*, v, gamma) from a device trace buffer."""
+    """Per update (i, j*, v, gamma) from a device trace buffer (word 2 holds
+    v in bits 0..28, all ones for none, and the direction above)."""
     t = tr.cpu().numpy().reshape(-1, 4)
-    return t[:, 0], t[:, 1], t[:, 2], t[:, 3].copy().view(np.float32).astype(np.float64)
+    v = t[:, 2] & 0x1FFFFFFF
+    v = np.where(v == 0x1FFFFFFF, -1, v)
+    return t[:, 0], t[:, 1], v, t[:, 3].copy().view(np.float32).astype(np.float64)
+
+
+def _trace_dirs(tr):
+    """Per update the direction the GPU stepped in: 0 toward j*, 1 away from
+    v, 2 pairwise, -1 no step."""
+    d = (tr.cpu().numpy().reshape(-1, 4)[:, 2] >> 29) & 3
+    return np.where(d == 3, -1, d)
 
 
 def near_tie(C, a, T, r, i, rho, variant, tol_rel=2e-6):
@@ -350,16 +360,39 @@ def near_tie(C, a, T, r, i, rho, variant, tol_rel=2e-6):
     return None
 
 
-def _gpu_direction(variant, tie, oracle_dir):
-    """The direction the GPU took at an update whose decision differed from
-    the oracle's at a near tie: BCFW always steps toward the LMO vertex and
-    BCPFW always moves mass pairwise; a BCAFW step changes direction only
-    when the tie was the choice between the FW and the away direction."""
-    if variant == "BCFW":
-        return 0
-    if variant == "BCPFW":
-        return 2
-    return (1 - oracle_dir) if (tie == "FW or away" and oracle_dir in (0, 1)) else oracle_dir
+def _fw_away_gammas(C, a, T, r, i, rho, j, v):
+    """Exact line-search steps (eq. 8) of row i toward vertex j (FW) and away
+    from atom v, at state (T, r); None where the direction does not exist."""
+    g = C[i] + rho * r
+    t = T[i]
+    ai = a[i]
+    s2 = float(t @ t)
+    tg = float(t @ g)
+    out = [None, None]
+    dd = (s2 - t[j] * t[j]) + (ai - t[j]) ** 2
+    if dd > 0:
+        out[0] = min(max((tg - ai * g[j]) / (rho * dd), 0.0), 1.0)
+    if 0 <= v < len(t) and 0 < t[v] < ai:
+        dd = (s2 - t[v] * t[v]) + (ai - t[v]) ** 2
+        alpha = t[v] / ai
+        if dd > 0:
+            out[1] = min(max((ai * g[v] - tg) / (rho * dd), 0.0), alpha / (1.0 - alpha))
+    return out
+
+
+def _followed_gamma(direction, row, ai, v, gam_g):
+    """The step the oracle applies when the GPU's gamma matched its own: the
+    GPU's. A GPU gamma within 1e-6 of gamma_max is the drop step it was in
+    FP32 (atom v removed); below that the GPU kept atom v with the mass its
+    gamma leaves, whatever the oracle's own step would have done (a drop the
+    GPU did not take leaves an atom of up to 1e-7 of mass that later
+    decisions see)."""
+    if direction in (1, 2) and 0 <= v < len(row) and 0 < row[v] < ai:
+        alpha = row[v] / ai
+        gmax = alpha if direction == 2 else alpha / (1.0 - alpha)
+        if gam_g >= gmax * (1.0 - 1e-6):
+            return gmax
+    return gam_g
 
 
 EPS32 = 2.0 ** -24   # unit roundoff of binary32
@@ -411,7 +444,8 @@ def replay_epochs(S, h, O, inst, C, kw, variant, step, order, epochs, prec=None,
     vertex j*, away vertex v, step gamma; from the device trace) is compared
     with the oracle's block step at the same state, update by update:
       - the same vertices and gamma within 1e-7 + 1e-5 gamma (in units of
-        a_i): the oracle's step stands;
+        a_i): the oracle continues from the GPU's gamma (a drop stays a drop),
+        so that every later update is judged from the GPU's own state;
       - the same vertices and gamma within what FP32 resolves for this step
         (fp32_step_allowance: the line-search numerator cancels when the row
         is nearly converged, the away curvature when alpha_v is near 1) -- an
@@ -443,6 +477,7 @@ def replay_epochs(S, h, O, inst, C, kw, variant, step, order, epochs, prec=None,
     var_o, step_o, order_o = getattr(O, variant), getattr(O, step), getattr(O, order)
     ties = []
     kinds = {}
+    events = []
     steps_ill = 0
     for ep in range(epochs):
         tr = torch.full((4 * m,), -1, dtype=torch.int32, device="cuda")
@@ -452,6 +487,7 @@ def replay_epochs(S, h, O, inst, C, kw, variant, step, order, epochs, prec=None,
                       seed=seed + ep, rho=inst.rho, max_epochs=1, trace=tr, trace_capacity=m, **kw)
         Tg = host(T)
         gi, gj, gv, gg = _trace_rows(tr)
+        gd = _trace_dirs(tr)
         _, ro, ti, _, _ = O.solve(C, inst.a, inst.b, T0=start, rho=inst.rho, variant=var_o,
                                   step=step_o, order=order_o, seed=seed + ep, max_epochs=1, trace=True)
         np.testing.assert_array_equal(gi, ti)  # same block order
@@ -469,8 +505,16 @@ def replay_epochs(S, h, O, inst, C, kw, variant, step, order, epochs, prec=None,
                                           rho=inst.rho)
             if gam == 0.0 and gg[p] == 0.0:
                 continue  # neither moved: the state is the same whatever vertex was named
-            same_vertices = gj[p] == js and (variant == "BCFW" or gv[p] == v)
+            same_vertices = gj[p] == js and (variant == "BCFW" or gv[p] == v) and (gd[p] == dr or gam == 0.0)
             if same_vertices and abs(gg[p] - gam) * ai <= 1e-7 + 1e-5 * abs(gam) * ai:
+                # the same decision: the oracle takes the GPU's gamma from here on, so
+                # that the states both sides decide from do not drift apart by the
+                # tolerance of this comparison over the epoch
+                gam_f = _followed_gamma(dr, row_before, ai, v, float(gg[p]))
+                if gam_f != gam:
+                    Tr[i] = row_before
+                    rr[:] = r_before
+                    O.apply_step(inst.a, Tr, rr, i, dr, js, v, gam_f)
                 continue
             Tpre = Tr.copy()
             Tpre[i] = row_before
@@ -491,8 +535,14 @@ def replay_epochs(S, h, O, inst, C, kw, variant, step, order, epochs, prec=None,
                             g_fw=float(tt @ gr - ai * gr[js]),
                             g_aw=(float(ai * gr[v] - tt @ gr) if 0 <= v < n else None),
                             allowance=fp32_step_allowance(C, inst.a, Tpre, r_before, i, inst.rho, dr, js, v, gam)
-                            if same_vertices else None, nnz=int((tt > 0).sum()), row_drift=float(tt.sum() - ai))
-            assert tie is not None, (ep, p, i, (gj[p], js), (gv[p], v), (gg[p], gam), info)
+                            if same_vertices else None, nnz=int((tt > 0).sum()), row_drift=float(tt.sum() - ai),
+                            gammas_fw_away=_fw_away_gammas(C, inst.a, Tpre, r_before, i, inst.rho, int(gj[p]),
+                                                           int(gv[p])),
+                            r_consistent=float(np.abs(r_before - (Tpre.sum(0) - inst.b)).max()),
+                            kinds=dict(kinds), steps_ill=steps_ill,
+                            events_here=[e for e in events if e[2] == i or e[5] in (js, v) or e[6] in (js, v)][-8:],
+                            last_events=events[-5:])
+            assert tie is not None, repr((ep, p, i, (gj[p], js), (gv[p], v), (gg[p], gam), info))
             kinds[tie] = kinds.get(tie, 0) + 1
             if tie == "ill-conditioned step":
                 steps_ill += 1  # the same decision, a step FP32 resolves only this far
@@ -504,7 +554,8 @@ def replay_epochs(S, h, O, inst, C, kw, variant, step, order, epochs, prec=None,
             light = (Tr[i] > 0) & (Tr[i] <= NEGLIGIBLE * ai)
             rr[light] -= Tr[i][light]
             Tr[i][light] = 0.0
-            gdir, gam_g = _gpu_direction(variant, tie, dr), float(gg[p])
+            gdir, gam_g = int(gd[p]), float(gg[p])  # the direction the GPU took (from its trace)
+            events.append((ep, p, i, tie, gdir, int(gj[p]), int(gv[p]), gam_g))
             gvc = int(gv[p])
             if gdir in (1, 2) and 0 <= gvc < n and Tr[i, gvc] > 0:
                 alpha = Tr[i, gvc] / ai
