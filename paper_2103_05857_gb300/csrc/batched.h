@@ -58,6 +58,8 @@ struct SpecInstState {
     long long updates;    // block updates done
     long long next_cert;  // epochs done before the next certificate may be taken
     double f, g, feas;    // last certificate
+    double est;           // running gap of the last epoch (sum of its pairwise gaps)
+    double kappa;         // est / g at the last certificate (0: none yet)
     int active;           // 1 while the instance runs
     int status;           // InstStatus once stopped
     int devstat;          // DevStatus word of the epoch kernel (0: none)

@@ -97,19 +97,50 @@ __device__ inline RecCert rec_certificate(const int4 *grec, int m, int n, const 
     float feas = 0.f;
     for (int r0 = 0; r0 < m; r0 += kRecRowChunk) {
         const int r1 = min(m, r0 + kRecRowChunk);
-        // (a) LMO vertex of each row: FP32 keys of c_ij + q_j, ties to the
-        // smallest j
-        for (int i = r0 + warp; i < r1; i += nw) {
-            const float x0 = X[(size_t)i * 3], x1 = X[(size_t)i * 3 + 1], x2 = X[(size_t)i * 3 + 2];
-            uint32_t kb = 0xFFFFFFFFu;
-            int jb = 0x7FFFFFFF;
-            for (int j = lane; j < n; j += kWarp) {
-                const uint32_t k = f2key(rec_cost3(x0, x1, x2, ys[j]) + qf[j]);
-                if (k < kb) { kb = k; jb = j; }
+        // (a) LMO vertex of each row, c_ij + q_j in FP32 (the operations of
+        // rec_cost3, on row pairs in packed FP32x2), ties to the smallest j;
+        // four rows per warp pass, so each (y_j, q_j) read from shared
+        // memory serves four rows
+        for (int i0 = r0 + 4 * warp; i0 < r1; i0 += 4 * nw) {
+            float2 x0[2], x1[2], x2[2];
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                const int ra = min(i0 + 2 * p, r1 - 1), rb = min(i0 + 2 * p + 1, r1 - 1);
+                x0[p] = make_float2(X[(size_t)ra * 3], X[(size_t)rb * 3]);
+                x1[p] = make_float2(X[(size_t)ra * 3 + 1], X[(size_t)rb * 3 + 1]);
+                x2[p] = make_float2(X[(size_t)ra * 3 + 2], X[(size_t)rb * 3 + 2]);
             }
-            const uint32_t wk = __reduce_min_sync(FULL, kb);
-            const int jm = __reduce_min_sync(FULL, kb == wk ? jb : 0x7FFFFFFF);
-            if (lane == 0) jrow[i - r0] = jm;
+            float best[4];
+            int bj[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                best[r] = __int_as_float(0x7f800000);  // +inf; a column index in range even if no
+                bj[r] = min(lane, n - 1);               // value is below it
+            }
+            for (int j = lane; j < n; j += kWarp) {
+                const float4 y = ys[j];
+                const float qj = qf[j];
+                const float2 ny0 = make_float2(-y.x, -y.x), ny1 = make_float2(-y.y, -y.y),
+                             ny2 = make_float2(-y.z, -y.z), q2 = make_float2(qj, qj);
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    const float2 d0 = __fadd2_rn(x0[p], ny0), d1 = __fadd2_rn(x1[p], ny1),
+                                 d2 = __fadd2_rn(x2[p], ny2);
+                    float2 c = __fmul2_rn(d0, d0);
+                    c = __ffma2_rn(d1, d1, c);
+                    c = __ffma2_rn(d2, d2, c);
+                    c = __fadd2_rn(c, q2);
+                    if (c.x < best[2 * p]) { best[2 * p] = c.x; bj[2 * p] = j; }
+                    if (c.y < best[2 * p + 1]) { best[2 * p + 1] = c.y; bj[2 * p + 1] = j; }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const uint32_t kb = f2key(best[r]);
+                const uint32_t wk = __reduce_min_sync(FULL, kb);
+                const int jm = __reduce_min_sync(FULL, kb == wk ? bj[r] : 0x7FFFFFFF);
+                if (lane == 0 && i0 + r < r1) jrow[i0 + r - r0] = jm;
+            }
         }
         __syncthreads();
         // (b) one row per thread, FP64: <t_i, c_i>, <t_i, q>, a_i (c_ij* + q_j*)
@@ -125,7 +156,7 @@ __device__ inline RecCert rec_certificate(const int4 *grec, int m, int n, const 
                 l2 += t * q[at.x];
                 l3 += t;
             }
-            const int jm = jrow[i - r0];
+            const int jm = min(max(jrow[i - r0], 0), n - 1);
             const double ai = (double)a[i];
             lin += l1;
             tq += l2;
