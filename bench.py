@@ -51,8 +51,9 @@ BATCH_WORKLOADS = ("colour_batch512", "colour_batch64_2048")
 # is built from are the ones captured: their digest at capture time must match.
 CAPTURED_TRAFFIC = {
     ("colour4096_fp32", "roofline"): {
-        "bytes": 4403200, "files": ("solve_spec.cu", "atoms.cuh", "step.cuh", "cpasync.cuh", "common.cuh"),
-        "digest": "873f40eed9762843"},
+        "bytes": 731648, "files": ("solve_spec.cu", "atoms.cuh", "step.cuh", "cpasync.cuh", "common.cuh",
+                                   "cert_records.cuh", "batched.h", "internal.h"),
+        "digest": "a566bce288bbb9e4"},
     ("feature8192_d128", "roofline_cost"): {
         "bytes": 4290048 + 207054592, "files": ("cost_bf16.cu", "common.cuh"), "digest": "37d37fe188a2335d"},
     ("colour_batch64_2048", "roofline_adjoint"): {
