@@ -58,8 +58,8 @@ struct SpecInstState {
     long long updates;    // block updates done
     long long next_cert;  // epochs done before the next certificate may be taken
     double f, g, feas;    // last certificate
-    double est;           // running gap of the last epoch (sum of its pairwise gaps)
-    double kappa;         // est / g at the last certificate (0: none yet)
+    double g_prev;        // gap at the last certificate that did not stop (0: none yet)
+    long long ep_prev;    // epochs done at that certificate
     int active;           // 1 while the instance runs
     int status;           // InstStatus once stopped
     int devstat;          // DevStatus word of the epoch kernel (0: none)

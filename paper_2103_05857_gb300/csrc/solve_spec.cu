@@ -128,7 +128,6 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
     int *ctl = reinterpret_cast<int *>(prep + kSpecSlots);                   // [0] stop
     int *recent = ctl + 4;                                                   // rows of the last 16 updates
     double *cred = reinterpret_cast<double *>(recent + 16);                  // certificate partials (BATCH)
-    float *egap = reinterpret_cast<float *>(cred + 6 * 16);                  // running gap per chain warp (BATCH)
 
     EpochArgs<float> A = A0;
     int inst = -1;
@@ -173,7 +172,6 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
             S.f = c.f;
             S.g = c.g;
             S.feas = c.feas;
-            if (c.g > 0.0 && S.est > 0.0) S.kappa = S.est / c.g;
             const bool conv = Bt.tol > 0.0 && c.g <= Bt.tol * c.f && c.feas <= kFeasTol;
             int stop = 0;
             if (conv || E >= Bt.max_epochs) {
@@ -181,9 +179,18 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
                 S.active = 0;
                 stop = 1;
             } else if (Bt.tol > 0.0) {
-                // far above the tolerance the next certificate comes later
-                const double rel = c.f > 0.0 ? c.g / c.f : 0.0;
-                const long long skip = rel > 100.0 * Bt.tol ? 8 : (rel > 10.0 * Bt.tol ? 4 : 2);
+                // the next certificate when the gap's decay since the last one,
+                // taken as geometric (linear convergence), predicts the
+                // tolerance; at most 8 epochs on (each refreshes the residual)
+                long long skip = 2;
+                if (S.g_prev > 0.0 && c.g > 0.0 && c.g < S.g_prev && E > S.ep_prev) {
+                    const double rate = log(c.g / S.g_prev) / (double)(E - S.ep_prev);  // < 0
+                    const double need = log(Bt.tol * c.f / c.g) / rate;                  // > 0
+                    const double early = 0.75 * need;  // rather a certificate too early than late
+                    skip = early >= 8.0 ? 8 : (early < 1.0 ? 1 : (long long)early);
+                }
+                S.g_prev = c.g;
+                S.ep_prev = E;
                 S.next_cert = E + skip * Bt.gap_every;
             }
             ctl[1] = stop;
@@ -236,7 +243,6 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
         ctl[0] = 0;
         if (SPLIT)
             for (int e = 0; e < 16; ++e) recent[e] = -1;
-        for (int e = 0; e < 4; ++e) egap[e] = 0.f;
         if (A.resume) *A.resume = -1;
         if (A.gate) {  // the start gate: a bounded wait for a non-zero word
             long long it = 0;
@@ -511,7 +517,6 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
         // applies and publishes -- with no hand-over between warps on its
         // chain.
         bool aborted = false;
-        float rgap = 0.f;  // BATCH: sum of the pairwise gaps a_i (g_v - g_min) of this epoch's updates
         int c1[2] = {-1, -1}, c2[2] = {-1, -1}, c3[2] = {-1, -1};  // columns of updates u-1, u-2, u-3
         const bool repeats = order == SR_OT_UNIFORM;  // a row may come back within the window
         for (int u = 0; u < m; ++u) {
@@ -650,7 +655,6 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
                 A.trace[4 * k + 2] = trace_vdir((st.v >= 0 && st.v < n) ? st.v : -1, S.kind);
                 A.trace[4 * k + 3] = __float_as_int(S.gamma);
             }
-            if (BATCH && st.vpos >= 0 && ai > 0.f) rgap += ai * (st.gmax - gmin);
             c3[0] = c2[0];
             c3[1] = c2[1];
             c2[0] = c1[0];
@@ -658,7 +662,6 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
             c1[0] = moved ? S.js : -1;
             c1[1] = moved ? S.v : -1;
         }
-        if (BATCH && lane == 0) egap[0] = rgap;
         if (aborted && lane == 0) vstore(ctl, 1);  // releases every other warp still waiting
     } else {
         // ================= chain warps ====================================
@@ -671,7 +674,6 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
         // evaluates them and decides.
         const int cwi = warp - (NWP + 2);
         bool aborted = false;
-        float rgap = 0.f;  // BATCH: sum of the pairwise gaps a_i (g_v - g_min) of this warp's updates
         auto wait_bar = [&](uint64_t *b, unsigned parity) -> bool {
             long long it = 0;
             while (!mbar_try(b, parity)) {
@@ -871,9 +873,7 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
                 A.trace[4 * k + 2] = trace_vdir((st.v >= 0 && st.v < n) ? st.v : -1, S.kind);
                 A.trace[4 * k + 3] = __float_as_int(S.gamma);
             }
-            if (BATCH && st.vpos >= 0 && ai > 0.f) rgap += ai * (st.gmax - gmin);
         }
-        if (BATCH && lane == 0) egap[1 + cwi] = rgap;
         if (aborted && lane == 0) vstore(ctl, 1);  // releases every other warp still waiting
     }
     __syncthreads();
@@ -894,16 +894,8 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
                 S.active = 0;
                 stop = 1;
             } else {
-                // due every gap_every epochs from next_cert on, and at once when
-                // the epoch's running gap (an upper estimate: a pairwise gap
-                // bounds the block's FW gap) scaled by its last observed ratio
-                // to the certificate says the tolerance is reached
                 const long long E = S.ep;
-                const double est = (double)egap[0] + (double)egap[1] + (double)egap[2] + (double)egap[3];
-                S.est = est;
-                const double kap = S.kappa > 1.0 ? S.kappa : 1.0;
-                const bool near = Bt.tol > 0.0 && S.f > 0.0 && est <= kap * Bt.tol * S.f;
-                due = (E % Bt.gap_every == 0 && (E >= S.next_cert || near)) || E >= Bt.max_epochs;
+                due = (E % Bt.gap_every == 0 && E >= S.next_cert) || E >= Bt.max_epochs;
             }
             ctl[1] = stop;
             ctl[2] = due;
@@ -923,7 +915,7 @@ static size_t spec_smem() {
     size_t b = (size_t)WID * (4 + 4 + 16 + 4);
     b += (size_t)kSpecRecSlots * kAtomRecord * 16;
     b += (size_t)kSpecSlots * (kAtomWords * 16 + NWP * 8 + 4 * 8 + 8 + 16);
-    b += 16 + 16 * 4 + 6 * 16 * sizeof(double) + 4 * sizeof(float);
+    b += 16 + 16 * 4 + 6 * 16 * sizeof(double);
     return b;
 }
 
