@@ -230,8 +230,8 @@ def settings(args):
 
 def epoch_kernel_name(s, n):
     """The epoch kernel the library runs for these settings (its own dispatch:
-    speculative for pairwise steps on d = 3 points with n <= 4096, pipelined up
-    to n = 8192, else two-phase; FP64 BCFW up to n = 512 runs on one warp;
+    speculative for pairwise steps on d = 3 points with n <= 4096 and on a
+    given cost with n <= 8192, pipelined up to n = 8192, else two-phase; FP64 BCFW up to n = 512 runs on one warp;
     other FP64 and BCFW settings keep the dense-row kernel)."""
     if s["precision"] == "FP64" and s["variant"] == "BCFW" and n <= 512 and not s.get("ga"):
         return ("k_epoch_f64w (one warp, m block updates; dense rows, FP32 argmin screen with exact "
@@ -240,6 +240,9 @@ def epoch_kernel_name(s, n):
         return "k_epoch (one CTA, m block updates; dense rows)"
     if s["variant"] == "BCAFW":
         return "k_epoch_sparse (one CTA, m block updates; active-set, away steps)"
+    if s["precision"] == "FP32_BF16COST" and n <= 8192 and n % 4 == 0:
+        return ("k_epoch_spec (one CTA, m block updates; pairwise; given cost: producers stream each row, "
+                "the chain warp of an update pulls its row into L1; three chain warps in rotation)")
     if s["precision"] != "FP32_BF16COST" and n <= 4096:
         return ("k_epoch_spec (one CTA, m block updates; pairwise; segment minima and away statistics taken "
                 "ahead by producer warps, three chain warps in rotation)")

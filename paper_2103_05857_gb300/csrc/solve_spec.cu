@@ -63,6 +63,8 @@ constexpr int kSpecRecHead = 8;    // record entries fetched ahead: the count an
 // update; it knows every column changed since the producers' residual
 // without waiting on another warp).
 constexpr long long kSpecSpin = 1ll << 26;  // default polls before a wait gives up
+constexpr int kGcAhead = 2;                 // given cost: rows a producer thread has in flight
+constexpr int kGcRing = kGcAhead + 1;       // and its row slots in shared memory
 static_assert(kSpecSlots > kSpecLag && kSpecRecSlots > kSpecLag + kSpecRecAhead, "slot rings too small");
 static_assert(kSpecRecSlots * kAtomRecord * 4 >= kRecRowChunk, "the certificate's row chunk lives in the record ring");
 
@@ -93,13 +95,21 @@ __device__ inline bool mbar_try(uint64_t *b, unsigned parity) {
 }
 constexpr int kAtomWords = 3;  // atom warp output per update: int4 words
 
+// Given cost: the chain warp of an update pulls its row into L1 while it
+// prepares, so the entries it needs after the hand-over come from L1.
+__device__ inline void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];\n" ::"l"(p)); }
+
 }  // namespace
 
 // BATCH: CTA c solves instance Bt.list[c] of a batch (its sizes and arrays
 // from the batch descriptors, the other settings from A0): epoch after epoch,
 // the barriers re-initialised between them, the certificate of Thm 2 taken
 // inside the CTA when it is due, until the instance stops.
-template <int NWP, int G, int CH, bool SPLIT, bool BATCH>
+// GC: the cost matrix C is given (row-major m x n, rows on 16-byte
+// boundaries, n a multiple of 4) instead of the points: the producers load
+// their segment of each row ahead of the residual gate, the other warps read
+// the entries they need (a few per update) from global memory.
+template <int NWP, int G, int CH, bool SPLIT, bool BATCH, bool GC>
 __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <= 4) ? 2 : 1)
     k_epoch_spec(EpochArgs<float> A0, SpecBatchArgs Bt) {
     constexpr int NTC = NWP * kWarp;  // producer threads
@@ -109,13 +119,14 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
     static_assert(CH == 1 || CH == 3, "one chain warp, or three in rotation");
     static_assert(!SPLIT || CH == 3, "the split chain has two preparer warps and one decider");
     static_assert(CH <= kSpecLag, "the changed columns are known for the updates ver .. u-1");
-    static_assert(WID <= 8192, "column index must fit 13 bits");
+    static_assert(WID <= 8192, "column index must fit the 14 bits of the atom word");
+    static_assert(!(GC && BATCH), "the batched form takes points");
     static_assert(NWP + 2 * (kSpecLag - CH + 1) <= kWarp, "candidates and changed columns must fit one warp");
     extern __shared__ __align__(16) unsigned char smem[];
     float *qh = reinterpret_cast<float *>(smem);
     float *ql = qh + WID;
     float4 *ys = reinterpret_cast<float4 *>(ql + WID);
-    int *lastmod = reinterpret_cast<int *>(ys + WID);            // last update that changed column j
+    int *lastmod = reinterpret_cast<int *>(ys + (GC ? 0 : WID));  // last update that changed column j
     int4 *aring = reinterpret_cast<int4 *>(lastmod + WID);       // kSpecRecSlots atom records
     int4 *aw = aring + (size_t)kSpecRecSlots * kAtomRecord;       // kSpecSlots x kAtomWords
     unsigned long long *cand = reinterpret_cast<unsigned long long *>(aw + kSpecSlots * kAtomWords);  // kSpecSlots x NWP
@@ -128,6 +139,7 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
     int *ctl = reinterpret_cast<int *>(prep + kSpecSlots);                   // [0] stop
     int *recent = ctl + 4;                                                   // rows of the last 16 updates
     double *cred = reinterpret_cast<double *>(recent + 16);                  // certificate partials (BATCH)
+    float *cring = reinterpret_cast<float *>(cred + 6 * 16);                 // GC: kGcRing rows of C
 
     EpochArgs<float> A = A0;
     int inst = -1;
@@ -217,11 +229,12 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
             const float h = (float)qq;
             qh[j] = h;
             ql[j] = (float)((double)h - qq);
-            ys[j] = make_float4(A.in.Y[(size_t)j * 3], A.in.Y[(size_t)j * 3 + 1], A.in.Y[(size_t)j * 3 + 2], 0.f);
+            if (!GC)
+                ys[j] = make_float4(A.in.Y[(size_t)j * 3], A.in.Y[(size_t)j * 3 + 1], A.in.Y[(size_t)j * 3 + 2], 0.f);
         } else {
             qh[j] = 1e30f;
             ql[j] = 0.f;
-            ys[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (!GC) ys[j] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         lastmod[j] = -1;
     }
@@ -265,12 +278,18 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
         if (SPLIT && order == SR_OT_UNIFORM) return scale_u64(sm64_draw(A.seed, 2, (uint64_t)(A.k0 + u)), m);
         return u;
     };
-    // gradient of row x at column j with the residual as it is now
-    auto grad_at = [&](int j, float x0, float x1, float x2) -> float {
-        const float4 y = ys[j];
-        const float d0 = x0 - y.x, d1 = x1 - y.y, d2 = x2 - y.z;
-        return fmaf(d2, d2, fmaf(d1, d1, __fmul_rn(d0, d0))) + qh[j];
+    // gradient of row x (points) or of the row of C at crow (GC) at column j
+    // with the residual as it is now
+    auto grad_at = [&](int j, float x0, float x1, float x2, const float *crow) -> float {
+        if constexpr (GC) {
+            return (j < n ? __ldg(crow + j) : 0.f) + qh[j];  // padding columns: qh = 1e30
+        } else {
+            const float4 y = ys[j];
+            const float d0 = x0 - y.x, d1 = x1 - y.y, d2 = x2 - y.z;
+            return fmaf(d2, d2, fmaf(d1, d1, __fmul_rn(d0, d0))) + qh[j];
+        }
     };
+    auto crow_of = [&](int row) -> const float * { return GC ? A.in.C + (size_t)row * n : nullptr; };
     // producers and the atom warp: wait until the chain has applied update
     // u - kSpecLag - 1 (its residual is then visible); false to stop
     auto gate = [&](int u) -> bool {
@@ -295,9 +314,11 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
         xa[s][0] = xa[s][1] = xa[s][2] = xa[s][3] = 0.f;
         if (u < m) {
             const int i = row_of(u);
-            xa[s][0] = A.in.X[(size_t)i * 3];
-            xa[s][1] = A.in.X[(size_t)i * 3 + 1];
-            xa[s][2] = A.in.X[(size_t)i * 3 + 2];
+            if (!GC) {
+                xa[s][0] = A.in.X[(size_t)i * 3];
+                xa[s][1] = A.in.X[(size_t)i * 3 + 1];
+                xa[s][2] = A.in.X[(size_t)i * 3 + 2];
+            }
             xa[s][3] = A.in.a[i];
         }
     };
@@ -310,20 +331,50 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
         // the start gate timed out: no update is made, the residual is kept
     } else if (warp < NWP) {
         // ================= producers: segment minima =====================
-        float2 ny0[2 * G], ny1[2 * G], ny2[2 * G];
+        float2 ny0[GC ? 1 : 2 * G], ny1[GC ? 1 : 2 * G], ny2[GC ? 1 : 2 * G];
+        if constexpr (!GC) {
 #pragma unroll
-        for (int g = 0; g < G; ++g)
+            for (int g = 0; g < G; ++g)
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int j = 4 * (tid + NTC * g) + 2 * h;
-                const float4 ya = ys[j], yb = ys[j + 1];
-                ny0[2 * g + h] = make_float2(-ya.x, -yb.x);
-                ny1[2 * g + h] = make_float2(-ya.y, -yb.y);
-                ny2[2 * g + h] = make_float2(-ya.z, -yb.z);
-            }
+                for (int h = 0; h < 2; ++h) {
+                    const int j = 4 * (tid + NTC * g) + 2 * h;
+                    const float4 ya = ys[j], yb = ys[j + 1];
+                    ny0[2 * g + h] = make_float2(-ya.x, -yb.x);
+                    ny1[2 * g + h] = make_float2(-ya.y, -yb.y);
+                    ny2[2 * g + h] = make_float2(-ya.z, -yb.z);
+                }
+        }
         load_xa(0, 0);
         load_xa(1, 1);
+        // GC: each thread copies its own columns of the rows kGcAhead updates
+        // ahead into its part of a ring of rows (cp.async, L2 only), so the
+        // HBM latency of a row is hidden behind the updates before it
+        auto fetch_row = [&](int t) {
+            if (t < m) {
+                const float *crow = crow_of(row_of(t));
+                float *dst = cring + (size_t)(t % kGcRing) * WID;
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    const int j0 = 4 * (tid + NTC * g);
+                    if (j0 < n) cp16(dst + j0, crow + j0);
+                }
+            }
+            commit();
+        };
+        if constexpr (GC)
+            for (int t = 0; t < kGcAhead; ++t) fetch_row(t);
         for (int u = 0; u < m; ++u) {
+            float4 cv[GC ? G : 1];
+            if constexpr (GC) {
+                fetch_row(u + kGcAhead);
+                wait_groups<kGcAhead>();  // row u has landed (this thread's own copies)
+                const float *src = cring + (size_t)(u % kGcRing) * WID;
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    const int j0 = 4 * (tid + NTC * g);
+                    cv[g] = j0 < n ? *reinterpret_cast<const float4 *>(src + j0) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
             if (!gate(u)) break;
             const float2 X0 = make_float2(xa[0][0], xa[0][0]), X1 = make_float2(xa[0][1], xa[0][1]),
                          X2 = make_float2(xa[0][2], xa[0][2]);
@@ -334,13 +385,18 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
                 const int j0 = 4 * (tid + NTC * g);
                 const float4 q4 = *reinterpret_cast<const float4 *>(qh + j0);
                 float2 c[2];
+                if constexpr (GC) {
+                    c[0] = make_float2(cv[g].x, cv[g].y);
+                    c[1] = make_float2(cv[g].z, cv[g].w);
+                } else {
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const float2 d0 = __fadd2_rn(X0, ny0[2 * g + h]), d1 = __fadd2_rn(X1, ny1[2 * g + h]),
-                                 d2 = __fadd2_rn(X2, ny2[2 * g + h]);
-                    float2 cc = __fmul2_rn(d0, d0);
-                    cc = __ffma2_rn(d1, d1, cc);
-                    c[h] = __ffma2_rn(d2, d2, cc);
+                    for (int h = 0; h < 2; ++h) {
+                        const float2 d0 = __fadd2_rn(X0, ny0[2 * g + h]), d1 = __fadd2_rn(X1, ny1[2 * g + h]),
+                                     d2 = __fadd2_rn(X2, ny2[2 * g + h]);
+                        float2 cc = __fmul2_rn(d0, d0);
+                        cc = __ffma2_rn(d1, d1, cc);
+                        c[h] = __ffma2_rn(d2, d2, cc);
+                    }
                 }
                 const float2 ga = __fadd2_rn(c[0], make_float2(q4.x, q4.y));
                 const float2 gb = __fadd2_rn(c[1], make_float2(q4.z, q4.w));
@@ -366,6 +422,7 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
             shift_xa();
             load_xa(1, u + 2);
         }
+        if constexpr (GC) wait_groups<0>();  // no copy in flight at exit
     } else if (warp < AW + 2) {
         // ============ two atom warps (even, odd updates): records, away
         // ============ statistics, row data
@@ -400,15 +457,16 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
             const float x0 = xa[0][0], x1 = xa[0][1], x2 = xa[0][2], au = xa[0][3];
             LaneAtoms at = load_atoms(rs, lane);
             DF tvd{0.f, 0.f};
-            auto grad = [&](int j) -> float { return grad_at(j, x0, x1, x2); };
+            const float *crow = crow_of(row_of(u));
+            auto grad = [&](int j) -> float { return grad_at(j, x0, x1, x2, crow); };
             const AtomStats st = atom_stats(at, grad, au, false, &tvd);
             if (lane == 0) {
                 const float ra = au > 0.f ? 1.f / au : 0.f;
                 const float ia = au > 0.f ? 1.f / (2.f * rho * au) : 0.f;
-                const int vv = (st.v >= 0 && st.v < n) ? st.v : 0x1FFF;
+                const int vv = (st.v >= 0 && st.v < n) ? st.v : 0x3FFF;
                 int4 *o = aw + (u % kSpecSlots) * kAtomWords;
                 o[0] = make_int4(__float_as_int(st.gmax), __float_as_int(tvd.hi), __float_as_int(tvd.lo),
-                                 vv | ((st.vpos + 1) << 13));
+                                 vv | ((st.vpos + 1) << 14));
                 o[1] = make_int4(__float_as_int(x0), __float_as_int(x1), __float_as_int(x2), __float_as_int(au));
                 o[2] = make_int4(__float_as_int(ra), __float_as_int(ia), row_of(u), 0);
                 mbar_arrive(full + u % kSpecSlots);
@@ -453,7 +511,8 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
             const int ver = u > kSpecLag ? u - kSpecLag : 0;
             const float x0 = __int_as_float(w1.x), x1 = __int_as_float(w1.y), x2 = __int_as_float(w1.z);
             LaneAtoms at = load_atoms(aring + (size_t)(u % kSpecRecSlots) * kAtomRecord, lane);
-            auto grad = [&](int j) -> float { return grad_at(j, x0, x1, x2); };
+            const float *crow = crow_of(aw[slot * kAtomWords + 2].z);
+            auto grad = [&](int j) -> float { return grad_at(j, x0, x1, x2, crow); };
             uint32_t key = 0xFFFFFFFFu;
             int col = 0x7FFFFFFF;
             bool stale = false;
@@ -564,7 +623,8 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
                 __syncwarp();
                 if (lane == 0) recent[u & 15] = row;
             }
-            auto grad = [&](int j) -> float { return grad_at(j, x0, x1, x2); };
+            const float *crow = crow_of(row);
+            auto grad = [&](int j) -> float { return grad_at(j, x0, x1, x2, crow); };
             // the columns of updates u-1, u-2, u-3 (lanes 0..5) join the
             // prepared minimum (lane 6); a prepared minimum on one of them was
             // taken at a residual that has changed since: the full LMO instead
@@ -612,9 +672,9 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
             if (redo_atoms) {
                 st = atom_stats(at, grad, ai, false, &tvd);
             } else {
-                const int v13 = w0.w & 0x1FFF;
-                st.v = v13 == 0x1FFF ? 0x7FFFFFFF : v13;
-                st.vpos = (w0.w >> 13) - 1;
+                const int v14 = w0.w & 0x3FFF;
+                st.v = v14 == 0x3FFF ? 0x7FFFFFFF : v14;
+                st.vpos = (w0.w >> 14) - 1;
                 st.gmax = __int_as_float(w0.x);
                 st.t_v = tvd.hi;
                 st.nnz = at.cnt;
@@ -703,7 +763,10 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
             const float ai = __int_as_float(w1.w), ra = __int_as_float(w2.x), ia = __int_as_float(w2.y);
             // the atom warp's copy of the record (ordered by the full barrier)
             LaneAtoms at = load_atoms(aring + (size_t)(u % kSpecRecSlots) * kAtomRecord, lane);
-            auto grad = [&](int j) -> float { return grad_at(j, x0, x1, x2); };
+            const float *crow = crow_of(row);
+            if constexpr (GC)  // the row into L1: 128-byte lines lane, lane + 32, ...
+                for (int off = 32 * lane; off < n; off += 32 * kWarp) prefetch_l1(crow + off);
+            auto grad = [&](int j) -> float { return grad_at(j, x0, x1, x2, crow); };
             // clean segment minima and the columns changed by updates ver..u-2
             uint32_t key = 0xFFFFFFFFu;
             int col = 0x7FFFFFFF;
@@ -794,9 +857,13 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
             const int ec = lane == 0 ? c1[0] : c1[1];
             float ce = 0.f;
             if (lane < 2 && ec >= 0) {
-                const float4 y = ys[ec];
-                const float d0 = x0 - y.x, d1 = x1 - y.y, d2 = x2 - y.z;
-                ce = fmaf(d2, d2, fmaf(d1, d1, __fmul_rn(d0, d0)));
+                if constexpr (GC) {
+                    ce = __ldg(crow + ec);
+                } else {
+                    const float4 y = ys[ec];
+                    const float d0 = x0 - y.x, d1 = x1 - y.y, d2 = x2 - y.z;
+                    ce = fmaf(d2, d2, fmaf(d1, d1, __fmul_rn(d0, d0)));
+                }
             }
             if (CH > 1 && u >= 1 && !wait_bar(done + ps, pp)) { aborted = true; break; }
             if (redo_lmo) {
@@ -825,9 +892,9 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
             if (redo_atoms) {
                 st = atom_stats(at, grad, ai, false, &tvd);
             } else {
-                const int v13 = w0.w & 0x1FFF;
-                st.v = v13 == 0x1FFF ? 0x7FFFFFFF : v13;
-                st.vpos = (w0.w >> 13) - 1;
+                const int v14 = w0.w & 0x3FFF;
+                st.v = v14 == 0x3FFF ? 0x7FFFFFFF : v14;
+                st.vpos = (w0.w >> 14) - 1;
                 st.gmax = __int_as_float(w0.x);
                 st.t_v = tvd.hi;
                 st.nnz = at.cnt;
@@ -909,27 +976,28 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
     }  // epochs
 }
 
-template <int NWP, int G>
+template <int NWP, int G, bool GC = false>
 static size_t spec_smem() {
     constexpr int WID = NWP * kWarp * 4 * G;
-    size_t b = (size_t)WID * (4 + 4 + 16 + 4);
+    size_t b = (size_t)WID * (4 + 4 + (GC ? 0 : 16) + 4);
+    if (GC) b += (size_t)kGcRing * WID * 4;
     b += (size_t)kSpecRecSlots * kAtomRecord * 16;
     b += (size_t)kSpecSlots * (kAtomWords * 16 + NWP * 8 + 4 * 8 + 8 + 16);
     b += 16 + 16 * 4 + 6 * 16 * sizeof(double);
     return b;
 }
 
-template <int NWP, int G, int CH, bool SPLIT, bool BATCH = false>
+template <int NWP, int G, int CH, bool SPLIT, bool BATCH = false, bool GC = false>
 static void launch_spec(const EpochArgs<float> &A, cudaStream_t st, const SpecBatchArgs *B = nullptr,
                         int grid = 1) {
-    auto kern = k_epoch_spec<NWP, G, CH, SPLIT, BATCH>;
+    auto kern = k_epoch_spec<NWP, G, CH, SPLIT, BATCH, GC>;
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
         attr_set = true;
     }
     SpecBatchArgs none{};
-    kern<<<grid, NWP * kWarp + (2 + CH) * kWarp, spec_smem<NWP, G>(), st>>>(A, B ? *B : none);
+    kern<<<grid, NWP * kWarp + (2 + CH) * kWarp, spec_smem<NWP, G, GC>(), st>>>(A, B ? *B : none);
 }
 
 template <int CH, bool SPLIT>
@@ -976,8 +1044,25 @@ bool launch_spec_batch_solve(int bucket, bool uniform, const SpecBatchArgs &B, i
                    : launch_spec_batch_b<false>(bucket, A, B, count, st);
 }
 
+// Given cost: three chain warps in rotation, cyclic or permuted order, n a
+// multiple of 4 up to 8192 with 16-byte aligned rows.
+static bool launch_spec_given(const EpochArgs<float> &A, cudaStream_t st) {
+    const int n = A.in.n;
+    if (!A.vec || (n % 4) != 0) return false;
+    if (A.order != SR_OT_CYCLIC && A.order != SR_OT_PERMUTE) return false;
+    if (n <= 128 * 4) launch_spec<4, 1, 3, false, false, true>(A, st);
+    else if (n <= 128 * 8) launch_spec<4, 2, 3, false, false, true>(A, st);
+    else if (n <= 128 * 16) launch_spec<4, 4, 3, false, false, true>(A, st);
+    else if (n <= 128 * 32) launch_spec<4, 8, 3, false, false, true>(A, st);
+    else if (n <= 128 * 64) launch_spec<4, 16, 3, false, false, true>(A, st);
+    else return false;
+    return true;
+}
+
 bool launch_epoch_spec(const EpochArgs<float> &A, cudaStream_t st, int chain) {
-    if (A.variant != SR_OT_BCPFW || A.in.cost_mode != kCostPts3) return false;
+    if (A.variant != SR_OT_BCPFW) return false;
+    if (A.in.cost_mode == kCostGiven) return chain == 3 && launch_spec_given(A, st);
+    if (A.in.cost_mode != kCostPts3) return false;
     if (chain == kSpecChainSplit) {
         if (A.order != SR_OT_CYCLIC && A.order != SR_OT_PERMUTE && A.order != SR_OT_UNIFORM) return false;
         return launch_spec_ch<3, true>(A, st);

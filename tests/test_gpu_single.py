@@ -937,7 +937,9 @@ def test_fp32_dense_steps_conserve_row_mass(S, h, oracle_mod, variant, order):
                                                ("PERMUTE", 200, 1500, 15, "pts"), ("CYCLIC", 190, 600, 20, "cost"),
                                                ("CYCLIC", 1024, 4096, 3, "pts"), ("PERMUTE", 2048, 3000, 4, "pts"),
                                                ("CYCLIC", 3, 40, 200, "pts"), ("CYCLIC", 5000, 1025, 2, "pts"),
-                                               ("UNIFORM", 6, 300, 60, "pts"), ("UNIFORM", 40, 2000, 12, "pts")])
+                                               ("UNIFORM", 6, 300, 60, "pts"), ("UNIFORM", 40, 2000, 12, "pts"),
+                                               ("CYCLIC", 256, 8192, 3, "cost"), ("PERMUTE", 300, 2048, 6, "cost"),
+                                               ("CYCLIC", 3, 4100, 40, "cost"), ("CYCLIC", 100, 1001, 10, "cost")])
 def test_pairwise_kernels_match_two_phase(S, h, oracle_mod, order, m, n, ep, mode):
     """The pipelined BCPFW kernel takes the next row's LMO and away vertex over
     the columns the current update leaves unchanged and completes them at the
@@ -947,7 +949,10 @@ def test_pairwise_kernels_match_two_phase(S, h, oracle_mod, order, m, n, ep, mod
     the final plan equal the two-phase active-set kernel's bit for bit (where
     a kernel does not apply, the fallback runs and must match as well). In
     uniform order rows come back within a few updates (m = 6: every few
-    updates), which the split chain handles by re-reading the record."""
+    updates), which the split chain handles by re-reading the record. With a
+    given cost matrix the speculative kernel reads C (n a multiple of 4, up
+    to 8192 = the widest rows, where the last column can be the away vertex;
+    n = 1001 takes the fallback)."""
     inst = W.colour_instance(17 + m, m, n, rho=10.0, b_dirichlet=True).rounded()
     C = dev(oracle_mod.cost(inst.X, inst.Y), torch.float32) if mode == "cost" else None
     out = []
