@@ -95,9 +95,6 @@ __device__ inline bool mbar_try(uint64_t *b, unsigned parity) {
 }
 constexpr int kAtomWords = 3;  // atom warp output per update: int4 words
 
-// Given cost: the chain warp of an update pulls its row into L1 while it
-// prepares, so the entries it needs after the hand-over come from L1.
-__device__ inline void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];\n" ::"l"(p)); }
 
 }  // namespace
 
@@ -439,6 +436,25 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
         fetch_record(aw0 + 2);
         load_xa(0, aw0);
         load_xa(1, aw0 + 2);
+        // GC: the cost entries of the next update's head atoms (lane l: atom
+        // l < 7), loaded one iteration of this warp before their use
+        float pc = 0.f;
+        int pcj = -1;
+        auto prefetch_c = [&](int t) {
+            pcj = -1;
+            if (GC && t < m) {
+                const int4 *r = aring + (size_t)(t % kSpecRecSlots) * kAtomRecord;
+                if (lane < r[0].x && lane < kSpecRecHead - 1) {
+                    pcj = r[1 + lane].x;
+                    pc = __ldg(crow_of(row_of(t)) + pcj);
+                }
+            }
+        };
+        if constexpr (GC) {
+            wait_groups<1>();  // the head of update aw0's record
+            __syncwarp();
+            prefetch_c(aw0);
+        }
         for (int u = aw0; u < m; u += 2) {
             if (!gate(u)) break;
             wait_groups<1>();  // the head of update u's record has landed (u + 2's may be in flight)
@@ -458,7 +474,10 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
             LaneAtoms at = load_atoms(rs, lane);
             DF tvd{0.f, 0.f};
             const float *crow = crow_of(row_of(u));
-            auto grad = [&](int j) -> float { return grad_at(j, x0, x1, x2, crow); };
+            auto grad = [&](int j) -> float {
+                if constexpr (GC) return (j == pcj ? pc : __ldg(crow + j)) + qh[j];
+                else return grad_at(j, x0, x1, x2, crow);
+            };
             const AtomStats st = atom_stats(at, grad, au, false, &tvd);
             if (lane == 0) {
                 const float ra = au > 0.f ? 1.f / au : 0.f;
@@ -470,6 +489,11 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
                 o[1] = make_int4(__float_as_int(x0), __float_as_int(x1), __float_as_int(x2), __float_as_int(au));
                 o[2] = make_int4(__float_as_int(ra), __float_as_int(ia), row_of(u), 0);
                 mbar_arrive(full + u % kSpecSlots);
+            }
+            if constexpr (GC) {
+                wait_groups<0>();  // the head of update u + 2's record
+                __syncwarp();
+                prefetch_c(u + 2);
             }
             fetch_record(u + kSpecRecAhead);
             shift_xa();
@@ -764,8 +788,28 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
             // the atom warp's copy of the record (ordered by the full barrier)
             LaneAtoms at = load_atoms(aring + (size_t)(u % kSpecRecSlots) * kAtomRecord, lane);
             const float *crow = crow_of(row);
-            if constexpr (GC)  // the row into L1: 128-byte lines lane, lane + 32, ...
-                for (int off = 32 * lane; off < n; off += 32 * kWarp) prefetch_l1(crow + off);
+            // GC: the cost entries of row u at the likely columns of update
+            // u-1 (its segment minima and away vertex as prepared, and the
+            // columns of u-3, which it merges), loaded now so that the
+            // columns u-1 changes are found here after the hand-over
+            float pcv = 0.f, hcv = 0.f;
+            int pcx = -1, hcx = -1;
+            if constexpr (GC) {
+                if (u >= 1) {
+                    const int sp = (u - 1) % kSpecSlots;
+                    if (lane < NWP) {
+                        pcx = (int)(cand[sp * NWP + lane] >> 32);
+                    } else if (lane == NWP) {
+                        const int v14 = aw[sp * kAtomWords].w & 0x3FFF;  // may still be filling: only a guess
+                        pcx = v14 == 0x3FFF ? -1 : v14;
+                    } else if (lane < NWP + 3 && u >= 3) {
+                        const int2 d = dec[(u - 3) % kSpecSlots];
+                        pcx = lane == NWP + 1 ? d.x : d.y;
+                    }
+                    if (pcx >= 0 && pcx < n) pcv = __ldg(crow + pcx);
+                    else pcx = -1;
+                }
+            }
             auto grad = [&](int j) -> float { return grad_at(j, x0, x1, x2, crow); };
             // clean segment minima and the columns changed by updates ver..u-2
             uint32_t key = 0xFFFFFFFFu;
@@ -835,7 +879,16 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
             int js = pj;
             {
                 const int c = lane == 0 ? c2[0] : c2[1];
-                const uint32_t ke = (lane < 2 && c >= 0) ? f2key(grad(c)) : 0xFFFFFFFFu;
+                uint32_t ke = 0xFFFFFFFFu;
+                if (lane < 2 && c >= 0) {
+                    if constexpr (GC) {  // kept for the hand-over of u-1 (its columns may be these)
+                        hcx = c;
+                        hcv = __ldg(crow + c);
+                        ke = f2key(hcv + qh[c]);
+                    } else {
+                        ke = f2key(grad(c));
+                    }
+                }
                 const uint32_t k0 = __shfl_sync(FULL, ke, 0), k1 = __shfl_sync(FULL, ke, 1);
                 if (c2[0] >= 0 && (k0 < fk || (k0 == fk && c2[0] < js))) { fk = k0; js = c2[0]; }
                 if (c2[1] >= 0 && (k1 < fk || (k1 == fk && c2[1] < js))) { fk = k1; js = c2[1]; }
@@ -856,9 +909,22 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
             // row at its two columns (lanes 0, 1)
             const int ec = lane == 0 ? c1[0] : c1[1];
             float ce = 0.f;
+            if constexpr (GC) {
+                // the cost at the columns of u-1 from the entries loaded ahead,
+                // else (rarely) from memory
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int c = c1[e];
+                    const unsigned ma = __ballot_sync(FULL, c >= 0 && pcx == c);
+                    const unsigned mb = __ballot_sync(FULL, c >= 0 && hcx == c);
+                    const float va = __shfl_sync(FULL, pcv, ma ? __ffs(ma) - 1 : 0);
+                    const float vb = __shfl_sync(FULL, hcv, mb ? __ffs(mb) - 1 : 0);
+                    const float v = ma ? va : (mb ? vb : (c >= 0 ? __ldg(crow + c) : 0.f));
+                    if (lane == e) ce = v;
+                }
+            }
             if (lane < 2 && ec >= 0) {
                 if constexpr (GC) {
-                    ce = __ldg(crow + ec);
                 } else {
                     const float4 y = ys[ec];
                     const float d0 = x0 - y.x, d1 = x1 - y.y, d2 = x2 - y.z;
