@@ -51,9 +51,13 @@ BATCH_WORKLOADS = ("colour_batch512", "colour_batch64_2048")
 # is built from are the ones captured: their digest at capture time must match.
 CAPTURED_TRAFFIC = {
     ("colour4096_fp32", "roofline"): {
-        "bytes": 731648, "files": ("solve_spec.cu", "atoms.cuh", "step.cuh", "cpasync.cuh", "common.cuh",
+        "bytes": 731904, "files": ("solve_spec.cu", "atoms.cuh", "step.cuh", "cpasync.cuh", "common.cuh",
                                    "cert_records.cuh", "batched.h", "internal.h"),
-        "digest": "a566bce288bbb9e4"},
+        "digest": "4163572d83ddba7e"},
+    ("feature8192_d128", "roofline"): {
+        "bytes": 269801728 + 3680256, "files": ("solve_spec.cu", "atoms.cuh", "step.cuh", "cpasync.cuh", "common.cuh",
+                                                "cert_records.cuh", "batched.h", "internal.h"),
+        "digest": "4163572d83ddba7e"},
     ("feature8192_d128", "roofline_cost"): {
         "bytes": 4309248 + 206549504, "files": ("cost_bf16.cu", "common.cuh"), "digest": "a6c016e0c5144edc"},
     ("colour_batch64_2048", "roofline_adjoint"): {
@@ -241,8 +245,9 @@ def epoch_kernel_name(s, n):
     if s["variant"] == "BCAFW":
         return "k_epoch_sparse (one CTA, m block updates; active-set, away steps)"
     if s["precision"] == "FP32_BF16COST" and n <= 8192 and n % 4 == 0:
-        return ("k_epoch_spec (one CTA, m block updates; pairwise; given cost: producers stream each row, "
-                "the chain warp of an update pulls its row into L1; three chain warps in rotation)")
+        return ("k_epoch_spec (one CTA, m block updates; pairwise; given cost: producers stream each row "
+                "through a shared-memory ring, the chain keeps the cost at the likely changed columns; "
+                "three chain warps in rotation)")
     if s["precision"] != "FP32_BF16COST" and n <= 4096:
         return ("k_epoch_spec (one CTA, m block updates; pairwise; segment minima and away statistics taken "
                 "ahead by producer warps, three chain warps in rotation)")
@@ -621,7 +626,12 @@ def bench_single(args, s, ws, rank, local, cpu_leg):
         floor3 = h.chain_floor(3)
         extra.update(chain_floor_ns=floor3, chain_floor_ns_one_warp=h.chain_floor(1),
                      chain_frac=floor3 / extra["chain_ns_per_update"])
-    roof = alu_roofline(FLOPS_PER_GRAD * n * m, avg, peaks, peak_src, kname, extra)
+    if s["precision"] == "FP32_BF16COST":
+        # the epoch reads the materialised cost: one row of C (4 n bytes) per
+        # block update, and the changed plan entries (8 bytes per support entry)
+        roof = hbm_roofline(float(m) * (4.0 * n + 8.0 * supp), avg, peaks, peak_src, kname, extra)
+    else:
+        roof = alu_roofline(FLOPS_PER_GRAD * n * m, avg, peaks, peak_src, kname, extra)
     cfg = config_for(args, s, inst, ws)
     line = {"metric": metric_for(s),
             "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
