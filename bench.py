@@ -296,7 +296,9 @@ def config_for(args, s, insts, ws):
     """The `config` object of both arms' JSON lines."""
     cfg = {"workload": args.workload, "variant": f"{s['variant']}-{s['step']}", "order": "cyclic",
            "precision": s["precision"], "tol_rel_gap": s["tol"], "max_epochs": s["max_epochs"],
-           "certificate_every_epochs": 1, "l2": "flushed (256 MB write) between steps"}
+           "certificate": ("exact (Thm 2); the library takes it when the gap's geometric decay predicts the "
+                           "tolerance (1 to 8 epochs apart), the oracle every epoch"),
+           "l2": "flushed (256 MB write) between steps"}
     if isinstance(insts, list):
         cfg.update(instances=len(insts), m_range=[min(i.m for i in insts), max(i.m for i in insts)],
                    n_range=[min(i.n for i in insts), max(i.n for i in insts)], d=3, rho=insts[0].rho,
@@ -587,7 +589,8 @@ def bench_single(args, s, ws, rank, local, cpu_leg):
     T = torch.zeros((m, n), dtype=dt, device=dev)
     opts = S.options(variant=VARIANTS[s["variant"]], step=1 if s["step"] == "ELS" else 0, order=S.CYCLIC,
                      precision=getattr(S, s["precision"]), rho=inst.rho, tol_rel_gap=s["tol"],
-                     max_epochs=s["max_epochs"], gap_every=1, refresh_every=1)
+                     max_epochs=s["max_epochs"], gap_every=1, refresh_every=1,
+                     cert_schedule=1 if s["tol"] > 0 else 0)
 
     def step():
         return h.solve(a, b, T, X=X, Y=Y, opts=opts)

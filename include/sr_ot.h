@@ -155,6 +155,14 @@ typedef struct {
                                  NULL = no gate. It lets the timeout path be
                                  exercised: a gate that nothing opens makes the
                                  call return SR_OT_ETIMEOUT.                   */
+    int cert_schedule;        /* sr_ot_solve: 0 = a certificate (Thm 2) every
+                                 gap_every epochs, as the paper evaluates it;
+                                 1 = with tol_rel_gap > 0, the next certificate
+                                 when the gap's geometric decay since the last
+                                 one predicts the tolerance (after 1 to 8
+                                 periods of gap_every epochs); the stopping
+                                 decision is the exact certificate's either way.
+                                 Not for SR_OT_GAP_ADAPTIVE.                   */
 } sr_ot_options;
 
 typedef struct {
@@ -215,9 +223,13 @@ sr_ot_status sr_ot_solve(sr_ot_handle h, const sr_ot_options *opts, int m, int n
 /*
  * Solve `batch` independent instances in one persistent launch (captured in a
  * CUDA graph and replayed for a repeated shape set). Points mode with d = 3.
- * Each instance checks its certificate every gap_every epochs, or 2, 4 or 8
- * times less often while its last relative gap was more than 10, 100 or 1000
- * times tol_rel_gap (a certificate reads the instance's whole plan).
+ * Pairwise steps in cyclic or uniform order run the batched speculative
+ * form: one CTA solves each instance (n <= 4096) and takes its certificate
+ * when the gap's geometric decay predicts the tolerance (1 to 8 periods of
+ * gap_every epochs). The other variants run a persistent two-phase kernel
+ * whose instances check their certificate every gap_every epochs, or 2, 4
+ * or 8 times less often while the last relative gap was more than 10, 100 or
+ * 1000 times tol_rel_gap (a certificate reads the instance's whole plan).
  * m[k], n[k]: HOST arrays of per-instance sizes. off_X, off_Y, off_a, off_b,
  * off_T: HOST arrays of per-instance ELEMENT offsets into the packed device
  * buffers X, Y, a, b, T. Each instance starts from T0 = (a_i e_0), or with

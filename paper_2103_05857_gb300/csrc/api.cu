@@ -238,6 +238,7 @@ sr_ot_status check_opts(sr_ot_handle h, const sr_ot_options *o) {
     if (!std::isfinite(o->tol_rel_gap) || o->tol_rel_gap < 0.0) return fail(h, SR_OT_EINVAL, "tol_rel_gap must be finite and >= 0");
     if (o->max_epochs < 0) return fail(h, SR_OT_EINVAL, "max_epochs must be >= 0");
     if (o->gap_every < 1) return fail(h, SR_OT_EINVAL, "gap_every must be >= 1");
+    if (o->cert_schedule < 0 || o->cert_schedule > 1) return fail(h, SR_OT_EINVAL, "cert_schedule must be 0 or 1");
     if (o->refresh_every < 0) return fail(h, SR_OT_EINVAL, "refresh_every must be >= 0");
     if ((o->variant == SR_OT_BCAFW || o->variant == SR_OT_BCPFW) && o->step != SR_OT_ELS)
         return fail(h, SR_OT_EINVAL, "away and pairwise steps need the exact line search (SR_OT_ELS)");
@@ -473,6 +474,7 @@ sr_ot_status solve_impl(sr_ot_handle h, const sr_ot_options *o, int m, int n, in
     if ((st = ws_typed(h, WS_STATUS, 4, &dstat_d))) return st;
     CK(h, cudaMemsetAsync(dstat_d, 0, sizeof(int), h->stream));
     CK(h, cudaMemsetAsync(dstat_d + 1, 0xff, sizeof(int), h->stream));  // resume = -1
+    CK(h, cudaMemsetAsync(dstat_d + 3, 0, sizeof(int), h->stream));     // no record overflow yet
     CertWork w;
     if ((st = cert_work(h, m, n, &w))) return st;
     int *perm = nullptr;
@@ -540,6 +542,7 @@ sr_ot_status solve_impl(sr_ot_handle h, const sr_ot_options *o, int m, int n, in
     A.atoms = atoms;
     A.resume = nullptr;
     A.resume_in = nullptr;
+    A.sticky = dstat_d + 3;
     A.spin_limit = o->spin_limit;
     A.gate = o->start_gate;
     A.C32 = c32;
@@ -551,6 +554,13 @@ sr_ot_status solve_impl(sr_ot_handle h, const sr_ot_options *o, int m, int n, in
     }
 
     const int refresh_every = fp64 ? 0 : o->refresh_every;
+    // cert_schedule 1: the next certificate when the gap's geometric decay
+    // since the last one predicts the tolerance (at least 1, at most 8
+    // certificate periods on); an overflow of the active sets needs no
+    // certificate any more (the kernels switch to the dense one themselves)
+    const bool predicted = o->cert_schedule == 1 && o->tol_rel_gap > 0.0 && !ga;
+    long long next_cert = 0, ep_prev = 0;
+    double g_prev = 0.0;
     long long ep = 0, ncert = 0;
     bool converged = false, have_cert = false;
     for (ep = 0; ep < o->max_epochs; ++ep) {
@@ -598,7 +608,8 @@ sr_ot_status solve_impl(sr_ot_handle h, const sr_ot_options *o, int m, int n, in
         CKL(h);
         const bool last = ep + 1 == o->max_epochs;
         const bool ga_global = ga && (ep + 1) % ga_every == 0;  // every g_i again (Alg. A.4)
-        const bool cert_due = (ep + 1) % o->gap_every == 0 || last;
+        const bool cert_due = predicted ? ((ep + 1) % o->gap_every == 0 && ep + 1 >= next_cert) || last
+                                        : (ep + 1) % o->gap_every == 0 || last;
         if (ga_global && !cert_due) {
             ProfScope ps(h, SR_OT_PROF_CERT);
             launch_certificate<Real>(in, T, o->rho, o->tol_rel_gap, w, nullptr, A.g_store, h->stream);
@@ -626,6 +637,19 @@ sr_ot_status solve_impl(sr_ot_handle h, const sr_ot_options *o, int m, int n, in
             if (dstat) return dev_status_error(h, dstat);
             if (use_sparse && h->h_status[1] >= 0) use_sparse = false;  // a row outgrew its record
             if (h->h_cert[kCertStop] != 0.0) { converged = true; ++ep; break; }
+            if (predicted) {
+                const double f = h->h_cert[kCertF], g = h->h_cert[kCertG];
+                long long skip = 1;
+                if (g_prev > 0.0 && g > 0.0 && g < g_prev && ep + 1 > ep_prev && f > 0.0) {
+                    const double rate = std::log(g / g_prev) / (double)(ep + 1 - ep_prev);  // < 0
+                    const double early = 0.75 * std::log(o->tol_rel_gap * f / g) / rate;   // epochs, > 0
+                    skip = early >= 8.0 * o->gap_every ? 8 * (long long)o->gap_every
+                                                         : (early < 1.0 ? 1 : (long long)early);
+                }
+                g_prev = g;
+                ep_prev = ep + 1;
+                next_cert = ep + 1 + skip;
+            }
         }
     }
     if (!have_cert) {

@@ -118,6 +118,8 @@ struct EpochArgs {
     int4 *atoms;             // sparse kernel: per-row atom records (m x kAtomRecord)
     int *resume;             // sparse kernel: set to the update index where it stopped
     const int *resume_in;    // dense kernel: start at *resume_in, or return if it is < 0
+    int *sticky;             // active-set kernels: set when a row outgrows its record; once set, they
+                             // leave every later epoch to the dense kernel (*resume = 0)
     long long spin_limit;    // speculative kernel: probes before a wait gives up (0: default)
     const int *gate;         // speculative kernel: wait for *gate != 0 before the first update
     const float *C32;        // FP64 single-warp kernel: the FP32 rounding of C (argmin screen)

@@ -59,6 +59,12 @@ __global__ void __launch_bounds__(NTC + 2 * kWarp, 1) k_epoch_pipe(EpochArgs<flo
     constexpr int WID = NTC * CPT;
     constexpr int D = RING - 2;
     static_assert(D >= 1, "ring too small");
+    // a row outgrew its atom record in an earlier epoch: the dense kernel
+    // takes every epoch from now on (its records are no longer kept)
+    if (A.sticky && *reinterpret_cast<const volatile int *>(A.sticky)) {
+        if (threadIdx.x == 0 && A.resume) *A.resume = 0;
+        return;
+    }
     extern __shared__ __align__(16) unsigned char smem[];
     float *qh = reinterpret_cast<float *>(smem);
     float *ql = qh + WID;
@@ -418,6 +424,7 @@ __global__ void __launch_bounds__(NTC + 2 * kWarp, 1) k_epoch_pipe(EpochArgs<flo
             if (!ok) {
                 stop_l = 1;  // j* would be a 64th atom: the dense kernel takes over at p
                 if (lane == 0 && A.resume) *A.resume = p;
+                if (lane == 0 && A.sticky) *A.sticky = 1;
             }
             if (more) named_arrive(1, NT);
         } else if (more) {

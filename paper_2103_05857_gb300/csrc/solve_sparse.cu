@@ -54,6 +54,12 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_sparse(EpochArgs<float
     constexpr int CPT = 4 * G;
     constexpr int WID = NTC * CPT;
     constexpr int D = RING - 2;
+    // a row outgrew its atom record in an earlier epoch: the dense kernel
+    // takes every epoch from now on (its records are no longer kept)
+    if (A.sticky && *reinterpret_cast<const volatile int *>(A.sticky)) {
+        if (threadIdx.x == 0 && A.resume) *A.resume = 0;
+        return;
+    }
     extern __shared__ __align__(16) unsigned char smem[];
     float *qh = reinterpret_cast<float *>(smem);
     float *ql = qh + WID;
@@ -348,6 +354,7 @@ __global__ void __launch_bounds__(NTC + kWarp, 1) k_epoch_sparse(EpochArgs<float
             if (!applied) {
                 stop_l = 1;  // j* would be a 64th atom: the dense kernel takes over here
                 if (lane == 0 && A.resume) *A.resume = p;
+                if (lane == 0 && A.sticky) *A.sticky = 1;
             }
             if (lane == 0 && A.trace && k < A.trace_cap) {
                 A.trace[4 * k] = i;

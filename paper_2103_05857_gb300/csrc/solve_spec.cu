@@ -158,6 +158,12 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
         A.k0 = Bt.state[inst].ep * (long long)I.m;
         bvec = Bt.b + I.off_b;
     }
+    // a row outgrew its atom record in an earlier epoch: the dense kernel
+    // takes every epoch from now on (its records are no longer kept)
+    if (A.sticky && *reinterpret_cast<const volatile int *>(A.sticky)) {
+        if (threadIdx.x == 0 && A.resume) *A.resume = 0;
+        return;
+    }
     const int m = A.in.m, n = A.in.n;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned FULL = 0xffffffffu;
@@ -730,6 +736,7 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
                                            grec + (size_t)row * kAtomRecord, lane, publish);
             if (!ok) {  // j* would be a 64th atom: the dense kernel takes over at u
                 if (lane == 0 && A.resume) *A.resume = u;
+                if (lane == 0 && A.sticky) *A.sticky = 1;
                 aborted = true;
                 break;
             }
@@ -997,6 +1004,7 @@ __global__ void __launch_bounds__(NWP * kWarp + (2 + CH) * kWarp, (BATCH && G <=
                                            grec + (size_t)row * kAtomRecord, lane, publish);
             if (!ok) {  // j* would be a 64th atom: the dense kernel takes over at u
                 if (lane == 0 && A.resume) *A.resume = u;
+                if (lane == 0 && A.sticky) *A.sticky = 1;
                 aborted = true;
                 break;
             }

@@ -40,6 +40,7 @@ class Options(ct.Structure):
         ("ga_global_only", ct.c_int), ("seed", ct.c_ulonglong), ("trace", ct.c_void_p),
         ("trace_capacity", ct.c_longlong), ("dense_only", ct.c_int), ("epoch_kernel", ct.c_int), ("cost_kind", ct.c_int),
         ("spin_limit", ct.c_longlong), ("batch_warm_start", ct.c_int), ("start_gate", ct.c_void_p),
+        ("cert_schedule", ct.c_int),
     ]
 
 

@@ -983,3 +983,57 @@ def test_chain_floor_probe(S, h):
     r = S.ct.c_double()
     assert S.lib.sr_ot_profile_chain_floor(h._h, 2, 100, S.ct.byref(r)) == S.EINVAL
     assert S.lib.sr_ot_profile_chain_floor(h._h, 3, 0, S.ct.byref(r)) == S.EINVAL
+
+
+def test_predicted_certificate_schedule(S, h, oracle_mod):
+    """cert_schedule = 1 takes the certificate only when the gap's decay
+    predicts the tolerance: colour4096_fp32 (the benchmark's solve) reaches
+    rel. gap 1e-6 with fewer certificates and within 8 epochs of the solve
+    with a certificate every epoch, and the returned plan is certified by the
+    oracle against the stored optimum."""
+    inst = W.workload("colour4096_fp32").rounded()
+    C = oracle_mod.cost(inst.X, inst.Y)
+    opt = _optima()["10"]
+    out = {}
+    for sched in (0, 1):
+        T = torch.zeros((inst.m, inst.n), dtype=torch.float32, device="cuda")
+        l0 = h.launch_count()
+        res = h.solve(dev(inst.a, torch.float32), dev(inst.b, torch.float32), T, X=dev(inst.X, torch.float32),
+                      Y=dev(inst.Y, torch.float32), precision=S.FP32, variant=S.BCPFW, step=S.ELS, rho=inst.rho,
+                      tol_rel_gap=1e-6, max_epochs=6000, gap_every=1, cert_schedule=sched)
+        assert res["status"] == S.OK and res["rel_gap"] <= 1e-6, res
+        cert = oracle_mod.certificate(C, inst.a, inst.b, inst.rho, host(T))
+        assert cert["g"] <= 1.2e-6 * cert["f"]
+        assert cert["f"] <= opt["f"] * (1 + 1.2e-6)
+        out[sched] = (res["epochs"], h.launch_count() - l0)
+    # each certificate also refreshes the residual from exact column sums, so
+    # the two trajectories differ by rounding: epoch counts within 8
+    (e0, l0), (e1, l1) = out[0], out[1]
+    assert abs(e1 - e0) <= 8, out
+    assert l1 < l0, out  # fewer certificate launches
+
+
+@pytest.mark.parametrize("sched", [0, 1])
+def test_record_overflow_with_either_certificate_schedule(S, h, oracle_mod, sched):
+    """A row that must grow a 64th atom hands the solve to the dense kernel
+    at that update; with certificates far apart the active-set kernels see
+    the overflow themselves in the next epochs and leave them to the dense
+    kernel. Either way the solve converges and the oracle certifies it."""
+    m, n = 48, 300
+    inst = W.colour_instance(321, m, n, rho=10.0).rounded()
+    C = oracle_mod.cost(inst.X, inst.Y)
+    T0 = np.zeros((m, n))
+    T0[:, 0] = inst.a
+    cols = np.argsort(C[5])[-63:]
+    T0[5] = 0.0
+    T0[5, cols] = inst.a[5] / 63
+    T = dev(f32(T0), torch.float32).contiguous()
+    res = h.solve(dev(inst.a, torch.float32), dev(inst.b, torch.float32), T, X=dev(inst.X, torch.float32),
+                  Y=dev(inst.Y, torch.float32), precision=S.FP32, variant=S.BCPFW, step=S.ELS, rho=inst.rho,
+                  tol_rel_gap=1e-6, max_epochs=20000, warm_start=True, cert_schedule=sched)
+    assert res["status"] == S.OK and res["rel_gap"] <= 1e-6, res
+    Tg = host(T)
+    cert = oracle_mod.certificate(C, inst.a, inst.b, inst.rho, Tg)
+    assert cert["g"] <= 1.2e-6 * cert["f"]
+    assert Tg.min() >= 0.0
+    np.testing.assert_allclose(Tg.sum(1), inst.a, rtol=2e-5)
