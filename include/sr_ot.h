@@ -126,9 +126,17 @@ typedef struct {
                                  runs an epoch. All make the same decisions bit
                                  for bit; AUTO takes the first that applies of
                                  SPECULATIVE (d = 3 points, cyclic or permuted
+                                 order, n <= 4096; or a given cost C, also the
+                                 BF16 one, cyclic or permuted, n <= 8192 a
+                                 multiple of 4, rows 16-byte aligned),
+                                 SPECULATIVE_SPLIT (d = 3 points, uniform
                                  order, n <= 4096), PIPELINED (n <= 8192),
                                  TWO_PHASE. A kernel that does not apply falls
-                                 back the same way.                            */
+                                 back the same way. In sr_ot_solve_batched,
+                                 TWO_PHASE selects the persistent two-phase
+                                 kernel, any other value the batched
+                                 speculative form (pairwise steps, cyclic or
+                                 uniform order).                               */
     int cost_kind;            /* cost from points X, Y: SR_OT_COST_SQUARED
                                  (default) or SR_OT_COST_EUCLIDEAN, the paper's
                                  ||x_i - y_j||_2 (Sec. 5.1), built once into the
