@@ -218,9 +218,10 @@ const char *sr_ot_last_error(sr_ot_handle h);
  * holds the final plan.
  * res: host pointer, filled on return.
  * Limits: block-coordinate variants take n <= 8192 (FP32) or n <= 2048
- * (FP64); SR_OT_GAP_ADAPTIVE also needs m <= 8192 (its per-row gaps are
- * refreshed by a certificate pass every ga_M epochs, or every epoch with
- * ga_global_only). SR_OT_FW has no size limit beyond memory: each iteration
+ * (FP64); SR_OT_GAP_ADAPTIVE also needs m <= 262144 (the draw walks a tree
+ * of sums of the gaps held in shared memory: chunks of 32 rows, and past 8192
+ * rows super nodes of 32 chunks; the per-row gaps are refreshed by a
+ * certificate pass every ga_M epochs, or every epoch with ga_global_only). SR_OT_FW has no size limit beyond memory: each iteration
  * is a certificate pass (which gives every row's LMO vertex and the gap) and
  * one pass over T, so gap_every is not used.
  */

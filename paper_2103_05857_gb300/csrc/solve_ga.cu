@@ -7,7 +7,8 @@
 // memory. Warp 0 samples: u = draw(seed, 3, k) gives the target u * total;
 // a warp scan over contiguous groups of chunk sums finds the chunk, a second
 // scan over the chunk's 32 gaps finds the row (first row whose cumulative
-// weight exceeds the target). After the update of row i its gap is evaluated
+// weight exceeds the target). Past 8192 rows the tree has a third level:
+// sums of super nodes of 32 chunks, scanned first. After the update of row i its gap is evaluated
 // again at the new plan and residual (the line of Alg. A.4 that follows the
 // update), and the chunk sum is recomputed from its 32 entries, so no
 // rounding accumulates in the sums. Full refreshes of every g_i (every M
@@ -35,7 +36,9 @@ namespace srot {
 
 namespace {
 
-constexpr int kGaMaxChunks = 256;  // m <= 8192
+constexpr int kGaMaxChunks = 256;     // two-level sampling: m <= 8192
+constexpr int kGaMaxSupers = 256;     // three-level sampling (32 chunks of 32 rows per super
+                                      // node): m <= 262144
 
 // Row drawn by gap-adaptive sampling; run by all 32 lanes of one warp,
 // returns the row on every lane.
@@ -108,6 +111,93 @@ __device__ inline int ga_sample(const double *g, const double *csum, int m, unsi
     return chunk * 32 + (31 - __clz(pos));
 }
 
+// Among 32 weights w (one per lane, in order) preceded by weight `base`: the
+// first lane whose cumulative weight exceeds `target` (with *before, the
+// weight before it), or with base < 0 (or no such lane: rounding put the
+// target past the total) the last lane of positive weight (*before = -1).
+// -1 if no weight is positive. All 32 lanes; every lane returns the same.
+__device__ inline int ga_pick32(double w, double base, double target, double *before) {
+    const unsigned F = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    double ci = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double v = __shfl_up_sync(F, ci, o);
+        if (lane >= o) ci += v;
+    }
+    const unsigned hit = base >= 0.0 ? __ballot_sync(F, w > 0.0 && base + ci > target) : 0u;
+    if (hit) {
+        const int l = __ffs(hit) - 1;
+        *before = base + __shfl_sync(F, ci - w, l);
+        return l;
+    }
+    const unsigned pos = __ballot_sync(F, w > 0.0);
+    *before = -1.0;
+    return pos ? 31 - __clz(pos) : -1;
+}
+
+// Gap-adaptive draw for m > 8192: the same inverse transform over a
+// three-level tree of cumulative sums (super nodes of 32 chunks of 32 rows):
+// a warp scan over the super sums (contiguous groups per lane) finds the
+// super node, a scan over its 32 chunk sums the chunk, a scan over the
+// chunk's 32 gaps the row. One warp; returns the row on every lane.
+__device__ inline int ga_sample3(const double *g, const double *csum, const double *ssum, int m,
+                                 unsigned long long seed, long long k) {
+    const unsigned F = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int nch = (m + 31) >> 5;
+    const int nsup = (nch + 31) >> 5;
+    const int L = (nsup + 31) >> 5;  // super nodes per lane, contiguous
+    const uint64_t u64 = sm64_draw(seed, 3, (uint64_t)k);
+    double part = 0.0;
+    for (int c = lane * L; c < min(nsup, lane * L + L); ++c) part += ssum[c];
+    double incl = part;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double v = __shfl_up_sync(F, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const double total = __shfl_sync(F, incl, 31);
+    if (!(total > 0.0)) return scale_u64(u64, m);
+    const double target = (double)(u64 >> 11) * 0x1.0p-53 * total;
+    // the super node: within the lane group that crosses the target
+    const unsigned cross = __ballot_sync(F, incl > target && part > 0.0);
+    int sup = -1;
+    double base = -1.0;
+    if (cross) {
+        const int src = __ffs(cross) - 1;
+        if (lane == src) {
+            double cum = incl - part;
+            for (int c = src * L; c < min(nsup, src * L + L); ++c) {
+                if (ssum[c] > 0.0 && cum + ssum[c] > target) { sup = c; base = cum; break; }
+                cum += ssum[c];
+            }
+            if (sup < 0)  // rounding: the last positive super node of the group
+                for (int c = min(nsup, src * L + L) - 1; c >= src * L; --c)
+                    if (ssum[c] > 0.0) { sup = c; base = -1.0; break; }
+        }
+        sup = __shfl_sync(F, sup, src);
+        base = __shfl_sync(F, base, src);
+    } else {
+        int lastc = -1;
+        for (int c = lane * L; c < min(nsup, lane * L + L); ++c)
+            if (ssum[c] > 0.0) lastc = c;
+        sup = __reduce_max_sync(F, lastc + 1) - 1;
+    }
+    if (sup < 0) return scale_u64(u64, m);
+    const int c1 = sup * 32 + lane;
+    double before = -1.0;
+    const int lc = ga_pick32(c1 < nch ? csum[c1] : 0.0, base, target, &before);
+    if (lc < 0) return scale_u64(u64, m);
+    const int chunk = sup * 32 + lc;
+    const int r = chunk * 32 + lane;
+    const double w = (r < m && g[r] > 0.0) ? g[r] : 0.0;
+    double unused;
+    const int lr = ga_pick32(w, before, target, &unused);
+    if (lr < 0) return scale_u64(u64, m);
+    return chunk * 32 + lr;
+}
+
 template <typename Real, int NT, int G, bool PTS, bool AWAY>
 __global__ void __launch_bounds__(NT, 1) k_epoch_ga(EpochArgs<Real> A) {
     using RedT = typename std::conditional<std::is_same<Real, float>::value, RedF, RedD>::type;
@@ -117,8 +207,9 @@ __global__ void __launch_bounds__(NT, 1) k_epoch_ga(EpochArgs<Real> A) {
     constexpr int WID = NT * CPT;
     __shared__ __align__(16) Real rowbuf[WID];
     __shared__ RedT red[2][kMaxWarps];
-    __shared__ double csum[kGaMaxChunks];
+    __shared__ double ssum[kGaMaxSupers];
     __shared__ int sel;
+    extern __shared__ double csum[];  // chunk sums: ceil(m / 32)
 
     const int m = A.in.m, n = A.in.n;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -157,6 +248,19 @@ __global__ void __launch_bounds__(NT, 1) k_epoch_ga(EpochArgs<Real> A) {
         if (lane == 0) csum[c] = w;
     }
     __syncthreads();
+    // super-node sums (32 chunks each), for m > 8192
+    const bool three = nch > kGaMaxChunks;
+    const int nsup = (nch + 31) >> 5;
+    if (three) {
+        for (int sp = warp; sp < nsup; sp += NW) {
+            const int c = sp * 32 + lane;
+            double w = c < nch ? csum[c] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+            if (lane == 0) ssum[sp] = w;
+        }
+        __syncthreads();
+    }
 
     const bool sums = (A.variant == SR_OT_BCFW && A.step == SR_OT_ELS) || A.variant == SR_OT_BCAFW;
     const bool cnt = A.variant == SR_OT_BCAFW;
@@ -165,7 +269,7 @@ __global__ void __launch_bounds__(NT, 1) k_epoch_ga(EpochArgs<Real> A) {
     for (int p = 0; p < m; ++p) {
         const long long k = A.k0 + p;
         if (warp == 0) {
-            const int i = ga_sample(g, csum, m, A.seed, k);
+            const int i = three ? ga_sample3(g, csum, ssum, m, A.seed, k) : ga_sample(g, csum, m, A.seed, k);
             if (lane == 0) sel = i;
         }
         __syncthreads();
@@ -328,6 +432,14 @@ __global__ void __launch_bounds__(NT, 1) k_epoch_ga(EpochArgs<Real> A) {
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
                 if (lane == 0) csum[c0] = w;
+                if (three) {  // its super node's sum, from its 32 chunk sums
+                    __syncwarp();
+                    const int c = (c0 >> 5) * 32 + lane;
+                    double w2 = c < nch ? csum[c] : 0.0;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) w2 += __shfl_xor_sync(0xffffffffu, w2, o);
+                    if (lane == 0) ssum[c0 >> 5] = w2;
+                }
             }
         }
         __syncthreads();  // sampling reads csum and g; rowbuf is rewritten
@@ -346,22 +458,35 @@ __global__ void __launch_bounds__(NT, 1) k_epoch_ga(EpochArgs<Real> A) {
         }
 }
 
+template <typename Real, int NT, int G, bool PTS, bool AWAY>
+void launch_ga_kernel(const EpochArgs<Real> &A, cudaStream_t st) {
+    auto kern = k_epoch_ga<Real, NT, G, PTS, AWAY>;
+    const size_t dyn = sizeof(double) * (size_t)((A.in.m + 31) / 32);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(double) * (32 * kGaMaxSupers)));
+        attr_set = true;
+    }
+    kern<<<1, NT, dyn, st>>>(A);
+}
+
 template <typename Real, int NT, int G>
 void launch_ga_shape(const EpochArgs<Real> &A, cudaStream_t st) {
     const bool pts = A.in.cost_mode == kCostPts3;
     const bool away = A.variant == SR_OT_BCAFW || A.variant == SR_OT_BCPFW;
     if (pts) {
-        if (away) k_epoch_ga<Real, NT, G, true, true><<<1, NT, 0, st>>>(A);
-        else k_epoch_ga<Real, NT, G, true, false><<<1, NT, 0, st>>>(A);
+        if (away) launch_ga_kernel<Real, NT, G, true, true>(A, st);
+        else launch_ga_kernel<Real, NT, G, true, false>(A, st);
     } else {
-        if (away) k_epoch_ga<Real, NT, G, false, true><<<1, NT, 0, st>>>(A);
-        else k_epoch_ga<Real, NT, G, false, false><<<1, NT, 0, st>>>(A);
+        if (away) launch_ga_kernel<Real, NT, G, false, true>(A, st);
+        else launch_ga_kernel<Real, NT, G, false, false>(A, st);
     }
 }
 
 }  // namespace
 
-int epoch_ga_max_m() { return 32 * kGaMaxChunks; }
+int epoch_ga_max_m() { return 32 * 32 * kGaMaxSupers; }
 
 template <>
 bool launch_epoch_ga<float>(const EpochArgs<float> &A, cudaStream_t st) {

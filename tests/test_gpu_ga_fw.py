@@ -63,13 +63,34 @@ def test_ga_fp64_decay_sequence(S, h, oracle_mod, ga_M, glob):
     assert rel(res["objective"], ro["f"]) <= 1e-12
 
 
-def test_ga_concentrates_on_large_gaps(S, h, oracle_mod):
+@pytest.mark.parametrize("m", [8192, 8193, 12000])
+def test_ga_fp64_decay_sequence_large_m(S, h, oracle_mod, m):
+    """Past 8192 rows the draw goes through a third level of sums (super
+    nodes of 32 chunks of 32 rows); 8192 is the largest two-level case."""
+    inst = W.colour_instance(81, m, 24, rho=10.0, b_dirichlet=True)
+    C = oracle_mod.cost(inst.X, inst.Y)
+    ep = 2
+    To, ro, ti, tj, _ = oracle_mod.solve(C, inst.a, inst.b, rho=inst.rho, variant=oracle_mod.BCFW,
+                                         step=oracle_mod.DEC, order=oracle_mod.GAP, seed=6, ga_M=1,
+                                         max_epochs=ep, trace=True)
+    cap = ep * inst.m
+    tr = torch.full((4 * cap,), -1, dtype=torch.int32, device="cuda")
+    T, res = _solve64(S, h, inst, variant=S.BCFW, step=S.DEC, order=S.GAP_ADAPTIVE, seed=6, ga_M=1,
+                      max_epochs=ep, trace=tr, trace_capacity=cap)
+    trh = tr.cpu().numpy().reshape(-1, 4)
+    np.testing.assert_array_equal(trh[:, 0], ti)
+    np.testing.assert_array_equal(trh[:, 1], tj)
+    assert np.abs(host(T) - To).max() <= 1e-13
+    assert rel(res["objective"], ro["f"]) <= 1e-12
+
+
+@pytest.mark.parametrize("m,ep", [(64, 5), (9000, 2)])
+def test_ga_concentrates_on_large_gaps(S, h, oracle_mod, m, ep):
     """The sampled rows follow the gaps: rows with zero gap are never drawn."""
-    inst = W.colour_instance(78, 64, 80, rho=10.0)
+    inst = W.colour_instance(78, m, 80, rho=10.0)
     a = inst.a.copy()
     a[::2] = 0.0  # zero-weight rows have g_i = 0 at every T
     a /= a.sum()
-    ep = 5
     cap = ep * inst.m
     tr = torch.full((4 * cap,), -1, dtype=torch.int32, device="cuda")
     T = torch.zeros((inst.m, inst.n), dtype=torch.float64, device="cuda")
