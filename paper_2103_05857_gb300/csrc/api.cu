@@ -853,9 +853,11 @@ sr_ot_status solve_batched_spec(sr_ot_handle h, const sr_ot_options *o, int batc
         bq[bk].push_back(k);
         qlen = std::max(qlen, inst[k].off_b + n[k]);
     }
-    // largest first within a bucket: the hardware starts CTAs in index order
-    auto by_size = [&](int x, int y) { return (long long)m[x] * n[x] > (long long)m[y] * n[y]; };
-    for (auto &v : bq) std::stable_sort(v.begin(), v.end(), by_size);
+    // longest epoch first within a bucket (the hardware starts CTAs in index
+    // order): an update costs about the same at every width of a bucket, so
+    // an instance's chain is m updates per epoch
+    auto by_chain = [&](int x, int y) { return m[x] != m[y] ? m[x] > m[y] : n[x] > n[y]; };
+    for (auto &v : bq) std::stable_sort(v.begin(), v.end(), by_chain);
     std::vector<int> hlist, lstart(kSpecBatchBuckets + 1, 0);
     for (int bk = 0; bk < kSpecBatchBuckets; ++bk) {
         lstart[bk] = (int)hlist.size();

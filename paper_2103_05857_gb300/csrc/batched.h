@@ -81,8 +81,8 @@ struct SpecBatchArgs {
 };
 
 constexpr int kSpecBatchMaxN = 4096;
-constexpr int kSpecBatchBuckets = 4;
-// Width bucket of an instance (n <= 512 * 2^bucket), -1 above kSpecBatchMaxN.
+constexpr int kSpecBatchBuckets = 2;
+// Width bucket of an instance (n <= 2048 * 2^bucket), -1 above kSpecBatchMaxN.
 int spec_batch_bucket(int n);
 // Set-up of the instances list[0 .. count).
 void launch_spec_batch_init(const SpecBatchArgs &B, int count, cudaStream_t st);

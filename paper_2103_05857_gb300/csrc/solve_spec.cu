@@ -1087,18 +1087,20 @@ static bool launch_spec_ch(const EpochArgs<float> &A, cudaStream_t st) {
 
 int spec_batch_bucket(int n) {
     for (int b = 0; b < kSpecBatchBuckets; ++b)
-        if (n <= 512 << b) return b;
+        if (n <= 2048 << b) return b;
     return -1;
 }
 
 template <bool SPLIT>
 static bool launch_spec_batch_b(int bucket, const EpochArgs<float> &A, const SpecBatchArgs &B, int count,
                                 cudaStream_t st) {
+    // one instantiation for every n <= 2048: CTAs of different kernels on
+    // one SM slowed each other's chains far more than two of the same code
+    // (measured at 2048-column tiles: 1.21x for a pair of one kernel, above
+    // 2x for a 2048-wide and a 512-wide kernel side by side)
     switch (bucket) {
-        case 0: launch_spec<4, 1, 3, SPLIT, true>(A, st, &B, count); return true;
-        case 1: launch_spec<4, 2, 3, SPLIT, true>(A, st, &B, count); return true;
-        case 2: launch_spec<4, 4, 3, SPLIT, true>(A, st, &B, count); return true;
-        case 3: launch_spec<4, 8, 3, SPLIT, true>(A, st, &B, count); return true;
+        case 0: launch_spec<4, 4, 3, SPLIT, true>(A, st, &B, count); return true;
+        case 1: launch_spec<4, 8, 3, SPLIT, true>(A, st, &B, count); return true;
         default: return false;
     }
 }
