@@ -253,6 +253,30 @@ def test_batched_warm_start(S, h, oracle_mod):
     assert cert["g"] <= 1.5e-6 * cert["f"]
 
 
+def test_batched_speculative_both_widths_at_once(S, h, oracle_mod):
+    """The speculative form runs n <= 2048 and 2048 < n <= 4096 as two
+    concurrent launches (2048- and 4096-column tiles); instances of both,
+    in one call, are each certified by the oracle."""
+    from paper_2103_05857_gb300.batch import PackedBatch
+    sizes = [(500, 3000), (1200, 700), (300, 2100), (90, 4096), (700, 2048), (64, 65)]
+    insts = [W.colour_instance(4200 + k, m, n, rho=10.0, b_dirichlet=bool(k % 2)).rounded()
+             for k, (m, n) in enumerate(sizes)]
+    pb = PackedBatch(insts)
+    st, res = h.solve_batched(pb.X, pb.Y, pb.a, pb.b, pb.T, pb.sizes, pb.offsets, variant=S.BCPFW,
+                              step=S.ELS, rho=10.0, tol_rel_gap=1e-6, max_epochs=20000)
+    assert st == S.OK
+    for k, inst in enumerate(insts):
+        r = res[k]
+        assert r["status"] == S.OK and r["rel_gap"] <= 1e-6, (k, r)
+        Tg = host(pb.plan(k))
+        cert = oracle_mod.certificate(oracle_mod.cost(inst.X, inst.Y), inst.a, inst.b, inst.rho, Tg)
+        assert rel(r["objective"], cert["f"]) <= 2e-7
+        assert abs(r["gap"] - cert["g"]) <= 2e-7 * cert["f"]
+        assert cert["g"] <= 1.5e-6 * cert["f"], (k, cert["g"] / cert["f"])
+        assert Tg.min() >= 0.0
+        np.testing.assert_allclose(Tg.sum(1), inst.a, rtol=2e-5)
+
+
 def test_batched_speculative_fixed_epochs_and_zero_epochs(S, h, oracle_mod):
     """Without a tolerance the batched speculative form runs exactly
     max_epochs epochs of every instance (uniform order here), and the
