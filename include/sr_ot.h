@@ -233,9 +233,9 @@ sr_ot_status sr_ot_solve(sr_ot_handle h, const sr_ot_options *opts, int m, int n
  * Solve `batch` independent instances in one persistent launch (captured in a
  * CUDA graph and replayed for a repeated shape set). Points mode with d = 3.
  * Pairwise steps in cyclic or uniform order run the batched speculative
- * form: one CTA solves each instance (n <= 4096) and takes its certificate
- * when the gap's geometric decay predicts the tolerance (1 to 8 periods of
- * gap_every epochs). The other variants run a persistent two-phase kernel
+ * form: one CTA solves each instance (n <= 4096; instances with more rows
+ * start first) and takes its certificate when the gap's geometric decay
+ * predicts the tolerance (1 to 8 periods of gap_every epochs). The other variants run a persistent two-phase kernel
  * whose instances check their certificate every gap_every epochs, or 2, 4
  * or 8 times less often while the last relative gap was more than 10, 100 or
  * 1000 times tol_rel_gap (a certificate reads the instance's whole plan).
