@@ -51,13 +51,13 @@ BATCH_WORKLOADS = ("colour_batch512", "colour_batch64_2048")
 # is built from are the ones captured: their digest at capture time must match.
 CAPTURED_TRAFFIC = {
     ("colour4096_fp32", "roofline"): {
-        "bytes": 732416, "files": ("solve_spec.cu", "atoms.cuh", "step.cuh", "cpasync.cuh", "common.cuh",
+        "bytes": 733440, "files": ("solve_spec.cu", "atoms.cuh", "step.cuh", "cpasync.cuh", "common.cuh",
                                    "cert_records.cuh", "batched.h", "internal.h"),
-        "digest": "63b6de8696b7dcdc"},
+        "digest": "955cbcb7a06fa863"},
     ("feature8192_d128", "roofline"): {
-        "bytes": 269822976 + 3280896, "files": ("solve_spec.cu", "atoms.cuh", "step.cuh", "cpasync.cuh", "common.cuh",
+        "bytes": 269742336 + 3024384, "files": ("solve_spec.cu", "atoms.cuh", "step.cuh", "cpasync.cuh", "common.cuh",
                                                 "cert_records.cuh", "batched.h", "internal.h"),
-        "digest": "63b6de8696b7dcdc"},
+        "digest": "955cbcb7a06fa863"},
     ("feature8192_d128", "roofline_cost"): {
         "bytes": 4309248 + 206549504, "files": ("cost_bf16.cu", "common.cuh"), "digest": "a6c016e0c5144edc"},
     ("colour_batch64_2048", "roofline_adjoint"): {
