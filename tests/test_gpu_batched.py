@@ -158,8 +158,9 @@ def test_batched_instance_turning_non_finite_is_isolated(S, h, oracle_mod):
     assert st == S.OK and all(r["status"] == S.OK for r in res)
 
 
-# every size bucket of the batched kernel (n <= 256, 512, 1024, 2048), two
-# instances each, with m across the whole range of the colour_batch512 workload
+# every size bucket of the two-phase batched kernel (n <= 256, 512, 1024, 2048;
+# the speculative form takes them all in its 2048-column tile), two instances
+# each, with m across the whole range of the colour_batch512 workload
 FULL_SIZES = [(300, 250), (1900, 256), (700, 500), (2048, 511), (1500, 1000), (400, 1024),
               (2048, 2048), (1200, 1900)]
 
